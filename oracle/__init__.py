@@ -1,0 +1,244 @@
+"""FP64 CPU oracle for the sparse LBGK collide-and-stream path (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+package.  It wraps ``oracle.c`` (plain C, float64, optional OpenMP over sites)
+through ctypes and shares no code with the CUDA library.  Each function
+follows the stated reading of the paper's method (Section 2: collision and
+propagation over sparse fluid sites; Section 4: simple bounce-back walls);
+see ``oracle.c`` for the definitions.
+
+All arrays use caller site order; populations are float64 [q, n].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None  # the default Oracle instance
+_lock = threading.Lock()
+
+
+def _compile(src: str, out: str) -> None:
+    base = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", src, "-o", out + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:4] + ["-fopenmp"] + base[4:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(out + ".tmp", out)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (OpenMP when available); returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    _compile(_SRC, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _bind(path: str):
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i64, i32, f64 = C.c_int64, C.c_int, C.c_double
+    lib.orc_lattice.argtypes = [i32, P, P, P]
+    lib.orc_equilibrium.argtypes = [i32, f64, P, P]
+    lib.orc_links_build.argtypes = [i32, i64, P, i64, P, P, P, P, P]
+    lib.orc_step.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, P, P]
+    lib.orc_run.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, P]
+    lib.orc_macros.argtypes = [i32, i64, P, f64, P, P, P, P]
+    lib.orc_mass.argtypes = [i32, i64, P]
+    lib.orc_mass.restype = f64
+    lib.orc_num_threads.restype = i32
+    lib.orc_set_threads.argtypes = [i32]
+    return lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class _Iolets:
+    def __init__(self, geom=None, rho_mean=None, amp=None, period=None, phase=None):
+        if geom is not None:
+            rho_mean, amp, period, phase = geom.rho_mean, geom.amp, geom.period, geom.phase
+        k = 0 if rho_mean is None else len(rho_mean)
+        z = np.zeros(max(k, 1))
+        self.k = k
+        self.mean = _c(rho_mean if k else z, np.float64)
+        self.amp = _c(amp if (k and amp is not None) else z, np.float64)
+        self.period = _c(period if (k and period is not None) else z, np.float64)
+        self.phase = _c(phase if (k and phase is not None) else z, np.float64)
+
+
+class Oracle:
+    """The oracle functions bound to one compiled copy of the C source."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.lib = _bind(path)
+
+    def num_threads(self) -> int:
+        return int(self.lib.orc_num_threads())
+
+    def set_threads(self, nt: int) -> None:
+        self.lib.orc_set_threads(int(nt))
+
+    def lattice(self, q: int):
+        """(c [q,3] int32, w [q] float64, opp [q] int32) of D3Q15 or D3Q19."""
+        e = np.zeros((q, 3), np.int32)
+        w = np.zeros(q, np.float64)
+        opp = np.zeros(q, np.int32)
+        if self.lib.orc_lattice(q, _p(e), _p(w), _p(opp)) != 0:
+            raise ValueError("q must be 15 or 19")
+        return e, w, opp
+
+    def equilibrium(self, q: int, rho: float, u) -> np.ndarray:
+        u = _c(u, np.float64)
+        out = np.zeros(q, np.float64)
+        if self.lib.orc_equilibrium(q, float(rho), _p(u), _p(out)) != 0:
+            raise ValueError("q must be 15 or 19")
+        return out
+
+    def links_build(self, q: int, xyz, io_xyz=None, io_id=None, periodic=(0, 0, 0)):
+        """Neighbour table nbr int32 [q, n] and link flags uint8 [q, n]."""
+        xyz = _c(xyz, np.int32).reshape(-1, 3)
+        n = xyz.shape[0]
+        io_xyz = _c(np.zeros((0, 3)) if io_xyz is None else io_xyz, np.int32).reshape(-1, 3)
+        io_id = _c(np.zeros(0) if io_id is None else io_id, np.int32)
+        per = _c(periodic, np.int32)
+        nbr = np.zeros((q, n), np.int32)
+        link = np.zeros((q, n), np.uint8)
+        r = self.lib.orc_links_build(q, n, _p(xyz), io_xyz.shape[0], _p(io_xyz), _p(io_id),
+                                     _p(per), _p(nbr), _p(link))
+        if r != 0:
+            raise ValueError("orc_links_build failed with %d" % r)
+        return nbr, link
+
+    def step(self, q, nbr, link, tau, f, t=0, geom=None, **io):
+        """One push-form step t -> t+1; returns the new [q, n] populations."""
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        f = _c(f, np.float64)
+        n = f.shape[1]
+        I = _Iolets(geom, **io)
+        out = np.empty_like(f)
+        r = self.lib.orc_step(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
+                              _p(I.period), _p(I.phase), int(t), _p(f), _p(out))
+        if r != 0:
+            raise ValueError("orc_step failed")
+        return out
+
+    def run(self, q, nbr, link, tau, f, nsteps, t0=0, geom=None, **io):
+        """nsteps steps from time t0; returns the state at t0 + nsteps."""
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        n = f.shape[1]
+        I = _Iolets(geom, **io)
+        work = np.empty_like(f)
+        r = self.lib.orc_run(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
+                             _p(I.period), _p(I.phase), int(t0), int(nsteps), _p(f), _p(work))
+        if r != 0:
+            raise ValueError("orc_run failed")
+        return f
+
+    def macros(self, q, link, tau, f):
+        """(rho [n], u [n,3], wss [n]) of the pre-collision state f."""
+        link = _c(link, np.uint8)
+        f = _c(f, np.float64)
+        n = f.shape[1]
+        rho = np.empty(n)
+        u = np.empty((n, 3))
+        wss = np.empty(n)
+        if self.lib.orc_macros(q, n, _p(link), float(tau), _p(f), _p(rho), _p(u), _p(wss)) != 0:
+            raise ValueError("orc_macros failed")
+        return rho, u, wss
+
+    def mass(self, f) -> float:
+        f = _c(f, np.float64)
+        return float(self.lib.orc_mass(f.shape[0], f.shape[1], _p(f)))
+
+    def rest_state(self, q: int, n: int, rho0: float = 1.0) -> np.ndarray:
+        """f_i = w_i rho0 at every site (fluid at rest)."""
+        _, w, _ = self.lattice(q)
+        return np.repeat((w * rho0)[:, None], n, axis=1)
+
+
+def default() -> Oracle:
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = Oracle(build())
+        return _lib
+
+
+def variant(src_text: str, workdir: str) -> Oracle:
+    """Compile a modified copy of the oracle source (used by the tests that
+    plant a mistake in the oracle and check that a pin catches it)."""
+    os.makedirs(workdir, exist_ok=True)
+    src = os.path.join(workdir, "oracle_variant.c")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    out = os.path.join(workdir, "liboracle_variant.so")
+    _compile(src, out)
+    return Oracle(out)
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def num_threads() -> int:
+    return default().num_threads()
+
+
+def set_threads(nt: int) -> None:
+    default().set_threads(nt)
+
+
+def lattice(q):
+    return default().lattice(q)
+
+
+def equilibrium(q, rho, u):
+    return default().equilibrium(q, rho, u)
+
+
+def links_build(q, xyz, io_xyz=None, io_id=None, periodic=(0, 0, 0)):
+    return default().links_build(q, xyz, io_xyz, io_id, periodic)
+
+
+def step(q, nbr, link, tau, f, t=0, geom=None, **io):
+    return default().step(q, nbr, link, tau, f, t, geom, **io)
+
+
+def run(q, nbr, link, tau, f, nsteps, t0=0, geom=None, **io):
+    return default().run(q, nbr, link, tau, f, nsteps, t0, geom, **io)
+
+
+def macros(q, link, tau, f):
+    return default().macros(q, link, tau, f)
+
+
+def mass(f):
+    return default().mass(f)
+
+
+def rest_state(q: int, n: int, rho0: float = 1.0) -> np.ndarray:
+    """f_i = w_i rho0 at every site (fluid at rest)."""
+    return default().rest_state(q, n, rho0)

@@ -1,0 +1,349 @@
+/*
+ * FP64 CPU oracle for the sparse lattice-Boltzmann (LBGK) collide-and-stream
+ * path.  TEST INFRASTRUCTURE ONLY: it is called by the tests, by the smoke
+ * check and by the timed CPU baseline of the benchmark, never by the product
+ * library, and it shares no code, header, table or helper with it.
+ *
+ * What the paper fixes (HemeLB, arXiv 1906.11925):
+ *   Section 2: the fluid is a lattice of sparse fluid sites, each holding a
+ *     single-particle distribution over a finite set of lattice vectors; a
+ *     time step is a collision followed by propagation to the neighbouring
+ *     site along each vector; the lattice is D3Q19 (Fig. 1).
+ *   Section 4: walls use simple bounce-back.
+ * Everything else is a stated reading (the paper gives no equation):
+ *   - single-relaxation-time (LBGK) collision toward the compressible
+ *     second-order equilibrium
+ *       feq_i = w_i rho (1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 |u|^2),
+ *   - D3Q15 as a second velocity set (textbook weights 2/9, 1/9, 1/72),
+ *   - halfway bounce-back: a population that would leave x through a wall
+ *     link i comes back to x as population opp(i) at the next step,
+ *   - density (pressure) iolets: a link from x into iolet k returns the
+ *     equilibrium population feq_opp(i)(rho_k(t), u(x,t)) with the iolet's
+ *     prescribed density and the site's own velocity,
+ *     rho_k(t) = mean_k + amp_k sin(2 pi t / period_k + phase_k),
+ *   - wall shear stress from the non-equilibrium stress
+ *       sigma = -(1 - 1/(2 tau)) sum_i (f_i - feq_i) c_i c_i,
+ *     traction t = sigma n, WSS = |t - (n.t) n|, with the wall normal
+ *     n = -normalize(sum of c_i over the site's wall links).
+ *
+ * Direction order: 0 is the rest vector; after it, opposite vectors are
+ * adjacent (opp(i) = i + 1 for odd i, i - 1 for even i > 0).
+ *
+ * Layouts: populations f[q][n] (direction-major), caller site order;
+ * nbr[q][n] int32 (index of the site x + c_i, -1 if none); link[q][n] uint8
+ * (0 fluid, 1 wall, 2 + k iolet k); u[n][3].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- lattices */
+
+static const int E15[15][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1},
+    {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+
+static const int E19[19][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+typedef struct {
+    int q;
+    int e[19][3];
+    double w[19];
+    int opp[19];
+} lattice_t;
+
+static int get_lattice(int q, lattice_t *L) {
+    if (q != 15 && q != 19) return -1;
+    L->q = q;
+    for (int i = 0; i < q; ++i) {
+        for (int a = 0; a < 3; ++a) L->e[i][a] = (q == 15) ? E15[i][a] : E19[i][a];
+        int len2 = L->e[i][0] * L->e[i][0] + L->e[i][1] * L->e[i][1] + L->e[i][2] * L->e[i][2];
+        if (q == 15) L->w[i] = len2 == 0 ? 2.0 / 9.0 : (len2 == 1 ? 1.0 / 9.0 : 1.0 / 72.0);
+        else         L->w[i] = len2 == 0 ? 1.0 / 3.0 : (len2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        L->opp[i] = (i == 0) ? 0 : ((i & 1) ? i + 1 : i - 1);
+    }
+    return 0;
+}
+
+/* Export of the velocity set, so that tests can check it against the
+ * isotropy conditions that define it. */
+int orc_lattice(int q, int32_t *e, double *w, int32_t *opp) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+    for (int i = 0; i < q; ++i) {
+        for (int a = 0; a < 3; ++a) e[3 * i + a] = L.e[i][a];
+        w[i] = L.w[i];
+        opp[i] = L.opp[i];
+    }
+    return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int nt) {
+#ifdef _OPENMP
+    if (nt > 0) omp_set_num_threads(nt);
+#else
+    (void)nt;
+#endif
+}
+
+/* ------------------------------------------------------------- equilibrium */
+
+static void equilibrium(const lattice_t *L, double rho, const double u[3], double *feq) {
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < L->q; ++i) {
+        double cu = L->e[i][0] * u[0] + L->e[i][1] * u[1] + L->e[i][2] * u[2];
+        feq[i] = L->w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+int orc_equilibrium(int q, double rho, const double *u, double *feq) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+    equilibrium(&L, rho, u, feq);
+    return 0;
+}
+
+/* density and velocity moments of one site's populations */
+static void moments(const lattice_t *L, const double *g, double *rho, double u[3]) {
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < L->q; ++i) {
+        r += g[i];
+        for (int a = 0; a < 3; ++a) j[a] += L->e[i][a] * g[i];
+    }
+    *rho = r;
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
+}
+
+/* prescribed iolet density at the start of step t */
+static double iolet_rho(int k, int64_t t, const double *mean, const double *amp,
+                        const double *period, const double *phase) {
+    double r = mean[k];
+    if (period[k] != 0.0 && amp[k] != 0.0)
+        r += amp[k] * sin(2.0 * M_PI * (double)t / period[k] + phase[k]);
+    return r;
+}
+
+/* ---------------------------------------------------------------- links */
+
+#define KB 21
+#define KOFF (1LL << 20)
+
+static int64_t vkey(int64_t x, int64_t y, int64_t z) {
+    return ((z + KOFF) << (2 * KB)) | ((y + KOFF) << KB) | (x + KOFF);
+}
+
+typedef struct {
+    int64_t key;
+    int64_t val;
+} kv_t;
+
+static int kv_cmp(const void *a, const void *b) {
+    int64_t ka = ((const kv_t *)a)->key, kb = ((const kv_t *)b)->key;
+    return (ka > kb) - (ka < kb);
+}
+
+/* binary search of a sorted key array; -1 if absent */
+static int64_t kv_find(const kv_t *t, int64_t n, int64_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (t[mid].key < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && t[lo].key == key) ? t[lo].val : -1;
+}
+
+/*
+ * Neighbour-link table (Section 2: each fluid site propagates to the
+ * neighbouring site along every lattice vector).  For site x and direction i
+ * the target voxel is y = x + c_i (wrapped per axis where periodic[a] > 0).
+ * nbr[i][x] = index of y if y is a fluid site, else -1.
+ * link[i][x] = 0 if y is fluid; 2 + k if y is an iolet-k voxel; else 1 (wall).
+ * Returns 0, or -1 on a bad lattice, -2 on duplicate fluid voxels, -3 on an
+ * iolet id outside [0, 253], -4 on a coordinate outside the key range.
+ */
+int orc_links_build(int q, int64_t n, const int32_t *xyz, int64_t n_io,
+                    const int32_t *io_xyz, const int32_t *io_id,
+                    const int32_t *periodic, int32_t *nbr, uint8_t *link) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+    for (int64_t m = 0; m < n_io; ++m)
+        if (io_id[m] < 0 || io_id[m] > 253) return -3;
+    for (int64_t x = 0; x < n; ++x)
+        for (int a = 0; a < 3; ++a)
+            if (xyz[3 * x + a] < -(1 << 19) || xyz[3 * x + a] >= (1 << 19)) return -4;
+    kv_t *fl = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+    kv_t *io = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n_io > 0 ? n_io : 1));
+    if (!fl || !io) { free(fl); free(io); return -5; }
+    for (int64_t x = 0; x < n; ++x) {
+        fl[x].key = vkey(xyz[3 * x], xyz[3 * x + 1], xyz[3 * x + 2]);
+        fl[x].val = x;
+    }
+    for (int64_t m = 0; m < n_io; ++m) {
+        io[m].key = vkey(io_xyz[3 * m], io_xyz[3 * m + 1], io_xyz[3 * m + 2]);
+        io[m].val = io_id[m];
+    }
+    qsort(fl, (size_t)n, sizeof(kv_t), kv_cmp);
+    qsort(io, (size_t)n_io, sizeof(kv_t), kv_cmp);
+    for (int64_t x = 1; x < n; ++x)
+        if (fl[x].key == fl[x - 1].key) { free(fl); free(io); return -2; }
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < n; ++x) {
+        for (int i = 0; i < q; ++i) {
+            int64_t y[3];
+            for (int a = 0; a < 3; ++a) {
+                y[a] = (int64_t)xyz[3 * x + a] + L.e[i][a];
+                if (periodic && periodic[a] > 0) y[a] = ((y[a] % periodic[a]) + periodic[a]) % periodic[a];
+            }
+            int64_t key = vkey(y[0], y[1], y[2]);
+            int64_t j = kv_find(fl, n, key);
+            if (j >= 0) {
+                nbr[(int64_t)i * n + x] = (int32_t)j;
+                link[(int64_t)i * n + x] = 0;
+            } else {
+                int64_t k = kv_find(io, n_io, key);
+                nbr[(int64_t)i * n + x] = -1;
+                link[(int64_t)i * n + x] = (uint8_t)(k >= 0 ? 2 + k : 1);
+            }
+        }
+    }
+    free(fl);
+    free(io);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ step */
+
+/*
+ * One time step t -> t+1 in push form (Section 2: collision, then
+ * propagation).  f and fout are [q][n]; every slot of fout is written
+ * exactly once for a consistent (symmetric) link table.
+ *   1. rho = sum_i f_i, u = sum_i c_i f_i / rho, feq_i(rho, u);
+ *   2. post-collision f*_i = f_i - (f_i - feq_i) / tau;
+ *   3. for each i: fluid link -> fout_i(nbr) = f*_i;
+ *                  wall link  -> fout_opp(i)(x) = f*_i   (halfway bounce-back);
+ *                  iolet k    -> fout_opp(i)(x) = feq_opp(i)(rho_k(t), u).
+ */
+int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+             int n_io, const double *rho_mean, const double *amp,
+             const double *period, const double *phase, int64_t t,
+             const double *f, double *fout) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < n; ++x) {
+        double g[19], feq[19], rho, u[3];
+        for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
+        moments(&L, g, &rho, u);
+        equilibrium(&L, rho, u, feq);
+        for (int i = 0; i < q; ++i) {
+            double fs = g[i] - (g[i] - feq[i]) / tau;
+            int lk = link[(int64_t)i * n + x];
+            if (lk == 0) {
+                fout[(int64_t)i * n + nbr[(int64_t)i * n + x]] = fs;
+            } else if (lk == 1) {
+                fout[(int64_t)L.opp[i] * n + x] = fs;
+            } else {
+                int k = lk - 2;
+                double feq_k[19];
+                double rk = iolet_rho(k, t, rho_mean, amp, period, phase);
+                equilibrium(&L, rk, u, feq_k);
+                fout[(int64_t)L.opp[i] * n + x] = feq_k[L.opp[i]];
+            }
+        }
+    }
+    (void)n_io;
+    return 0;
+}
+
+/* nsteps steps from time t0; f holds the state on entry and on exit;
+ * work is scratch of the same size. */
+int orc_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+            int n_io, const double *rho_mean, const double *amp, const double *period,
+            const double *phase, int64_t t0, int64_t nsteps, double *f, double *work) {
+    double *a = f, *b = work;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int r = orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t0 + s, a, b);
+        if (r) return r;
+        double *tmp = a; a = b; b = tmp;
+    }
+    if (a != f) memcpy(f, a, sizeof(double) * (size_t)q * (size_t)n);
+    return 0;
+}
+
+/* --------------------------------------------------------------- macros */
+
+/*
+ * Density, velocity and wall shear stress of the state f (pre-collision
+ * populations at time t).  u is [n][3].  Sites without wall links, or whose
+ * wall-link vectors sum to zero, get wss = 0.
+ */
+int orc_macros(int q, int64_t n, const uint8_t *link, double tau, const double *f,
+               double *rho_out, double *u_out, double *wss_out) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < n; ++x) {
+        double g[19], feq[19], rho, u[3];
+        for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
+        moments(&L, g, &rho, u);
+        if (rho_out) rho_out[x] = rho;
+        if (u_out) for (int a = 0; a < 3; ++a) u_out[3 * x + a] = u[a];
+        if (!wss_out) continue;
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < q; ++i)
+            if (link[(int64_t)i * n + x] == 1)
+                for (int a = 0; a < 3; ++a) s[a] += L.e[i][a];
+        double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+        if (sn == 0.0) { wss_out[x] = 0.0; continue; }
+        double nv[3] = {-s[0] / sn, -s[1] / sn, -s[2] / sn};
+        equilibrium(&L, rho, u, feq);
+        double pi[3][3] = {{0}};
+        for (int i = 0; i < q; ++i) {
+            double d = g[i] - feq[i];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) pi[a][b] += d * L.e[i][a] * L.e[i][b];
+        }
+        double coef = -(1.0 - 1.0 / (2.0 * tau));
+        double tr[3];
+        for (int a = 0; a < 3; ++a) {
+            tr[a] = 0.0;
+            for (int b = 0; b < 3; ++b) tr[a] += coef * pi[a][b] * nv[b];
+        }
+        double tn = tr[0] * nv[0] + tr[1] * nv[1] + tr[2] * nv[2];
+        double w2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double c = tr[a] - tn * nv[a];
+            w2 += c * c;
+        }
+        wss_out[x] = sqrt(w2);
+    }
+    return 0;
+}
+
+/* total mass sum_x sum_i f_i(x), summed in site order */
+double orc_mass(int q, int64_t n, const double *f) {
+    double m = 0.0;
+    for (int64_t x = 0; x < n; ++x)
+        for (int i = 0; i < q; ++i) m += f[(int64_t)i * n + x];
+    return m;
+}

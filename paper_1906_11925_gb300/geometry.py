@@ -1,0 +1,455 @@
+"""Seeded synthetic vessel geometries: the inputs of the lattice-Boltzmann path.
+
+This module only decides *which voxels are fluid* and *which voxels outside the
+fluid are inlet/outlet ("iolet") voxels*, and draws seeded random numbers.  It
+holds none of the method's arithmetic (no lattice, no links, no collision): the
+CUDA library and the FP64 oracle each build their own neighbour tables from the
+site list produced here, so that both sides see identical inputs and nothing
+else.
+
+The paper evaluates on patient geometries (3D rotational angiography turned
+into STL files, Section 4, Table II: 296,814 and 132,910 fluid sites).  Those
+files are not available, so the shapes below stand in for them:
+
+* ``tube``            straight cylinder, radius 8, length 64 (Poiseuille case),
+* ``aneurysm``        quarter-arc tube of radius 20 with a fused sphere of radius
+                      40 (saccular aneurysm) in a 256^3 box,
+* ``vessel_tree``     seeded bifurcating tree, six generations, Murray's law,
+                      in a 1024^3 box,
+* ``periodic_box``, ``walled_box``, ``slab``, ``random_mask``: small closed or
+                      periodic domains for invariants and brute-force checks.
+
+Voxelisation rule (the same for every shape): a voxel with integer centre p is
+fluid iff its squared distance to the shape is <= r^2, compared in float64.
+Iolet voxels are non-fluid voxels just beyond an open end of the vessel, within
+the end disk; a lattice link from a fluid site into such a voxel is an iolet
+link, every other link into a non-fluid voxel is a wall link.
+
+Caller order of the sites is the lexicographic (z, y, x) order of the voxels.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "Geometry",
+    "tube",
+    "aneurysm",
+    "vessel_tree",
+    "periodic_box",
+    "walled_box",
+    "slab",
+    "random_mask",
+    "random_populations",
+]
+
+
+@dataclass
+class Geometry:
+    """A sparse fluid-site list plus its iolet voxels and iolet schedule.
+
+    xyz:       int32 [N, 3] fluid voxel coordinates (caller order).
+    io_xyz:    int32 [M, 3] non-fluid voxels that are iolet k = io_id[m].
+    io_id:     int32 [M].
+    periodic:  int32 [3], box extent per axis for periodic wrap, 0 = open.
+    rho_mean, amp, period, phase: float64 [K] density schedule of iolet k,
+               rho_k(t) = rho_mean + amp * sin(2 pi t / period + phase)
+               (period 0 = constant).
+    site_weight: optional float64 [N] objective weights (e.g. the aneurysm
+               sphere sites for a wall-shear-stress objective).
+    """
+
+    name: str
+    xyz: np.ndarray
+    io_xyz: np.ndarray
+    io_id: np.ndarray
+    periodic: np.ndarray
+    rho_mean: np.ndarray
+    amp: np.ndarray
+    period: np.ndarray
+    phase: np.ndarray
+    site_weight: Optional[np.ndarray] = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_iolets(self) -> int:
+        return int(self.rho_mean.shape[0])
+
+
+# --------------------------------------------------------------------------
+# voxel-set helpers
+# --------------------------------------------------------------------------
+
+_KEY_BITS = 21
+_KEY_OFF = 1 << 20  # coordinates may be slightly negative (iolet planes)
+
+
+def _keys(xyz: np.ndarray) -> np.ndarray:
+    """Lexicographic (z, y, x) integer key; monotone in caller order."""
+    v = xyz.astype(np.int64) + _KEY_OFF
+    return (v[:, 2] << (2 * _KEY_BITS)) | (v[:, 1] << _KEY_BITS) | v[:, 0]
+
+
+def _unkeys(k: np.ndarray) -> np.ndarray:
+    m = (1 << _KEY_BITS) - 1
+    out = np.empty((k.shape[0], 3), dtype=np.int64)
+    out[:, 0] = k & m
+    out[:, 1] = (k >> _KEY_BITS) & m
+    out[:, 2] = k >> (2 * _KEY_BITS)
+    return (out - _KEY_OFF).astype(np.int32)
+
+
+def _scan_box(lo: Sequence[int], hi: Sequence[int],
+              pred: Callable[[np.ndarray, np.ndarray, np.ndarray], np.ndarray],
+              chunk: int = 1 << 22) -> np.ndarray:
+    """Keys of all integer voxels p in [lo, hi) (per axis) with pred(x,y,z)."""
+    lo = [int(v) for v in lo]
+    hi = [int(v) for v in hi]
+    if any(h <= l for l, h in zip(lo, hi)):
+        return np.empty(0, dtype=np.int64)
+    nx, ny = hi[0] - lo[0], hi[1] - lo[1]
+    xs = np.arange(lo[0], hi[0], dtype=np.float64)
+    ys = np.arange(lo[1], hi[1], dtype=np.float64)
+    X2, Y2 = np.meshgrid(xs, ys, indexing="xy")  # [ny, nx]
+    X2 = X2.ravel()
+    Y2 = Y2.ravel()
+    slab_z = max(1, chunk // max(1, nx * ny))
+    out: List[np.ndarray] = []
+    for z0 in range(lo[2], hi[2], slab_z):
+        zs = np.arange(z0, min(hi[2], z0 + slab_z), dtype=np.float64)
+        X = np.tile(X2, zs.shape[0])
+        Y = np.tile(Y2, zs.shape[0])
+        Z = np.repeat(zs, X2.shape[0])
+        m = pred(X, Y, Z)
+        if m.any():
+            p = np.stack([X[m], Y[m], Z[m]], axis=1).astype(np.int32)
+            out.append(_keys(p))
+    if not out:
+        return np.empty(0, dtype=np.int64)
+    return np.concatenate(out)
+
+
+def _finish(name: str, fluid_keys: List[np.ndarray], io_sets: List[np.ndarray],
+            periodic=(0, 0, 0), rho_mean=(), amp=None, period=None, phase=None,
+            meta=None) -> Geometry:
+    fk = np.unique(np.concatenate(fluid_keys)) if fluid_keys else np.empty(0, np.int64)
+    # iolet voxels: drop those that are fluid; a voxel claimed by several
+    # iolets goes to the lowest id
+    if io_sets:
+        ik = np.concatenate([np.asarray(s, dtype=np.int64) for s in io_sets])
+        iid = np.concatenate([np.full(len(s), k, dtype=np.int32)
+                              for k, s in enumerate(io_sets)])
+    else:
+        ik = np.empty(0, np.int64)
+        iid = np.empty(0, np.int32)
+    if fk.shape[0] and ik.shape[0]:
+        pos = np.minimum(np.searchsorted(fk, ik), fk.shape[0] - 1)
+        keep = fk[pos] != ik
+        ik, iid = ik[keep], iid[keep]
+    order = np.lexsort((iid, ik))
+    ik, iid = ik[order], iid[order]
+    first = np.ones(ik.shape[0], dtype=bool)
+    first[1:] = ik[1:] != ik[:-1]
+    ik, iid = ik[first], iid[first]
+    order = np.lexsort((ik, iid))  # group by iolet id, then voxel order
+    io_keys = [ik[order]]
+    io_ids = [iid[order]]
+    K = len(rho_mean)
+    z = np.zeros(K, dtype=np.float64)
+    g = Geometry(
+        name=name,
+        xyz=_unkeys(fk),
+        io_xyz=_unkeys(np.concatenate(io_keys)) if io_keys else np.empty((0, 3), np.int32),
+        io_id=np.concatenate(io_ids) if io_ids else np.empty(0, np.int32),
+        periodic=np.asarray(periodic, dtype=np.int32),
+        rho_mean=np.asarray(rho_mean, dtype=np.float64),
+        amp=z.copy() if amp is None else np.asarray(amp, dtype=np.float64),
+        period=z.copy() if period is None else np.asarray(period, dtype=np.float64),
+        phase=z.copy() if phase is None else np.asarray(phase, dtype=np.float64),
+        meta=dict(meta or {}),
+    )
+    return g
+
+
+def _sites_where(g: Geometry, pred) -> np.ndarray:
+    p = g.xyz.astype(np.float64)
+    return pred(p[:, 0], p[:, 1], p[:, 2])
+
+
+# --------------------------------------------------------------------------
+# shapes
+# --------------------------------------------------------------------------
+
+def tube(radius: float = 8.0, length: int = 64, nx: int = 17, ny: int = 17,
+         rho_in: float = 1.001, rho_out: float = 0.999) -> Geometry:
+    """Straight cylinder along z, axis at the box centre, open at both ends.
+
+    Fluid iff (x-cx)^2 + (y-cy)^2 <= r^2 for z in [0, length).  Inlet voxels
+    are the disk at z = -1 (iolet 0), outlet voxels the disk at z = length
+    (iolet 1).  With r = 8 in a 17x17x64 box this gives 12,608 fluid sites.
+    """
+    cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
+    r2 = float(radius) ** 2
+
+    def disk(X, Y, Z):
+        return (X - cx) ** 2 + (Y - cy) ** 2 <= r2
+
+    fluid = _scan_box((0, 0, 0), (nx, ny, length), disk)
+    inlet = _scan_box((0, 0, -1), (nx, ny, 0), disk)
+    outlet = _scan_box((0, 0, length), (nx, ny, length + 1), disk)
+    return _finish("tube_r%g_L%d" % (radius, length), [fluid], [inlet, outlet],
+                   rho_mean=(rho_in, rho_out),
+                   meta=dict(radius=radius, length=length, box=(nx, ny, length)))
+
+
+def aneurysm(tube_r: float = 20.0, arc_R: float = 150.0, sphere_r: float = 40.0,
+             box: int = 256, arc_c=(40.0, 40.0, 128.0), rho_in: float = 1.0,
+             amp_in: float = 0.001, period_in: float = 4000.0,
+             rho_out: float = 1.0) -> Geometry:
+    """Saccular aneurysm: a tube bent along a quarter circle plus a fused sphere.
+
+    Centreline: arc of radius arc_R about arc_c in the plane z = arc_c[2],
+    angle 0..pi/2, continued by straight segments to the box faces y = 0 (at
+    angle 0) and x = 0 (at angle pi/2).  The sphere is centred at mid-arc on
+    radius arc_R + tube_r + sphere_r/2 from the arc centre, so that it overlaps
+    the outer tube wall by sphere_r/2.  Inlet (iolet 0): the end disk at
+    y = -1, pulsatile rho = rho_in + amp_in sin(2 pi t / period_in).
+    Outlet (iolet 1): the end disk at x = -1, constant rho_out.
+    Objective weights mark the sphere sites that are outside the tube.
+    """
+    ax, ay, az = arc_c
+    r2 = tube_r ** 2
+    s_dist = arc_R + tube_r + sphere_r / 2.0
+    sx = ax + s_dist * math.cos(math.pi / 4)
+    sy = ay + s_dist * math.sin(math.pi / 4)
+    sz = az
+    e0 = (ax + arc_R, ay)          # arc end at angle 0, straight part toward y=0
+    e1 = (ax, ay + arc_R)          # arc end at angle pi/2, straight part toward x=0
+
+    def tube_d2(X, Y, Z):
+        dx, dy = X - ax, Y - ay
+        rr = np.sqrt(dx * dx + dy * dy)
+        th = np.arctan2(dy, dx)
+        on_arc = (th >= 0.0) & (th <= math.pi / 2)
+        d_arc = np.where(on_arc, (rr - arc_R) ** 2 + (Z - az) ** 2, np.inf)
+        # straight segment 0: x = e0.x, y in [-inf, e0.y]
+        d_s0 = np.where(Y <= e0[1], (X - e0[0]) ** 2 + (Z - az) ** 2, np.inf)
+        d_s1 = np.where(X <= e1[0], (Y - e1[1]) ** 2 + (Z - az) ** 2, np.inf)
+        return np.minimum(d_arc, np.minimum(d_s0, d_s1))
+
+    def fluid_pred(X, Y, Z):
+        in_tube = tube_d2(X, Y, Z) <= r2
+        in_sph = (X - sx) ** 2 + (Y - sy) ** 2 + (Z - sz) ** 2 <= sphere_r ** 2
+        return in_tube | in_sph
+
+    fluid = _scan_box((0, 0, 0), (box, box, box), fluid_pred)
+    inlet = _scan_box((0, -1, 0), (box, 0, box),
+                      lambda X, Y, Z: (X - e0[0]) ** 2 + (Z - az) ** 2 <= r2)
+    outlet = _scan_box((-1, 0, 0), (0, box, box),
+                       lambda X, Y, Z: (Y - e1[1]) ** 2 + (Z - az) ** 2 <= r2)
+    g = _finish("aneurysm_r%g_R%g_s%g" % (tube_r, arc_R, sphere_r), [fluid],
+                [inlet, outlet], rho_mean=(rho_in, rho_out), amp=(amp_in, 0.0),
+                period=(period_in, 0.0), phase=(0.0, 0.0),
+                meta=dict(box=(box, box, box), sphere_c=(sx, sy, sz),
+                          sphere_r=sphere_r))
+    w = _sites_where(g, lambda X, Y, Z: (((X - sx) ** 2 + (Y - sy) ** 2 + (Z - sz) ** 2
+                                          <= sphere_r ** 2)
+                                         & (tube_d2(X, Y, Z) > r2)))
+    g.site_weight = w.astype(np.float64)
+    return g
+
+
+def _perp_basis(d: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    h = np.array([1.0, 0.0, 0.0]) if abs(d[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = h - np.dot(h, d) * d
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    return e1, e2
+
+
+def _tree_segments(seed: int, generations: int, root_r: float, length_factor: float,
+                   root_start, murray_exp: float = 3.0):
+    """Seeded binary tree: list of (start, dir, radius, length, gen, is_leaf)."""
+    rng = np.random.default_rng(seed)
+    segs = []
+    queue = [(np.asarray(root_start, dtype=np.float64), np.array([0.0, 0.0, 1.0]),
+              float(root_r), 0)]
+    while queue:
+        nxt = []
+        for start, d, r, gen in queue:
+            L = length_factor * r
+            leaf = gen == generations - 1
+            segs.append((start, d, r, L, gen, leaf))
+            if leaf:
+                continue
+            end = start + L * d
+            a = rng.uniform(0.7, 1.0)
+            th1 = math.radians(rng.uniform(25.0, 45.0))
+            th2 = math.radians(rng.uniform(25.0, 45.0))
+            phi = rng.uniform(0.0, 2.0 * math.pi)
+            r1 = r / (1.0 + a ** murray_exp) ** (1.0 / murray_exp)
+            r2 = a * r1
+            e1, e2 = _perp_basis(d)
+            m = math.cos(phi) * e1 + math.sin(phi) * e2
+            d1 = math.cos(th1) * d + math.sin(th1) * m
+            d2 = math.cos(th2) * d - math.sin(th2) * m
+            nxt.append((end, d1 / np.linalg.norm(d1), r1, gen + 1))
+            nxt.append((end, d2 / np.linalg.norm(d2), r2, gen + 1))
+        queue = nxt
+    return segs
+
+
+def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
+                length_factor: float = 5.5, box: int = 1024,
+                rho_in: float = 1.001, rho_out: float = 1.0) -> Geometry:
+    """Seeded random bifurcating vessel tree (binary, ``generations`` levels).
+
+    Root: radius root_r, starting at z = 0 along +z, its (x, y) chosen so that
+    the tree's bounding box is centred in x and y.  At each
+    bifurcation a ~ U(0.7, 1.0) sets the asymmetry; the children radii follow
+    Murray's law with exponent 3, r1 = r / (1 + a^3)^(1/3), r2 = a r1; branch
+    angles U(25, 45) degrees on either side of the parent axis in a plane of
+    random azimuth U(0, 2 pi).  Every branch has length length_factor * r.
+    Fluid = union of flat-ended cylinders plus a sphere of the parent radius
+    at every bifurcation point, clipped to the box.  Iolet 0 is the root's
+    start disk (inlet, rho_in); iolets 1..2^(g-1) are the leaf end disks
+    (outlets, rho_out), numbered in breadth-first order.  With the defaults
+    (length 5.5 r) the whole tree lies inside the 1024^3 box.
+    """
+    segs = _tree_segments(seed, generations, root_r, length_factor, (0.0, 0.0, 0.0))
+    lo = np.min([np.minimum(s[0], s[0] + s[3] * s[1]) - s[2] for s in segs], axis=0)
+    hi = np.max([np.maximum(s[0], s[0] + s[3] * s[1]) + s[2] for s in segs], axis=0)
+    shift = np.array([math.floor(box / 2.0 - (lo[0] + hi[0]) / 2.0),
+                      math.floor(box / 2.0 - (lo[1] + hi[1]) / 2.0), 0.0])
+    segs = [(s[0] + shift,) + tuple(s[1:]) for s in segs]
+    fluid_keys = []
+
+    def clip_lo_hi(lo, hi):
+        lo = np.maximum(np.floor(lo), 0).astype(int)
+        hi = np.minimum(np.ceil(hi) + 1, box).astype(int)
+        return lo, hi
+
+    for start, d, r, L, gen, leaf in segs:
+        end = start + L * d
+        lo, hi = clip_lo_hi(np.minimum(start, end) - r - 1, np.maximum(start, end) + r + 1)
+
+        def cyl(X, Y, Z, start=start, d=d, r=r, L=L):
+            px, py, pz = X - start[0], Y - start[1], Z - start[2]
+            s = px * d[0] + py * d[1] + pz * d[2]
+            qx, qy, qz = px - s * d[0], py - s * d[1], pz - s * d[2]
+            return (s >= 0.0) & (s <= L) & (qx * qx + qy * qy + qz * qz <= r * r)
+
+        fluid_keys.append(_scan_box(lo, hi, cyl))
+        if not leaf:
+            lo, hi = clip_lo_hi(end - r - 1, end + r + 1)
+
+            def sph(X, Y, Z, c=end, r=r):
+                return (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
+
+            fluid_keys.append(_scan_box(lo, hi, sph))
+
+    def end_disk(c, n, r):
+        lo = np.floor(c - r - 3).astype(int)
+        hi = np.ceil(c + r + 3).astype(int) + 1
+
+        def pred(X, Y, Z):
+            px, py, pz = X - c[0], Y - c[1], Z - c[2]
+            s = px * n[0] + py * n[1] + pz * n[2]
+            qx, qy, qz = px - s * n[0], py - s * n[1], pz - s * n[2]
+            return (s > 0.0) & (s <= 2.0) & (qx * qx + qy * qy + qz * qz <= r * r)
+
+        return _scan_box(lo, hi, pred)
+
+    io_sets = []
+    s0, d0, r0 = segs[0][0], segs[0][1], segs[0][2]
+    io_sets.append(end_disk(s0, -d0, r0))
+    leaves = [s for s in segs if s[5]]
+    for start, d, r, L, gen, leaf in leaves:
+        io_sets.append(end_disk(start + L * d, d, r))
+    K = len(io_sets)
+    rho_mean = [rho_in] + [rho_out] * (K - 1)
+    g = _finish("vessel_tree_s%d_g%d_r%g" % (seed, generations, root_r), fluid_keys,
+                io_sets, rho_mean=rho_mean,
+                meta=dict(box=(box, box, box), segments=len(segs), leaves=len(leaves)))
+    return g
+
+
+def periodic_box(nx: int, ny: int, nz: int) -> Geometry:
+    """Every voxel of an nx*ny*nz box is fluid and every axis wraps around."""
+    fluid = _scan_box((0, 0, 0), (nx, ny, nz), lambda X, Y, Z: np.ones_like(X, dtype=bool))
+    return _finish("periodic_%dx%dx%d" % (nx, ny, nz), [fluid], [],
+                   periodic=(nx, ny, nz), rho_mean=())
+
+
+def walled_box(nx: int, ny: int, nz: int) -> Geometry:
+    """A closed box: every link leaving it is a wall link, no iolets."""
+    fluid = _scan_box((0, 0, 0), (nx, ny, nz), lambda X, Y, Z: np.ones_like(X, dtype=bool))
+    return _finish("walled_%dx%dx%d" % (nx, ny, nz), [fluid], [], rho_mean=())
+
+
+def slab(nx: int, ny: int, h: int, rho_in: float = 1.001,
+         rho_out: float = 0.999) -> Geometry:
+    """Plane channel: fluid z in [0, h), periodic in y, walls at z = -1 and
+    z = h (halfway walls at z = -1/2 and h - 1/2), inlet plane x = -1
+    (iolet 0), outlet plane x = nx (iolet 1)."""
+    allp = lambda X, Y, Z: np.ones_like(X, dtype=bool)
+    fluid = _scan_box((0, 0, 0), (nx, ny, h), allp)
+    inlet = _scan_box((-1, 0, 0), (0, ny, h), allp)
+    outlet = _scan_box((nx, 0, 0), (nx + 1, ny, h), allp)
+    return _finish("slab_%dx%dx%d" % (nx, ny, h), [fluid], [inlet, outlet],
+                   periodic=(0, ny, 0), rho_mean=(rho_in, rho_out),
+                   meta=dict(h=h, nx=nx))
+
+
+def random_mask(shape=(6, 6, 6), p: float = 0.6, seed: int = 0, n_iolets: int = 2,
+                periodic: bool = False, p_io: float = 0.3) -> Geometry:
+    """A seeded random fluid mask in a small box (for brute-force checks).
+
+    Each voxel is fluid with probability p.  Non-fluid voxels inside the box
+    and on its one-voxel skin become iolet k (k uniform in [0, n_iolets)) with
+    probability p_io, otherwise they are walls.  With periodic=True the box
+    wraps around and only interior non-fluid voxels can be iolets.
+    """
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    m = rng.random((nz, ny, nx)) < p
+    zz, yy, xx = np.nonzero(m)
+    fluid = _keys(np.stack([xx, yy, zz], 1).astype(np.int32))
+    lo = (0, 0, 0) if periodic else (-1, -1, -1)
+    hi = (nx, ny, nz) if periodic else (nx + 1, ny + 1, nz + 1)
+    io_sets = [[] for _ in range(n_iolets)]
+    if n_iolets:
+        for z in range(lo[2], hi[2]):
+            for y in range(lo[1], hi[1]):
+                for x in range(lo[0], hi[0]):
+                    inside = 0 <= x < nx and 0 <= y < ny and 0 <= z < nz
+                    if inside and m[z, y, x]:
+                        continue
+                    if rng.random() < p_io:
+                        io_sets[int(rng.integers(0, n_iolets))].append((x, y, z))
+    io = [_keys(np.asarray(s, dtype=np.int32).reshape(-1, 3)) for s in io_sets]
+    rho_mean = 1.0 + 0.002 * (rng.random(n_iolets) - 0.5)
+    amp = 0.001 * rng.random(n_iolets)
+    period = rng.uniform(20.0, 60.0, n_iolets)
+    phase = rng.uniform(0.0, 2 * math.pi, n_iolets)
+    return _finish("random_%dx%dx%d_p%g_s%d" % (nx, ny, nz, p, seed), [fluid], io,
+                   periodic=shape if periodic else (0, 0, 0), rho_mean=rho_mean,
+                   amp=amp, period=period, phase=phase)
+
+
+def random_populations(q: int, n: int, seed: int, amplitude: float = 1e-3,
+                       rho0: float = 1.0) -> np.ndarray:
+    """Seeded float64 [q, n] populations: (1 + amplitude * U(-1, 1)) times a
+    per-direction base value rho0 / q.  These are raw random inputs, not an
+    equilibrium; both sides receive the same array."""
+    rng = np.random.default_rng(seed)
+    base = rho0 / q
+    return base * (1.0 + amplitude * (2.0 * rng.random((q, n)) - 1.0))

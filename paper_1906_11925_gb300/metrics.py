@@ -1,0 +1,26 @@
+"""Throughput and roofline arithmetic used by the benchmark.
+
+Site updates per second (SUPS) is the paper's metric (Section 4, Table III):
+the number of fluid sites times the number of time steps, divided by the
+wall time.  Bytes per site update are the algorithmic traffic of one pull
+step on the sparse site list (see ``bytes_per_site_update``).
+"""
+from __future__ import annotations
+
+
+def sups(n_sites: int, steps: int, seconds: float) -> float:
+    """Site updates per second: n_sites * steps / seconds."""
+    return float(n_sites) * float(steps) / float(seconds)
+
+
+def msups(n_sites: int, steps: int, seconds: float) -> float:
+    return sups(n_sites, steps, seconds) / 1e6
+
+
+def bytes_per_site_update(q: int, storage: str) -> int:
+    """Algorithmic HBM bytes of one fused pull collide-and-stream update:
+    q populations read and q written (4 B each in fp32, 2 B in fp16
+    deviation storage) plus q - 1 int32 neighbour entries (the rest
+    population needs none)."""
+    elem = {"fp32": 4, "fp16": 2}[storage]
+    return 2 * q * elem + 4 * (q - 1)

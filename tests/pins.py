@@ -1,0 +1,298 @@
+"""Checks that pin the FP64 oracle to facts outside itself.
+
+Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError when the
+oracle disagrees with a closed form, an invariant, a textbook special case or
+a brute-force computation.  The same functions run against the real oracle
+(they must pass) and against copies of it with a planted mistake (at least
+one of them must fail), see test_oracle_mutants.py.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from paper_1906_11925_gb300 import geometry as G
+
+TAU_EXACT_BB = 0.5 + math.sqrt(3.0 / 16.0)  # halfway bounce-back has zero slip here
+
+
+# ---------------------------------------------------------------- lattice
+
+def _rational_weights(vecs):
+    """Weights of a three-shell 3D velocity set, by speed shell, from the
+    isotropy conditions sum w = 1, sum w c_x^2 = 1/3 and
+    sum w c_x^2 c_y^2 = 1/9, solved exactly in rationals (for components in
+    {-1, 0, 1}, c_x^4 = c_x^2, so the mixed fourth moment is the independent
+    one)."""
+    shells = sorted({sum(v * v for v in c) for c in vecs})
+    rows = []
+    rhs = []
+
+    def add(fun, val):
+        rows.append([sum(Fraction(fun(c)) for c in vecs if sum(v * v for v in c) == s)
+                     for s in shells])
+        rhs.append(Fraction(val))
+
+    add(lambda c: 1, 1)
+    add(lambda c: c[0] ** 2, Fraction(1, 3))
+    add(lambda c: c[0] ** 2 * c[1] ** 2, Fraction(1, 9))
+    assert len(shells) == 3
+    # Gaussian elimination in rationals (square system)
+    n = len(shells)
+    A = [r[:] + [b] for r, b in zip(rows[:n], rhs[:n])]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                fac = A[r][col] / A[col][col]
+                A[r] = [a - fac * b for a, b in zip(A[r], A[col])]
+    return {s: A[i][n] / A[i][i] for i, s in enumerate(shells)}
+
+
+def pin_lattice(o, q):
+    e, w, opp = o.lattice(q)
+    shells = {15: {0, 1, 3}, 19: {0, 1, 2}}[q]
+    want = {c for c in itertools.product((-1, 0, 1), repeat=3)
+            if sum(v * v for v in c) in shells}
+    got = [tuple(int(v) for v in row) for row in e]
+    assert len(got) == q and set(got) == want, "velocity set"
+    assert got[0] == (0, 0, 0), "rest vector first"
+    for i in range(q):
+        assert tuple(-v for v in got[i]) == got[opp[i]], "opposite of %d" % i
+        if i > 0:
+            assert opp[i] == (i + 1 if i % 2 == 1 else i - 1), "pair ordering"
+    wr = _rational_weights(got)
+    for i, c in enumerate(got):
+        assert w[i] == float(wr[sum(v * v for v in c)]), "weight %d" % i
+    # isotropy up to fourth order, exactly in rationals
+    W = [wr[sum(v * v for v in c)] for c in got]
+    d = lambda a, b: 1 if a == b else 0
+    assert sum(W) == 1
+    for a in range(3):
+        assert sum(Wi * c[a] for Wi, c in zip(W, got)) == 0
+        for b in range(3):
+            assert sum(Wi * c[a] * c[b] for Wi, c in zip(W, got)) == Fraction(d(a, b), 3)
+            for g in range(3):
+                assert sum(Wi * c[a] * c[b] * c[g] for Wi, c in zip(W, got)) == 0
+                for h in range(3):
+                    m4 = sum(Wi * c[a] * c[b] * c[g] * c[h] for Wi, c in zip(W, got))
+                    assert m4 == Fraction(d(a, b) * d(g, h) + d(a, g) * d(b, h)
+                                          + d(a, h) * d(b, g), 9)
+
+
+def pin_equilibrium(o, q, seed=0):
+    """sum feq = rho, sum c feq = rho u, sum c c feq = rho/3 I + rho u u."""
+    e, _, _ = o.lattice(q)
+    e = e.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        rho = rng.uniform(0.8, 1.2)
+        u = rng.uniform(-0.1, 0.1, 3)
+        feq = o.equilibrium(q, rho, u)
+        assert abs(feq.sum() - rho) <= 1e-14 * rho
+        assert np.allclose(e.T @ feq, rho * u, rtol=0, atol=1e-15)
+        P = (e.T * feq) @ e
+        assert np.allclose(P, rho / 3.0 * np.eye(3) + rho * np.outer(u, u), rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- links
+
+def brute_links(e, xyz, io_xyz, io_id, periodic):
+    """O(N^2 Q) neighbour search written independently of both builders."""
+    q = e.shape[0]
+    n = xyz.shape[0]
+    nbr = np.full((q, n), -1, np.int32)
+    link = np.ones((q, n), np.uint8)
+    for x in range(n):
+        for i in range(q):
+            y = [int(xyz[x, a]) + int(e[i, a]) for a in range(3)]
+            for a in range(3):
+                if periodic[a] > 0:
+                    y[a] %= int(periodic[a])
+            hit = [j for j in range(n) if list(xyz[j]) == y]
+            assert len(hit) <= 1
+            if hit:
+                nbr[i, x] = hit[0]
+                link[i, x] = 0
+                continue
+            io = [int(io_id[m]) for m in range(io_xyz.shape[0]) if list(io_xyz[m]) == y]
+            if io:
+                link[i, x] = 2 + io[0]
+    return nbr, link
+
+
+def pin_links(o, q, seed, periodic):
+    g = G.random_mask((5, 4, 4), p=0.55, seed=seed, n_iolets=3, periodic=periodic)
+    e, _, opp = o.lattice(q)
+    nbr, link = o.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    bn, bl = brute_links(e, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    assert np.array_equal(nbr, bn), "nbr vs brute force"
+    assert np.array_equal(link, bl), "link vs brute force"
+    # symmetry of fluid links
+    for i in range(q):
+        m = nbr[i] >= 0
+        xs = np.nonzero(m)[0]
+        assert np.array_equal(nbr[opp[i], nbr[i, m]], xs), "link symmetry"
+
+
+# ---------------------------------------------------------------- invariants
+
+def _setup(o, q, g):
+    nbr, link = o.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    return nbr, link
+
+
+def pin_mass_periodic(o, q, steps=300):
+    """Closed periodic box: mass and momentum are conserved exactly (FP64)."""
+    g = G.periodic_box(5, 4, 3)
+    nbr, link = _setup(o, q, g)
+    e, _, _ = o.lattice(q)
+    f0 = G.random_populations(q, g.n, seed=3, amplitude=0.2)
+    f = o.run(q, nbr, link, 0.7, f0, steps)
+    m0, m1 = f0.sum(), f.sum()
+    assert abs(m1 - m0) <= 1e-13 * m0, "mass drift %g" % ((m1 - m0) / m0)
+    j0 = e.T.astype(np.float64) @ f0.sum(axis=1)
+    j1 = e.T.astype(np.float64) @ f.sum(axis=1)
+    assert np.all(np.abs(j1 - j0) <= 1e-13 * m0), "momentum drift"
+    # the state must have changed (a step that copies its input is no step)
+    assert np.abs(f - f0).max() > 1e-4
+
+
+def pin_mass_walled(o, q, steps=300):
+    """Closed box with halfway bounce-back on every side: mass is conserved
+    exactly (every population leaving through a wall comes back)."""
+    g = G.walled_box(5, 4, 6)
+    nbr, link = _setup(o, q, g)
+    f0 = G.random_populations(q, g.n, seed=4, amplitude=0.2)
+    f = o.run(q, nbr, link, 0.9, f0, steps)
+    m0, m1 = f0.sum(), f.sum()
+    assert abs(m1 - m0) <= 1e-13 * m0, "mass drift %g" % ((m1 - m0) / m0)
+    assert np.abs(f - f0).max() > 1e-4
+
+
+def pin_rest(o, q, steps=100):
+    """Fluid at rest between iolets of the rest density stays at rest."""
+    g = G.tube(radius=3, length=8, nx=7, ny=7, rho_in=1.0, rho_out=1.0)
+    nbr, link = _setup(o, q, g)
+    f0 = o.rest_state(q, g.n)
+    f = o.run(q, nbr, link, 0.8, f0, steps, geom=g)
+    assert np.abs(f - f0).max() <= 1e-15
+
+
+def pin_iolet_density(o, q):
+    """Between two iolets of density rho1 and no walls (periodic cross
+    section), fluid at rest relaxes to uniform density rho1 and rest."""
+    g = G.slab(6, 1, 1, rho_in=1.0003, rho_out=1.0003)
+    g.periodic[:] = (0, 1, 1)
+    nbr, link = _setup(o, q, g)
+    assert (link == 1).sum() == 0
+    f = o.run(q, nbr, link, 0.8, o.rest_state(q, g.n), 2000, geom=g)
+    rho, u, _ = o.macros(q, link, 0.8, f)
+    assert np.abs(rho - 1.0003).max() < 1e-12 and np.abs(u).max() < 1e-12
+
+
+def pin_iolet_time(o, q):
+    """A single site between two pulsatile iolets: after the step t -> t+1
+    each population arriving from iolet k equals the (pinned) equilibrium at
+    the iolet density evaluated at the step's start time t and the site's
+    velocity before the step."""
+    g = G.slab(1, 1, 1)
+    g.periodic[:] = (0, 1, 1)
+    nbr, link = _setup(o, q, g)
+    e, _, opp = o.lattice(q)
+    io = dict(rho_mean=np.array([1.0, 1.0]), amp=np.array([0.01, 0.02]),
+              period=np.array([7.0, 11.0]), phase=np.array([0.3, 1.1]))
+    f = G.random_populations(q, 1, seed=9, amplitude=0.3)
+    for t in (0, 5, 13):
+        rho, u, _ = o.macros(q, link, 0.8, f)
+        fn = o.step(q, nbr, link, 0.8, f, t=t, **io)
+        for k in (0, 1):
+            rk = io["rho_mean"][k] + io["amp"][k] * math.sin(
+                2 * math.pi * t / io["period"][k] + io["phase"][k])
+            feq = o.equilibrium(q, rk, u[0])
+            for i in range(q):
+                if link[i, 0] == 2 + k:
+                    assert abs(fn[opp[i], 0] - feq[opp[i]]) <= 1e-15, (t, k, i)
+        f = fn
+
+
+# ---------------------------------------------------------------- Poiseuille
+
+def pin_slab_poiseuille(o, q, steps=6000):
+    """Plane Poiseuille flow between halfway bounce-back walls at
+    tau = 1/2 + sqrt(3/16), where BGK with halfway bounce-back has no slip
+    (He, Zou, Luo & Dembo, J. Stat. Phys. 87, 1997): the profile across the
+    channel is the parabola u = G/(2 rho nu) (a^2 - s^2) with the walls
+    exactly half-way between sites, nu = (tau - 1/2)/3, G = c_s^2 |d rho/dx|,
+    and the wall shear stress at the wall-adjacent sites is G (h/2 - 1/2)."""
+    h = 12
+    tau = TAU_EXACT_BB
+    g = G.slab(64, 2, h)
+    nbr, link = _setup(o, q, g)
+    f = o.run(q, nbr, link, tau, o.rest_state(q, g.n), steps, geom=g)
+    rho, u, wss = o.macros(q, link, tau, f)
+    x, y, z = g.xyz.T
+    nu = (tau - 0.5) / 3.0
+    xs = np.arange(16, 48)
+    rx = np.array([rho[x == k].mean() for k in xs])
+    Gr = -np.polyfit(xs, rx, 1)[0] / 3.0
+    sel = (x == 32) & (y == 0)
+    c = np.polyfit(z[sel], u[sel, 0], 2)
+    roots = np.sort(np.roots(c).real)
+    assert abs(roots[0] + 0.5) < 1e-4 and abs(roots[1] - (h - 0.5)) < 1e-4, roots
+    curv = -Gr / (2.0 * nu * rho[sel].mean())
+    assert abs(c[0] / curv - 1.0) < 1e-4, (c[0], curv)
+    assert np.abs(u[:, 1]).max() == 0.0  # mirror symmetry of the periodic cross-section
+    assert np.abs(u[sel, 2]).max() < 1e-3 * np.abs(u[sel, 0]).max()
+    wsel = sel & ((z == 0) | (z == h - 1))
+    assert np.allclose(wss[wsel], Gr * (h / 2.0 - 0.5), rtol=1e-4, atol=0)
+    inner = sel & (z > 0) & (z < h - 1)
+    assert np.all(wss[inner] == 0.0)
+
+
+def pin_tube_poiseuille(o, steps=1000):
+    """Pressure-driven flow in the straight tube (r = 8, 17x17x64, D3Q15,
+    tau = 0.8, rho 1.001 -> 0.999): near the axis the mass-flux profile is the
+    Hagen-Poiseuille parabola with curvature -G/(4 nu) (within 4%, the
+    staircase wall perturbs it), the effective radius lies within half a
+    lattice unit of 8, and the mean pressure gradient is within 10% of the
+    nominal drop over the tube length."""
+    q, tau = 15, 0.8
+    g = G.tube()
+    nbr, link = _setup(o, q, g)
+    f = o.run(q, nbr, link, tau, o.rest_state(q, g.n), steps, geom=g)
+    rho, u, _ = o.macros(q, link, tau, f)
+    x, y, z = g.xyz.T
+    r2 = (x - 8.0) ** 2 + (y - 8.0) ** 2
+    nu = (tau - 0.5) / 3.0
+    zs = np.arange(16, 48)
+    rz = np.array([rho[z == k].mean() for k in zs])
+    Gf = -np.polyfit(zs, rz, 1)[0] / 3.0
+    nominal = (1.001 - 0.999) / 3.0 / 65.0
+    assert abs(Gf / nominal - 1.0) < 0.1, (Gf, nominal)
+    sel = (z >= 16) & (z < 48) & (r2 <= 16)
+    c = np.polyfit(r2[sel], u[sel, 2] * rho[sel], 1)
+    assert abs(c[0] / (-Gf / (4.0 * nu)) - 1.0) < 0.04, c
+    reff = math.sqrt(-c[1] / c[0])
+    assert 7.5 <= reff <= 8.5, reff
+    assert u[:, 2].min() > -1e-5
+
+
+ALL_FAST = [
+    ("lattice15", lambda o: pin_lattice(o, 15)),
+    ("lattice19", lambda o: pin_lattice(o, 19)),
+    ("equilibrium15", lambda o: pin_equilibrium(o, 15)),
+    ("equilibrium19", lambda o: pin_equilibrium(o, 19)),
+    ("links15", lambda o: pin_links(o, 15, 1, False)),
+    ("links19p", lambda o: pin_links(o, 19, 2, True)),
+    ("mass_periodic19", lambda o: pin_mass_periodic(o, 19)),
+    ("mass_walled15", lambda o: pin_mass_walled(o, 15, 200)),
+    ("rest19", lambda o: pin_rest(o, 19)),
+    ("iolet_density15", lambda o: pin_iolet_density(o, 15)),
+    ("iolet_time19", lambda o: pin_iolet_time(o, 19)),
+    ("slab19", lambda o: pin_slab_poiseuille(o, 19, 3000)),
+]

@@ -1,0 +1,40 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins
+catch every one of them (CPU only; the real oracle is never modified)."""
+import pytest
+
+import oracle
+import pins
+
+MUTANTS = {
+    "feq_quadratic_coeff": ("4.5 * cu * cu", "4.0 * cu * cu"),
+    "feq_uu_sign": ("- 1.5 * uu", "+ 1.5 * uu"),
+    "weight_d3q15_diag": ("1.0 / 72.0", "1.0 / 64.0"),
+    "d3q19_direction_order": ("{1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},",
+                              "{1, 0, -1}, {-1, 0, -1}, {1, 0, 1}, {-1, 0, 1},"),
+    "bounce_back_same_dir": ("fout[(int64_t)L.opp[i] * n + x] = fs;",
+                             "fout[(int64_t)i * n + x] = fs;"),
+    "relaxation_tau_times": ("(g[i] - feq[i]) / tau", "(g[i] - feq[i]) * tau"),
+    "collision_sign": ("g[i] - (g[i] - feq[i]) / tau", "g[i] + (g[i] - feq[i]) / tau"),
+    "iolet_time_plus_one": ("iolet_rho(k, t, rho_mean", "iolet_rho(k, t + 1, rho_mean"),
+    "iolet_wrong_direction": ("= feq_k[L.opp[i]];", "= feq_k[i];"),
+    "wss_factor": ("-(1.0 - 1.0 / (2.0 * tau))", "-(1.0 - 1.0 / tau)"),
+    "velocity_not_divided": ("u[a] = j[a] / r;", "u[a] = j[a];"),
+    "no_periodic_wrap": ("if (periodic && periodic[a] > 0) y[a] =", "if (0) y[a] ="),
+    "iolet_id_off_by_one": ("(k >= 0 ? 2 + k : 1)", "(k >= 0 ? 1 + k : 1)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, "mutation anchor must be unique: %r" % old
+    o = oracle.variant(src.replace(old, new), str(tmp_path))
+    caught = []
+    for pin_name, fn in pins.ALL_FAST:
+        try:
+            fn(o)
+        except (AssertionError, ValueError, FloatingPointError) as exc:
+            caught.append(pin_name)
+            break
+    assert caught, "no pin caught the planted mistake %s" % name
