@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark: million site updates per second (MSUPS) of the fused sparse
+LBGK collide-and-stream on one GB300, with its HBM roofline fraction.
+
+Workload (default): the seeded six-generation bifurcating vessel tree
+(root radius 48, Murray's law, 1024^3 box, ~10.8M fluid sites), D3Q19 LBGK,
+tau = 0.6, one inlet at rho 1.001 and 32 outlets at rho 1.0, synthetic data.
+One benchmark step = 100 lattice-Boltzmann time steps (one fused kernel
+launch each) + density/velocity/wall-shear-stress fields + the float64 mass
+reduction.  value = fluid sites x LB time steps / device time, fp32 storage;
+the fp16-deviation storage form is reported beside it.  The inputs (~2.4 GB
+touched per LB step) are larger than the 126 MB L2, so no flush is needed.
+
+``--impl reference`` times the FP64 CPU oracle on this machine's host cores
+on the same workload and metric (a few LB steps per benchmark step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1906_11925_gb300 import geometry as G  # noqa: E402
+from paper_1906_11925_gb300 import metrics  # noqa: E402
+
+LB_STEPS_PER_BENCH_STEP = 100
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_kernels.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "vessel_tree": dict(q=19, tau=0.6, desc="seeded 6-generation bifurcating vessel tree, "
+                        "root r=48, Murray exponent 3, asymmetry U(0.7,1), angles U(25,45) deg, "
+                        "branch length 5.5 r, 1024^3 box, 1 inlet rho=1.001 + 32 outlets rho=1.0"),
+    "aneurysm": dict(q=15, tau=0.55, desc="quarter-arc tube r=20 on R=150 with fused sphere "
+                     "r=40, 256^3 box, pulsatile inlet 1+0.001 sin(2 pi t/4000), outlet 1.0"),
+    "tube": dict(q=15, tau=0.8, desc="straight tube r=8, 17x17x64, rho 1.001 -> 0.999"),
+}
+
+
+def make_geometry(name: str):
+    cache = os.path.join(tempfile.gettempdir(), "hemelb_gb300_geom_%s.npz" % name)
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return G.Geometry(name=str(z["name"]), xyz=z["xyz"], io_xyz=z["io_xyz"], io_id=z["io_id"],
+                          periodic=z["periodic"], rho_mean=z["rho_mean"], amp=z["amp"],
+                          period=z["period"], phase=z["phase"])
+    g = {"vessel_tree": G.vessel_tree, "aneurysm": G.aneurysm, "tube": G.tube}[name]()
+    try:
+        np.savez(cache + ".tmp.npz", name=g.name, xyz=g.xyz, io_xyz=g.io_xyz, io_id=g.io_id,
+                 periodic=g.periodic, rho_mean=g.rho_mean, amp=g.amp, period=g.period,
+                 phase=g.phase)
+        os.replace(cache + ".tmp.npz", cache)
+    except OSError:
+        pass
+    return g
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when it is missing or was taken on a different kernel source."""
+    try:
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        fields = {}
+        for line in open(PROFILE_SUMMARY):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_source_sha256") != src:
+            return None
+        return {k: float(fields[k]) for k in ("traffic_bytes_per_launch_fp32",
+                                               "traffic_bytes_per_launch_fp16") if k in fields}
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1906_11925_gb300 import lbm
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl")
+    W = WORKLOADS[args.workload]
+    q, tau = W["q"], W["tau"]
+    g = make_geometry(args.workload)
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    stream = torch.cuda.Stream()
+    inner = args.inner
+    legs = set(args.legs.split(","))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def device_leg(storage, sampler=None):
+        L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+        rho = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        u = torch.empty(g.n, 3, dtype=torch.float32, device="cuda")
+        wss = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        mass_dev = []
+
+        def bench_step(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            L.step(inner)
+            if ev is not None:
+                ev[1].record(stream)
+            L.macros(rho, u, wss)
+            mass_dev.append(L.mass())
+
+        for _ in range(args.warmup):
+            bench_step()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        if sampler:
+            sampler.start()
+        t0.record(stream)
+        for k in range(args.steps):
+            bench_step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        total_ms = max_over_ranks(t0.elapsed_time(t1))
+        step_kernel_ms = sum(a.elapsed_time(b) for a, b in evs)
+        finite = all(math.isfinite(m) for m in mass_dev)
+        L.close()
+        return dict(total_ms=total_ms, step_kernel_ms=step_kernel_ms, clocks=clocks, finite=finite,
+                    mass_last=mass_dev[-1] if mass_dev else None)
+
+    def e2e_leg():
+        # the user's call path with host buffers: per benchmark step, the inlet
+        # and outlet densities of its LB steps go host -> device from pinned
+        # memory, and the resulting total mass comes back device -> host.
+        L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP32, rho_mean=g.rho_mean,
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+        K = g.n_iolets
+        rows = []
+        for s in range(args.warmup + args.steps):
+            t = np.arange(s * inner, (s + 1) * inner, dtype=np.float64)[:, None]
+            r = g.rho_mean[None, :] + np.where(g.period > 0, g.amp, 0.0)[None, :] * np.sin(
+                2 * np.pi * t / np.where(g.period > 0, g.period, 1.0)[None, :] + g.phase[None, :])
+            rows.append(torch.from_numpy(np.ascontiguousarray(r)).pin_memory())
+        for s in range(args.warmup):
+            L.step_driven(rows[s], mass=False)
+            L.mass()
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.warmup, args.warmup + args.steps):
+            L.step_driven(rows[s], mass=False)
+            L.mass()
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        L.close()
+        return dict(seconds=dt, h2d=inner * K * 8, d2h=8)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    r32 = device_leg(lbm.STORE_FP32, sampler)
+    r16 = device_leg(lbm.STORE_FP16) if "fp16" in legs else None
+    e2e = e2e_leg() if "e2e" in legs else None
+
+    n_lb = args.steps * inner
+    value = world * metrics.msups(g.n, n_lb, r32["total_ms"] / 1e3)
+    peak, peak_kind = read_peaks()
+
+    def roofline(res, storage):
+        bps = metrics.bytes_per_site_update(q, storage)
+        per_launch_s = res["step_kernel_ms"] / 1e3 / n_lb
+        achieved = bps * g.n / per_launch_s / 1e9
+        return dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
+                    frac=round(achieved / peak, 4), peak_source=peak_kind,
+                    bytes_per_site_update=bps, launch_us=round(per_launch_s * 1e6, 2))
+
+    traffic = recorded_traffic()
+    rf32 = roofline(r32, "fp32")
+    rf32["traffic"] = traffic.get("traffic_bytes_per_launch_fp32") if traffic else None
+    if r16:
+        rf16 = roofline(r16, "fp16")
+        rf16["traffic"] = traffic.get("traffic_bytes_per_launch_fp16") if traffic else None
+
+    out = {
+        "metric": "MSUPS (million fluid-site updates per second), fused LBGK collide-and-stream",
+        "value": round(value, 2),
+        "unit": "MSUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(r32["total_ms"] / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded vessel geometry, fluid initialised at rest)",
+        "config": {"workload": args.workload, "description": W["desc"], "lattice": "D3Q%d" % q,
+                   "tau": tau, "fluid_sites": g.n, "iolets": g.n_iolets, "storage": "fp32",
+                   "lb_steps_per_bench_step": inner,
+                   "bench_step": "%d fused collide-stream launches + rho/u/WSS fields + fp64 mass"
+                                 % inner,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": rf32,
+        "fp16": None if not r16 else {
+            "value": round(world * metrics.msups(g.n, n_lb, r16["total_ms"] / 1e3), 2),
+            "unit": "MSUPS", "ms_per_step": round(r16["total_ms"] / args.steps, 4),
+            "roofline": rf16, "speedup_vs_fp32": round(r32["total_ms"] / r16["total_ms"], 3)},
+        "e2e": None if not e2e else {
+            "value": round(world * metrics.msups(g.n, n_lb, e2e["seconds"]), 2),
+            "unit": "MSUPS", "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+            "path": "lbm_step_driven (host iolet densities, pinned) + lbm_mass (host)"},
+        "gpu_launches": args.steps * (inner + 1 + 2),
+        "clocks": r32["clocks"],
+        "finite": r32["finite"] and (r16 is None or r16["finite"]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, g, nbr, link, q, tau,
+                                           budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(workload, g, nbr, link, q, tau, budget_s=15.0, lb_steps=None):
+    """The FP64 oracle as it stands, on this machine's host cores, on the same
+    geometry; about budget_s seconds of CPU work."""
+    import oracle
+    f = oracle.rest_state(q, g.n)
+    t0 = time.perf_counter()
+    f = oracle.step(q, nbr, link, tau, f, t=0, geom=g)
+    one = time.perf_counter() - t0
+    n = lb_steps or max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(q, nbr, link, tau, f, n, t0=1, geom=g)
+    dt = time.perf_counter() - t0
+    return {"value": round(metrics.msups(g.n, n, dt), 3), "unit": "MSUPS",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d LB steps of the full %s workload (%d sites), float64, push form"
+                      % (n, workload, g.n)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    W = WORKLOADS[args.workload]
+    q, tau = W["q"], W["tau"]
+    g = make_geometry(args.workload)
+    nbr, link = oracle.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    f = oracle.rest_state(q, g.n)
+    per_step = 1  # LB steps per benchmark step on the CPU (a bounded sample)
+    t = 0
+    for _ in range(args.warmup):
+        f = oracle.run(q, nbr, link, tau, f, per_step, t0=t, geom=g)
+        t += per_step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(q, nbr, link, tau, f, per_step, t0=t, geom=g)
+        t += per_step
+    dt = time.perf_counter() - t0
+    v = metrics.msups(g.n, args.steps * per_step, dt)
+    sample = "%d LB step(s) of the full %s workload (%d sites) per benchmark step, float64 oracle" % (
+        per_step, args.workload, g.n)
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "MSUPS (million fluid-site updates per second), fused LBGK collide-and-stream",
+        "value": round(v, 3), "unit": "MSUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded vessel geometry, fluid initialised at rest)",
+        "config": {"workload": args.workload, "description": W["desc"], "lattice": "D3Q%d" % q,
+                   "tau": tau, "fluid_sites": g.n, "iolets": g.n_iolets},
+        "cpu_baseline": {"value": round(v, 3), "unit": "MSUPS", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 3), "unit": "MSUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
+    ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
+                    help="LB time steps per benchmark step")
+    ap.add_argument("--legs", default="fp32,fp16,e2e",
+                    help="comma list of fp32 (always run), fp16, e2e")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

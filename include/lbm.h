@@ -1,0 +1,190 @@
+/*
+ * lbm.h -- C ABI of libhemelb_gb300.so: the sparse lattice-Boltzmann
+ * (LBGK) collide-and-stream hot path of HemeLB (arXiv 1906.11925) on one
+ * GB300 GPU (sm_103a).
+ *
+ * The paper's statement of the problem (Section 2): the vessel is a lattice
+ * of sparse fluid sites; each site holds a single-particle distribution over
+ * a finite set of lattice vectors (D3Q19, Fig. 1); a time step is a collision
+ * followed by propagation to the neighbouring site along each vector.
+ * Section 2 and Section 3.2 name the boundary families (walls and
+ * inlets/outlets, "iolets"); Section 4 states simple bounce-back walls.
+ * This library implements:
+ *   - LBGK collision, f*_i = f_i - (f_i - feq_i)/tau, with the compressible
+ *     second-order equilibrium feq_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2
+ *     - 3/2 u.u), on D3Q15 or D3Q19;
+ *   - halfway bounce-back at wall links;
+ *   - density (pressure) iolets: the population entering from iolet k is
+ *     feq(rho_k(t), u(x, t)), rho_k(t) = mean_k + amp_k sin(2 pi t/period_k
+ *     + phase_k) evaluated at the start of step t (period 0 = constant);
+ *   - wall shear stress from the non-equilibrium stress.
+ *
+ * Direction order (both lattices): 0 is the rest vector; after it opposite
+ * vectors are adjacent, opp(i) = i + 1 for odd i and i - 1 for even i > 0.
+ *   D3Q15: 1..6 = +x -x +y -y +z -z; 7..14 = (1,1,1) (-1,-1,-1) (1,1,-1)
+ *          (-1,-1,1) (1,-1,1) (-1,1,-1) (-1,1,1) (1,-1,-1).
+ *   D3Q19: 1..6 as D3Q15; 7..18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
+ *          (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1)
+ *          (0,-1,1).
+ *
+ * Conventions for every call:
+ *   - "caller order" is the order of the site list given to lbm_create; the
+ *     library reorders sites internally along a Morton (Z-order) curve and
+ *     converts back on every output.
+ *   - Canonical link tables are direction-major: nbr[i * n + x] is the
+ *     caller index of the site x + c_i, or -1 when that voxel is not fluid;
+ *     link[i * n + x] is 0 (fluid), 1 (wall) or 2 + k (iolet k).  For i = 0,
+ *     nbr = x and link = 0.
+ *   - Pointers named *_d are device pointers owned by the caller; the call
+ *     enqueues work on the context's stream and returns without waiting.
+ *     Every other pointer is host memory; calls that write host memory
+ *     synchronise the context's stream before returning.
+ *   - No call throws, aborts or traps.  Arguments are validated before any
+ *     allocation.  On error the context stays usable unless the status is
+ *     LBM_ERR_CUDA.  lbm_last_error() gives a message.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef HEMELB_GB300_LBM_H
+#define HEMELB_GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* bad argument (NULL, range, unsupported q/storage) */
+    LBM_ERR_TABLE = 2,    /* link table inconsistent (range, symmetry, flags)   */
+    LBM_ERR_NOMEM = 3,    /* not enough free device memory (checked up front)   */
+    LBM_ERR_CUDA = 4,     /* a CUDA call failed; the context must be destroyed  */
+    LBM_ERR_UNSTABLE = 5, /* non-finite state detected                          */
+    LBM_ERR_STATE = 6     /* call not valid in the context's current state      */
+} lbm_status;
+
+enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1 };
+enum { LBM_MAX_IOLETS = 64 };
+
+typedef struct lbm_ctx lbm_ctx; /* opaque */
+
+/* Parameters of a simulation (copied by lbm_create).
+ *   q          15 or 19.
+ *   storage    LBM_STORE_FP32: populations stored as float deviations
+ *              d_i = f_i - w_i rho0; LBM_STORE_FP16: stored as IEEE half
+ *              h_i = RN((f_i - w_i rho0) * 2^fp16_scale_log2).  Arithmetic is
+ *              float32 in both forms.
+ *   tau        relaxation time, tau > 0.5 (kinematic viscosity (tau - 1/2)/3).
+ *   rho0       reference density of the deviation storage and of the initial
+ *              rest state, > 0.
+ *   fp16_scale_log2  S in [0, 24]; ignored for LBM_STORE_FP32.
+ *   n_iolets   K in [0, LBM_MAX_IOLETS]; the four arrays hold K doubles each
+ *              (host memory, may be NULL when K = 0). */
+typedef struct {
+    int32_t q;
+    int32_t storage;
+    double tau;
+    double rho0;
+    int32_t fp16_scale_log2;
+    int32_t n_iolets;
+    const double *rho_mean;
+    const double *amp;
+    const double *period;
+    const double *phase;
+} lbm_params;
+
+/* Neighbour-link table of a sparse site list (Section 2: every fluid site
+ * propagates to its neighbour along each lattice vector), built on the host.
+ *   xyz       int32 [n][3] fluid voxel coordinates, all distinct, each in
+ *             [-2^19, 2^19).
+ *   io_xyz    int32 [n_io][3] non-fluid voxels that belong to iolet io_id[m]
+ *             (0 <= io_id < LBM_MAX_IOLETS); a link into such a voxel is an
+ *             iolet link, a link into any other non-fluid voxel is a wall.
+ *   periodic  int32 [3] or NULL: axis a wraps modulo periodic[a] when > 0.
+ *   nbr, link outputs, [q][n] each, caller-allocated (canonical tables).
+ * Errors: LBM_ERR_ARG for a bad q, NULL pointer with n > 0, duplicate
+ * coordinates, a coordinate or iolet id out of range.  No GPU is used. */
+lbm_status lbm_links_build(int32_t q, int64_t n, const int32_t *xyz, int64_t n_io,
+                           const int32_t *io_xyz, const int32_t *io_id,
+                           const int32_t *periodic, int32_t *nbr, uint8_t *link);
+
+/* Create a simulation on the current CUDA device from the canonical tables.
+ * Validates params and tables (range, symmetry nbr[opp i][nbr[i][x]] == x,
+ * fluid iff nbr >= 0, iolet ids < n_iolets), computes the Morton order of
+ * xyz (int32 [n][3]), uploads the internal tables and initialises the fluid
+ * at rest, f_i = w_i rho0, time t = 0.  All inputs are copied; the caller
+ * keeps ownership.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on which every later call enqueues its work.  n = 0 is allowed
+ * (every step is then a no-op).  On success *out receives the context. */
+lbm_status lbm_create(lbm_ctx **out, const lbm_params *params, int64_t n,
+                      const int32_t *xyz, const int32_t *nbr, const uint8_t *link,
+                      void *cuda_stream);
+
+/* Destroy a context and free its device memory (NULL is a no-op). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failed call on ctx, or of the last failed call
+ * without a context on this thread when ctx is NULL.  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Change the stream used by later calls. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Advance nsteps >= 0 time steps (Section 2: collision then propagation),
+ * one fused pull collide-and-stream kernel launch per step, asynchronous on
+ * the context's stream.  Step t uses the iolet densities rho_k(t). */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Advance nsteps steps with iolet densities supplied by the caller instead
+ * of the sinusoidal schedule (the paper drives its inlet from a file,
+ * Table I): rho_io_host is host memory, double [nsteps][n_iolets], row s
+ * used by step s.  If mass_host is not NULL it receives the total mass
+ * (see lbm_mass) after every step, double [nsteps].  Synchronous. */
+lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *rho_io_host,
+                           double *mass_host);
+
+/* Current time step counter t (number of steps taken since t = 0 or the
+ * last lbm_set_time). */
+lbm_status lbm_get_time(const lbm_ctx *ctx, int64_t *t);
+lbm_status lbm_set_time(lbm_ctx *ctx, int64_t t);
+
+/* Density, velocity and wall shear stress of the current state f(t), float32,
+ * in caller order: rho_d [n], u_d [n][3], wss_d [n] (device pointers; any may
+ * be NULL to skip it).  Wall shear stress: sigma = -(1 - 1/(2 tau))
+ * sum_i (f_i - feq_i) c_i c_i, traction s = sigma n with the unit wall normal
+ * n = -normalize(sum of c_i over the site's wall links), wss = |s - (n.s) n|;
+ * 0 at sites without wall links or whose wall vectors sum to zero.
+ * Asynchronous. */
+lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d);
+
+/* Total mass sum_x sum_i f_i(x, t), accumulated in float64 in a fixed order
+ * (deterministic for a given context).  Synchronous.  Returns
+ * LBM_ERR_UNSTABLE (and stores the value) when the sum is not finite. */
+lbm_status lbm_mass(lbm_ctx *ctx, double *out);
+
+/* Populations f(t) as float64 [q][n], caller order (host memory).  Sync. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
+
+/* Replace the state by f (float64 [q][n], caller order, host memory),
+ * rounded to the storage format.  Does not change t.  Synchronous. */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host);
+
+/* Raw stored state (checkpoint/resume): lbm_state_bytes gives the size of
+ * the stored population buffer; get/set copy it to/from host memory
+ * byte-for-byte, so that a resumed run is bit-identical.  Synchronous. */
+lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes);
+lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
+
+/* The link table the kernels use, converted back to canonical caller-order
+ * form (nbr, link: [q][n] host memory), for verification.  Synchronous. */
+lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link);
+
+/* Sizes: number of sites, padded plane length, and device bytes held. */
+lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_t *device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEMELB_GB300_LBM_H */

@@ -1,0 +1,602 @@
+// Host side of libhemelb_gb300: the C ABI declared in include/lbm.h.
+//
+// Set-up work (link building, validation, Morton reordering, folding of the
+// link flags into the kernel table) runs here on the host in C++ with OpenMP;
+// every per-step operation is a kernel launch on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lattice.h"
+#include "lbm_internal.h"
+
+#define HGB_API extern "C" __attribute__((visibility("default")))
+
+using namespace hemelb_gb300;
+
+struct lbm_ctx {
+    DevLattice L{};
+    int q = 0;
+    int storage = 0;
+    int scale_log2 = 0;
+    double tau = 0, rho0 = 1;
+    int n_iolets = 0;
+    int64_t n = 0, npad = 0;
+    int64_t t = 0;
+    cudaStream_t stream = nullptr;
+    void *f_cur = nullptr, *f_nxt = nullptr;
+    int32_t *tab = nullptr, *perm = nullptr;
+    double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
+    double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
+    double *partials = nullptr, *mass_dev = nullptr;
+    double *rho_io = nullptr;  // driven iolet densities, grown on demand
+    size_t rho_io_cap = 0;
+    double *mass_series = nullptr;
+    size_t mass_series_cap = 0;
+    size_t device_bytes = 0;
+    std::vector<int32_t> perm_host;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_ctx *ctx, lbm_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    g_err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                             \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+size_t elem_bytes(int storage) { return storage == LBM_STORE_FP16 ? 2 : 4; }
+
+// ------------------------------------------------------------------ links
+
+// Dense map of 8^3 voxel blocks over the bounding box of the site list; each
+// occupied block stores the 512 site indices of its voxels (-1 = none).
+class BlockMap {
+   public:
+    BlockMap(int64_t n, const int32_t *xyz) {
+        if (n == 0) return;
+        for (int a = 0; a < 3; ++a) {
+            lo_[a] = xyz[a];
+            hi_[a] = xyz[a];
+        }
+        for (int64_t x = 0; x < n; ++x)
+            for (int a = 0; a < 3; ++a) {
+                lo_[a] = std::min<int64_t>(lo_[a], xyz[3 * x + a]);
+                hi_[a] = std::max<int64_t>(hi_[a], xyz[3 * x + a]);
+            }
+        for (int a = 0; a < 3; ++a) nb_[a] = ((hi_[a] - lo_[a]) >> 3) + 1;
+        blocks_.assign((size_t)(nb_[0] * nb_[1] * nb_[2]), -1);
+        for (int64_t x = 0; x < n; ++x) {
+            int64_t b = block_of(xyz[3 * x], xyz[3 * x + 1], xyz[3 * x + 2]);
+            if (blocks_[b] < 0) {
+                blocks_[b] = (int64_t)(cells_.size() >> 9);
+                cells_.resize(cells_.size() + 512, -1);
+            }
+        }
+    }
+    // insert site x; returns false if the voxel is already taken
+    bool insert(int64_t x, const int32_t *p) {
+        int32_t &c = cell(p[0], p[1], p[2]);
+        if (c >= 0) return false;
+        c = (int32_t)x;
+        return true;
+    }
+    int32_t find(int64_t x, int64_t y, int64_t z) const {
+        if (x < lo_[0] || y < lo_[1] || z < lo_[2] || x > hi_[0] || y > hi_[1] || z > hi_[2])
+            return -1;
+        int64_t b = blocks_[block_of(x, y, z)];
+        if (b < 0) return -1;
+        return cells_[(size_t)(b << 9) + local(x, y, z)];
+    }
+
+   private:
+    int64_t block_of(int64_t x, int64_t y, int64_t z) const {
+        return (((z - lo_[2]) >> 3) * nb_[1] + ((y - lo_[1]) >> 3)) * nb_[0] + ((x - lo_[0]) >> 3);
+    }
+    int64_t local(int64_t x, int64_t y, int64_t z) const {
+        return (((z - lo_[2]) & 7) << 6) | (((y - lo_[1]) & 7) << 3) | ((x - lo_[0]) & 7);
+    }
+    int32_t &cell(int64_t x, int64_t y, int64_t z) {
+        return cells_[(size_t)(blocks_[block_of(x, y, z)] << 9) + local(x, y, z)];
+    }
+    int64_t lo_[3] = {0, 0, 0}, hi_[3] = {-1, -1, -1}, nb_[3] = {0, 0, 0};
+    std::vector<int64_t> blocks_;
+    std::vector<int32_t> cells_;
+};
+
+inline int64_t vkey(int64_t x, int64_t y, int64_t z) {
+    return ((z + (1LL << 20)) << 42) | ((y + (1LL << 20)) << 21) | (x + (1LL << 20));
+}
+
+// Morton (Z-order) key of a voxel, coordinates relative to the box minimum.
+inline uint64_t spread3(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+// Iolet densities of step t: rho_k(t) = mean + amp sin(2 pi t / period + phase),
+// in float64 on the host; the kernel receives rho_k and rho_k - rho0 as float.
+IoletStep iolet_step(const lbm_ctx *c, int64_t t) {
+    IoletStep s{};
+    for (int k = 0; k < c->n_iolets; ++k) {
+        double r = c->io_mean[k];
+        if (c->io_period[k] != 0.0 && c->io_amp[k] != 0.0)
+            r += c->io_amp[k] * std::sin(2.0 * M_PI * (double)t / c->io_period[k] + c->io_phase[k]);
+        s.drho[k] = (float)(r - c->rho0);
+        s.rho[k] = (float)r;
+    }
+    return s;
+}
+
+}  // namespace
+
+HGB_API const char *lbm_last_error(const lbm_ctx *ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_err.c_str();
+}
+
+HGB_API lbm_status lbm_links_build(int32_t q, int64_t n, const int32_t *xyz, int64_t n_io,
+                                   const int32_t *io_xyz, const int32_t *io_id,
+                                   const int32_t *periodic, int32_t *nbr, uint8_t *link) {
+    if (q != 15 && q != 19) return fail(nullptr, LBM_ERR_ARG, "q must be 15 or 19");
+    if (n < 0 || n_io < 0) return fail(nullptr, LBM_ERR_ARG, "negative size");
+    if (n >= (1LL << 31) - 1024) return fail(nullptr, LBM_ERR_ARG, "too many sites");
+    if (n > 0 && (!xyz || !nbr || !link)) return fail(nullptr, LBM_ERR_ARG, "NULL array");
+    if (n_io > 0 && (!io_xyz || !io_id)) return fail(nullptr, LBM_ERR_ARG, "NULL iolet array");
+    const int64_t lim = 1LL << 19;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (xyz[i] < -lim || xyz[i] >= lim) return fail(nullptr, LBM_ERR_ARG, "coordinate out of range");
+    for (int64_t m = 0; m < n_io; ++m) {
+        if (io_id[m] < 0 || io_id[m] >= LBM_MAX_IOLETS)
+            return fail(nullptr, LBM_ERR_ARG, "iolet id out of range");
+        for (int a = 0; a < 3; ++a)
+            if (io_xyz[3 * m + a] < -lim || io_xyz[3 * m + a] >= lim)
+                return fail(nullptr, LBM_ERR_ARG, "iolet coordinate out of range");
+    }
+    int32_t per[3] = {0, 0, 0};
+    if (periodic)
+        for (int a = 0; a < 3; ++a) {
+            if (periodic[a] < 0) return fail(nullptr, LBM_ERR_ARG, "negative period");
+            per[a] = periodic[a];
+        }
+    BlockMap map(n, xyz);
+    for (int64_t x = 0; x < n; ++x)
+        if (!map.insert(x, xyz + 3 * x)) return fail(nullptr, LBM_ERR_ARG, "duplicate fluid voxel");
+    std::unordered_map<int64_t, int32_t> io;
+    io.reserve((size_t)n_io * 2 + 1);
+    for (int64_t m = 0; m < n_io; ++m) {
+        int64_t k = vkey(io_xyz[3 * m], io_xyz[3 * m + 1], io_xyz[3 * m + 2]);
+        auto it = io.find(k);
+        if (it == io.end() || io_id[m] < it->second) io[k] = io_id[m];
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < n; ++x) {
+        for (int i = 0; i < q; ++i) {
+            int64_t p[3];
+            for (int a = 0; a < 3; ++a) {
+                p[a] = (int64_t)xyz[3 * x + a] + cdir_q(q, i, a);
+                if (per[a] > 0) p[a] = ((p[a] % per[a]) + per[a]) % per[a];
+            }
+            const int32_t j = map.find(p[0], p[1], p[2]);
+            const int64_t o = (int64_t)i * n + x;
+            if (j >= 0) {
+                nbr[o] = j;
+                link[o] = 0;
+            } else {
+                nbr[o] = -1;
+                auto it = io.find(vkey(p[0], p[1], p[2]));
+                link[o] = (uint8_t)(it == io.end() ? 1 : 2 + it->second);
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+namespace {
+
+lbm_status validate_params(const lbm_params *p) {
+    if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
+    if (p->q != 15 && p->q != 19) return fail(nullptr, LBM_ERR_ARG, "q must be 15 or 19");
+    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16)
+        return fail(nullptr, LBM_ERR_ARG, "storage must be LBM_STORE_FP32 or LBM_STORE_FP16");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+        return fail(nullptr, LBM_ERR_ARG, "tau must be finite and > 0.5");
+    if (!(p->rho0 > 0) || !std::isfinite(p->rho0))
+        return fail(nullptr, LBM_ERR_ARG, "rho0 must be finite and > 0");
+    if (p->storage == LBM_STORE_FP16 && (p->fp16_scale_log2 < 0 || p->fp16_scale_log2 > 24))
+        return fail(nullptr, LBM_ERR_ARG, "fp16_scale_log2 must be in [0, 24]");
+    if (p->n_iolets < 0 || p->n_iolets > LBM_MAX_IOLETS)
+        return fail(nullptr, LBM_ERR_ARG, "n_iolets out of range");
+    if (p->n_iolets > 0 && (!p->rho_mean || !p->amp || !p->period || !p->phase))
+        return fail(nullptr, LBM_ERR_ARG, "iolet arrays are NULL");
+    for (int k = 0; k < p->n_iolets; ++k) {
+        if (!std::isfinite(p->rho_mean[k]) || !(p->rho_mean[k] > 0) || !std::isfinite(p->amp[k]) ||
+            !std::isfinite(p->period[k]) || p->period[k] < 0 || !std::isfinite(p->phase[k]))
+            return fail(nullptr, LBM_ERR_ARG, "bad iolet schedule");
+    }
+    return LBM_OK;
+}
+
+lbm_status validate_tables(int q, int n_iolets, int64_t n, const int32_t *nbr, const uint8_t *link) {
+    int bad = 0;
+    int64_t bad_x = -1, bad_i = -1;
+#pragma omp parallel for schedule(static) reduction(max : bad)
+    for (int64_t x = 0; x < n; ++x) {
+        for (int i = 0; i < q; ++i) {
+            const int64_t o = (int64_t)i * n + x;
+            const int32_t nb = nbr[o];
+            const int lk = link[o];
+            int b = 0;
+            if (i == 0) {
+                b = (nb != x || lk != 0);
+            } else if (lk == 0) {
+                b = (nb < 0 || nb >= n) ? 1 : (nbr[(int64_t)opp(i) * n + nb] != x);
+            } else if (lk == 1) {
+                b = nb != -1;
+            } else {
+                b = (lk - 2 >= n_iolets) || nb != -1;
+            }
+            if (b) {
+                bad = 1;
+#pragma omp critical
+                {
+                    bad_x = x;
+                    bad_i = i;
+                }
+            }
+        }
+    }
+    if (bad) {
+        char msg[160];
+        snprintf(msg, sizeof msg,
+                 "inconsistent link table at site %lld direction %lld (range, symmetry or flag)",
+                 (long long)bad_x, (long long)bad_i);
+        return fail(nullptr, LBM_ERR_TABLE, msg);
+    }
+    return LBM_OK;
+}
+
+void free_ctx(lbm_ctx *c) {
+    if (!c) return;
+    cudaFree(c->f_cur);
+    cudaFree(c->f_nxt);
+    cudaFree(c->tab);
+    cudaFree(c->perm);
+    cudaFree(c->partials);
+    cudaFree(c->mass_dev);
+    cudaFree(c->rho_io);
+    cudaFree(c->mass_series);
+    delete c;
+}
+
+template <typename T>
+cudaError_t dmalloc(lbm_ctx *c, T **p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)p, bytes ? bytes : 16);
+    if (e == cudaSuccess) c->device_bytes += bytes;
+    return e;
+}
+
+}  // namespace
+
+HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, const int32_t *xyz,
+                              const int32_t *nbr, const uint8_t *link, void *cuda_stream) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    lbm_status st = validate_params(p);
+    if (st != LBM_OK) return st;
+    if (n < 0) return fail(nullptr, LBM_ERR_ARG, "negative n");
+    if (n >= (1LL << 31) - 1024) return fail(nullptr, LBM_ERR_ARG, "too many sites");
+    if (n > 0 && (!xyz || !nbr || !link)) return fail(nullptr, LBM_ERR_ARG, "NULL array");
+    const int q = p->q;
+    st = validate_tables(q, p->n_iolets, n, nbr, link);
+    if (st != LBM_OK) return st;
+    const int64_t lim = 1LL << 19;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (xyz[i] < -lim || xyz[i] >= lim) return fail(nullptr, LBM_ERR_ARG, "coordinate out of range");
+
+    const int64_t npad = std::max<int64_t>(128, (n + 127) / 128 * 128);
+    const size_t eb = elem_bytes(p->storage);
+    const size_t need = 2 * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
+                        (size_t)(mass_blocks() + 8) * 8;
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMemGetInfo");
+    if (need + (64u << 20) > free_b) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "need %zu bytes of device memory, %zu free", need, free_b);
+        return fail(nullptr, LBM_ERR_NOMEM, msg);
+    }
+
+    // Morton order of the sites
+    std::vector<int32_t> perm((size_t)n);
+    {
+        int64_t lo[3] = {0, 0, 0};
+        if (n > 0)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = xyz[a];
+                for (int64_t x = 0; x < n; ++x) lo[a] = std::min<int64_t>(lo[a], xyz[3 * x + a]);
+            }
+        std::vector<std::pair<uint64_t, int32_t>> keys((size_t)n);
+#pragma omp parallel for schedule(static)
+        for (int64_t x = 0; x < n; ++x) {
+            uint64_t k = spread3((uint64_t)(xyz[3 * x] - lo[0])) |
+                         (spread3((uint64_t)(xyz[3 * x + 1] - lo[1])) << 1) |
+                         (spread3((uint64_t)(xyz[3 * x + 2] - lo[2])) << 2);
+            keys[(size_t)x] = {k, (int32_t)x};
+        }
+        std::sort(keys.begin(), keys.end());
+        for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = keys[(size_t)i].second;
+    }
+    std::vector<int32_t> inv((size_t)n);
+    for (int64_t i = 0; i < n; ++i) inv[(size_t)perm[(size_t)i]] = (int32_t)i;
+
+    // kernel table: pull source of population i at internal site xi
+    std::vector<int32_t> tab((size_t)(q - 1) * npad, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t xi = 0; xi < n; ++xi) {
+        const int64_t x = perm[(size_t)xi];
+        for (int i = 1; i < q; ++i) {
+            const int j = opp(i);  // the link that population i arrives through
+            const int lk = link[(int64_t)j * n + x];
+            tab[(size_t)(i - 1) * npad + xi] = lk == 0 ? inv[(size_t)nbr[(int64_t)j * n + x]] : -lk;
+        }
+    }
+
+    lbm_ctx *c = new lbm_ctx();
+    c->q = q;
+    c->storage = p->storage;
+    c->scale_log2 = p->storage == LBM_STORE_FP16 ? p->fp16_scale_log2 : 0;
+    c->tau = p->tau;
+    c->rho0 = p->rho0;
+    c->n_iolets = p->n_iolets;
+    c->n = n;
+    c->npad = npad;
+    c->stream = (cudaStream_t)cuda_stream;
+    for (int k = 0; k < p->n_iolets; ++k) {
+        c->io_mean[k] = p->rho_mean[k];
+        c->io_amp[k] = p->amp[k];
+        c->io_period[k] = p->period[k];
+        c->io_phase[k] = p->phase[k];
+    }
+#define CKC(call)                                   \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) {                    \
+            lbm_status s_ = cuda_fail(nullptr, e_, #call); \
+            free_ctx(c);                            \
+            return s_;                              \
+        }                                           \
+    } while (0)
+    const size_t fbytes = (size_t)q * npad * eb;
+    CKC(dmalloc(c, &c->f_cur, fbytes));
+    CKC(dmalloc(c, &c->f_nxt, fbytes));
+    CKC(dmalloc(c, &c->tab, tab.size() * 4));
+    CKC(dmalloc(c, &c->perm, (size_t)n * 4));
+    CKC(dmalloc(c, &c->partials, (size_t)mass_blocks() * 8));
+    CKC(dmalloc(c, &c->mass_dev, 8));
+    CKC(cudaMemcpyAsync(c->tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (n) CKC(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    DevLattice &L = c->L;
+    L.q = q;
+    L.storage = p->storage;
+    L.n = (int)n;
+    L.npad = npad;
+    L.omega = (float)(1.0 / p->tau);
+    L.tau = (float)p->tau;
+    L.rho0 = (float)p->rho0;
+    L.scale = (float)std::ldexp(1.0, c->scale_log2);
+    L.inv_scale = (float)std::ldexp(1.0, -c->scale_log2);
+    L.n_iolets = p->n_iolets;
+    L.tab = c->tab;
+    L.perm = c->perm;
+    CKC(launch_zero(L, c->f_cur, c->stream));
+    CKC(launch_zero(L, c->f_nxt, c->stream));
+    CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
+#undef CKC
+    c->perm_host.swap(perm);
+    *out = c;
+    return LBM_OK;
+}
+
+HGB_API void lbm_destroy(lbm_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+HGB_API lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        CK(ctx, launch_step(ctx->L, ctx->f_cur, ctx->f_nxt, iolet_step(ctx, ctx->t), nullptr,
+                            ctx->stream));
+        std::swap(ctx->f_cur, ctx->f_nxt);
+        ++ctx->t;
+    }
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *rho_io_host,
+                                   double *mass_host) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    const int K = ctx->n_iolets;
+    if (K > 0 && !rho_io_host) return fail(ctx, LBM_ERR_ARG, "rho_io_host is NULL");
+    const size_t need = (size_t)nsteps * (size_t)std::max(K, 1) * 8;
+    if (need > ctx->rho_io_cap) {
+        cudaFree(ctx->rho_io);
+        ctx->rho_io = nullptr;
+        ctx->rho_io_cap = 0;
+        CK(ctx, cudaMalloc((void **)&ctx->rho_io, need));
+        ctx->rho_io_cap = need;
+    }
+    if (mass_host && (size_t)nsteps * 8 > ctx->mass_series_cap) {
+        cudaFree(ctx->mass_series);
+        ctx->mass_series = nullptr;
+        ctx->mass_series_cap = 0;
+        CK(ctx, cudaMalloc((void **)&ctx->mass_series, (size_t)nsteps * 8));
+        ctx->mass_series_cap = (size_t)nsteps * 8;
+    }
+    if (K > 0)
+        CK(ctx, cudaMemcpyAsync(ctx->rho_io, rho_io_host, (size_t)nsteps * K * 8,
+                                cudaMemcpyHostToDevice, ctx->stream));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        CK(ctx, launch_step(ctx->L, ctx->f_cur, ctx->f_nxt, IoletStep{}, ctx->rho_io + s * K,
+                            ctx->stream));
+        std::swap(ctx->f_cur, ctx->f_nxt);
+        ++ctx->t;
+        if (mass_host)
+            CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_series + s, ctx->stream));
+    }
+    if (mass_host)
+        CK(ctx, cudaMemcpyAsync(mass_host, ctx->mass_series, (size_t)nsteps * 8,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (mass_host)
+        for (int64_t s = 0; s < nsteps; ++s)
+            if (!std::isfinite(mass_host[s])) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite mass");
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_get_time(const lbm_ctx *ctx, int64_t *t) {
+    if (!ctx || !t) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    *t = ctx->t;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_time(lbm_ctx *ctx, int64_t t) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (t < 0) return fail(ctx, LBM_ERR_ARG, "t < 0");
+    ctx->t = t;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    CK(ctx, launch_macros(ctx->L, ctx->f_cur, rho_d, u_d, wss_d, ctx->stream));
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
+    if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_dev, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!std::isfinite(*out)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite mass");
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host) {
+    if (!ctx || (!f_host && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (ctx->n == 0) return LBM_OK;
+    const size_t bytes = (size_t)ctx->q * ctx->n * 8;
+    double *tmp = nullptr;
+    CK(ctx, cudaMalloc((void **)&tmp, bytes));
+    cudaError_t e = launch_gather_f64(ctx->L, ctx->f_cur, tmp, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_get_populations");
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
+    if (!ctx || (!f_host && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (ctx->n == 0) return LBM_OK;
+    const size_t bytes = (size_t)ctx->q * ctx->n * 8;
+    double *tmp = nullptr;
+    CK(ctx, cudaMalloc((void **)&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, f_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_scatter_f64(ctx->L, tmp, ctx->f_cur, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_populations");
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    *bytes = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage);
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes) {
+    if (!ctx || !host) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (bytes != (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage))
+        return fail(ctx, LBM_ERR_ARG, "wrong state size");
+    CK(ctx, cudaMemcpyAsync(host, ctx->f_cur, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
+    if (!ctx || !host) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (bytes != (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage))
+        return fail(ctx, LBM_ERR_ARG, "wrong state size");
+    CK(ctx, cudaMemcpyAsync(ctx->f_cur, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link) {
+    if (!ctx || ((!nbr || !link) && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const int q = ctx->q;
+    const int64_t n = ctx->n, npad = ctx->npad;
+    if (n == 0) return LBM_OK;
+    std::vector<int32_t> tab((size_t)(q - 1) * npad);
+    CK(ctx, cudaMemcpyAsync(tab.data(), ctx->tab, tab.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const std::vector<int32_t> &perm = ctx->perm_host;
+    for (int64_t xi = 0; xi < n; ++xi) {
+        const int64_t x = perm[(size_t)xi];
+        nbr[x] = (int32_t)x;
+        link[x] = 0;
+        for (int j = 1; j < q; ++j) {
+            const int32_t s = tab[(size_t)(opp(j) - 1) * npad + xi];
+            nbr[(int64_t)j * n + x] = s >= 0 ? perm[(size_t)s] : -1;
+            link[(int64_t)j * n + x] = (uint8_t)(s >= 0 ? 0 : -s);
+        }
+    }
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_t *device_bytes) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (n) *n = ctx->n;
+    if (npad) *npad = ctx->npad;
+    if (device_bytes) *device_bytes = ctx->device_bytes;
+    return LBM_OK;
+}

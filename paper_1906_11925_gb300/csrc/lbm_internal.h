@@ -1,0 +1,71 @@
+// Internal interface between the host side of libhemelb_gb300 (lbm_host.cpp)
+// and its CUDA kernels (lbm_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hemelb_gb300 {
+
+constexpr int kMaxIolets = 64;
+
+// Iolet densities of one step, evaluated on the host in float64 and passed
+// by value: drho[k] = rho_k(t) - rho0 (rounded once to float, so that the
+// small pressure differences keep their relative precision), rho[k] = rho_k(t).
+struct IoletStep {
+    float drho[kMaxIolets];
+    float rho[kMaxIolets];
+};
+
+// Device-side description of one simulation, passed by value to launchers.
+//
+// Kernel table layout (internal Morton order, planes of length npad):
+//   tab[(i - 1) * npad + x], i = 1..q-1, is the pull source of population i
+//   at site x: >= 0 -> population i of site tab (the site x - c_i);
+//   -1 -> wall link opp(i) at x (read own slot opp(i), halfway bounce-back);
+//   -2 - k -> iolet-k link opp(i) at x (read own slot opp(i), which the
+//   previous step filled with the iolet equilibrium).
+// Populations: f[i * npad + x] as float (fp32 storage) or __half bits
+// (fp16 storage) holding the deviation from w_i rho0 (times 2^S for fp16).
+struct DevLattice {
+    int q;
+    int storage;     // 0 fp32, 1 fp16
+    int n;           // sites
+    int64_t npad;    // plane length (multiple of 128)
+    float omega;     // 1 / tau
+    float tau;
+    float rho0;
+    float scale;     // 2^S (fp16 store multiplier)
+    float inv_scale; // 2^-S
+    int n_iolets;
+    const int32_t *tab;           // [q-1][npad]
+    const int32_t *perm;          // [n] internal -> caller index
+};
+
+// One fused pull collide-and-stream step from fin into fout.  The iolet
+// densities come from io, or, when rho_io (device, float64 [n_iolets]) is not
+// null, from rho_io.
+cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
+                        const double *rho_io, cudaStream_t s);
+
+// rho, u, wss of the state held in f (any output may be null), caller order.
+cudaError_t launch_macros(const DevLattice &L, const void *f, float *rho, float *u,
+                          float *wss, cudaStream_t s);
+
+// Deterministic float64 mass: partial sums into partials[nblk], final into out.
+int mass_blocks();
+cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, double *out,
+                        cudaStream_t s);
+
+// f(t) as float64 [q][n] caller order (gather of the stored state).
+cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out,
+                              cudaStream_t s);
+// stored state from float64 [q][n] caller order (inverse of the gather).
+cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f,
+                               cudaStream_t s);
+// stored state of the rest fluid (all deviations zero).
+cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s);
+
+}  // namespace hemelb_gb300

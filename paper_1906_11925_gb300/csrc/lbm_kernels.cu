@@ -1,0 +1,377 @@
+// CUDA kernels of libhemelb_gb300 (sm_103a): the fused pull collide-and-stream
+// step over the sparse, Morton-ordered site list, the macroscopic fields and
+// wall shear stress, the float64 mass reduction, and the gather/scatter that
+// convert the stored state to and from caller-order float64 populations.
+//
+// The method (arXiv 1906.11925, Section 2): collision then propagation of a
+// single-particle distribution on a sparse lattice of fluid sites, D3Q19
+// (Fig. 1); simple bounce-back walls (Section 4).  Collision is LBGK with the
+// compressible second-order equilibrium; iolets impose a density through the
+// equilibrium populations entering from the iolet (see lbm.h).
+//
+// Storage: the buffer read at step t holds, for every site x and direction i,
+// the slot P_i(x) that the pull of step t reads; this is the post-collision
+// population f*_i(x, t-1) for fluid and wall links, and for an iolet link the
+// equilibrium population already evaluated at the iolet density.  Reading
+// the slots through the table (lattice_internal.h) is a permutation, so the
+// gather reproduces f(t) exactly.  Values are deviations d = f - w_i rho0,
+// in float or in IEEE half scaled by 2^S.
+//
+// The step is a bandwidth-bound sparse stencil (about one flop per byte): no
+// tensor cores.  One site per thread; the q - 1 table entries are streamed
+// (evict-first) and coalesced; the q population reads are gathers through the
+// read-only path, made local by the Morton order; the q stores are coalesced
+// and streamed.
+#include <cuda_fp16.h>
+
+#include "lattice.h"
+#include "lbm_internal.h"
+
+namespace hemelb_gb300 {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMassBlocks = 2 * 152;  // fixed grid: deterministic reduction order
+
+template <bool HALF>
+struct Store;
+
+template <>
+struct Store<false> {
+    using T = float;
+    static __device__ __forceinline__ float load(const float *p, float) { return __ldg(p); }
+    static __device__ __forceinline__ float load_plain(const float *p, float) { return *p; }
+    static __device__ __forceinline__ void store(float *p, float v, float) { __stcs(p, v); }
+    static __device__ __forceinline__ void store_plain(float *p, float v, float) { *p = v; }
+};
+
+template <>
+struct Store<true> {
+    using T = __half;
+    static __device__ __forceinline__ float load(const __half *p, float inv) {
+        return __half2float(__ldg(p)) * inv;
+    }
+    static __device__ __forceinline__ float load_plain(const __half *p, float inv) {
+        return __half2float(*p) * inv;
+    }
+    static __device__ __forceinline__ void store(__half *p, float v, float sc) {
+        __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v * sc)));
+    }
+    static __device__ __forceinline__ void store_plain(__half *p, float v, float sc) {
+        *p = __float2half_rn(v * sc);
+    }
+};
+
+// Pull source slot of population i at site x for table entry s.
+__device__ __forceinline__ int64_t src_slot(int i, int s, int x, int64_t np) {
+    return s >= 0 ? (int64_t)i * np + s : (int64_t)opp(i) * np + x;
+}
+
+// Gather the q deviations of site x (pre-collision populations f(t) - w rho0).
+// Returns the smallest table entry seen (<= -2 means the site has iolet links)
+// and, through wall_n, the sum of c_i over entries == -1.
+template <int Q, bool HALF, bool STREAM_TAB>
+__device__ __forceinline__ int gather(const DevLattice &L, const typename Store<HALF>::T *__restrict__ f,
+                                      int x, float (&d)[Q], int (&wn)[3]) {
+    using S = Store<HALF>;
+    const int64_t np = L.npad;
+    int minc = 0;
+    wn[0] = wn[1] = wn[2] = 0;
+    int s[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int32_t *tp = L.tab + (int64_t)(i - 1) * np + x;
+        s[i] = STREAM_TAB ? __ldcs(tp) : __ldg(tp);
+    }
+    d[0] = S::load(f + x, L.inv_scale);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        d[i] = S::load(f + src_slot(i, s[i], x, np), L.inv_scale);
+        minc = min(minc, s[i]);
+        if (s[i] == -1) {
+            wn[0] += cdir<Q>(i, 0);
+            wn[1] += cdir<Q>(i, 1);
+            wn[2] += cdir<Q>(i, 2);
+        }
+    }
+    return minc;
+}
+
+struct Moments {
+    float drho, rho, ux, uy, uz, usq15;
+};
+
+template <int Q>
+__device__ __forceinline__ Moments moments(const float (&d)[Q], float rho0) {
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += d[i];
+        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * d[i];
+        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * d[i];
+        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * d[i];
+    }
+    Moments m;
+    m.drho = drho;
+    m.rho = rho0 + drho;
+    const float ir = 1.0f / m.rho;
+    m.ux = jx * ir;
+    m.uy = jy * ir;
+    m.uz = jz * ir;
+    m.usq15 = 1.5f * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    return m;
+}
+
+// deviation of the equilibrium: feq_i - w_i rho0 = w_i (drho + rho A_i)
+template <int Q>
+__device__ __forceinline__ float deq(int i, float drho, float rho, const Moments &m) {
+    const float cu = cdir<Q>(i, 0) * m.ux + cdir<Q>(i, 1) * m.uy + cdir<Q>(i, 2) * m.uz;
+    return (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - m.usq15));
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_step(const DevLattice L, const typename Store<HALF>::T *__restrict__ fin,
+       typename Store<HALF>::T *__restrict__ fout, const IoletStep io,
+       const double *__restrict__ rho_io) {
+    using S = Store<HALF>;
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    float d[Q];
+    int wn[3];
+    const int minc = gather<Q, HALF, true>(L, fin, x, d, wn);
+    const Moments m = moments<Q>(d, L.rho0);
+    float out[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i] = d[i] - L.omega * (d[i] - deq<Q>(i, m.drho, m.rho, m));
+    if (minc <= -2) {
+        // iolet links (rare): the slot read back through an iolet link at the
+        // next step holds the equilibrium at the iolet density and the site's
+        // current velocity.
+        const int64_t np = L.npad;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int s = L.tab[(int64_t)(i - 1) * np + x];
+            if (s <= -2) {
+                const int k = -2 - s;
+                float drk, rk;
+                if (rho_io) {
+                    const double r = rho_io[k];
+                    drk = (float)(r - (double)L.rho0);
+                    rk = (float)r;
+                } else {
+                    drk = io.drho[k];
+                    rk = io.rho[k];
+                }
+                out[opp(i)] = deq<Q>(i, drk, rk, m);
+            }
+        }
+    }
+    const int64_t np = L.npad;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) S::store(fout + (int64_t)i * np + x, out[i], L.scale);
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, float *__restrict__ rho,
+         float *__restrict__ u, float *__restrict__ wss) {
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    float d[Q];
+    int wn[3];
+    gather<Q, HALF, false>(L, f, x, d, wn);
+    const Moments m = moments<Q>(d, L.rho0);
+    const int xc = L.perm[x];
+    if (rho) rho[xc] = m.rho;
+    if (u) {
+        u[3 * (int64_t)xc + 0] = m.ux;
+        u[3 * (int64_t)xc + 1] = m.uy;
+        u[3 * (int64_t)xc + 2] = m.uz;
+    }
+    if (!wss) return;
+    // sum of c over wall links = -(sum of c_i over entries -1); n = -normalize()
+    const float nn2 = (float)(wn[0] * wn[0] + wn[1] * wn[1] + wn[2] * wn[2]);
+    if (nn2 == 0.f) {
+        wss[xc] = 0.f;
+        return;
+    }
+    const float inn = 1.0f / sqrtf(nn2);
+    const float n0 = wn[0] * inn, n1 = wn[1] * inn, n2 = wn[2] * inn;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float ne = d[i] - deq<Q>(i, m.drho, m.rho, m);
+        const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
+        if (cx) pxx += ne;
+        if (cy) pyy += ne;
+        if (cz) pzz += ne;
+        if (cx * cy) pxy += (cx * cy) * ne;
+        if (cx * cz) pxz += (cx * cz) * ne;
+        if (cy * cz) pyz += (cy * cz) * ne;
+    }
+    const float coef = -(1.0f - 0.5f / L.tau);
+    const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
+    const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
+    const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
+    const float tn = t0 * n0 + t1 * n1 + t2 * n2;
+    const float s0 = t0 - tn * n0, s1 = t1 - tn * n1, s2 = t2 - tn * n2;
+    wss[xc] = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum in a fixed order; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double part[kBlock / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    v = threadIdx.x < kBlock / 32 ? part[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+// mass = n rho0 + sum over all stored slots of the deviation: the gather is a
+// permutation of the slots, so the slots hold exactly the populations f(t).
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f,
+               double *__restrict__ partials) {
+    using S = Store<HALF>;
+    double acc = 0.0;
+    for (int x = blockIdx.x * kBlock + threadIdx.x; x < L.n; x += gridDim.x * kBlock) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
+        acc += (double)s;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_mass_final(const double *__restrict__ partials, int nparts, double base, double *__restrict__ out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += kBlock) acc += partials[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[0] = base + acc;
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, double *__restrict__ out) {
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    float d[Q];
+    int wn[3];
+    gather<Q, HALF, false>(L, f, x, d, wn);
+    const int64_t xc = L.perm[x];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = wdir<Q>(i) * (double)L.rho0 + (double)d[i];
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_scatter_f64(const DevLattice L, const double *__restrict__ in, typename Store<HALF>::T *__restrict__ f) {
+    using S = Store<HALF>;
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    const int64_t xc = L.perm[x];
+    const int64_t np = L.npad;
+    S::store_plain(f + x, (float)(in[xc] - wdir<Q>(0) * (double)L.rho0), L.scale);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int s = L.tab[(int64_t)(i - 1) * np + x];
+        const double v = in[(int64_t)i * L.n + xc] - wdir<Q>(i) * (double)L.rho0;
+        S::store_plain(f + src_slot(i, s, x, np), (float)v, L.scale);
+    }
+}
+
+inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <int Q, bool HALF>
+cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
+                      const double *rho_io, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_step<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HGB_DISPATCH(L, FN, ...)                                                         \
+    ((L).q == 15 ? ((L).storage ? FN<15, true>(__VA_ARGS__) : FN<15, false>(__VA_ARGS__)) \
+                 : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
+
+cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
+                        const double *rho_io, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
+}
+
+namespace {
+template <int Q, bool HALF>
+cudaError_t macros_impl(const DevLattice &L, const void *f, float *rho, float *u, float *wss,
+                        cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_macros<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, rho, u, wss);
+    return cudaGetLastError();
+}
+template <int Q, bool HALF>
+cudaError_t mass_impl(const DevLattice &L, const void *f, double *partials, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_mass_partial<Q, HALF><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, partials);
+    return cudaGetLastError();
+}
+template <int Q, bool HALF>
+cudaError_t gather_impl(const DevLattice &L, const void *f, double *out, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_gather_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, out);
+    return cudaGetLastError();
+}
+template <int Q, bool HALF>
+cudaError_t scatter_impl(const DevLattice &L, const double *in, void *f, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_scatter_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, in, (T *)f);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_macros(const DevLattice &L, const void *f, float *rho, float *u, float *wss,
+                          cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, macros_impl, L, f, rho, u, wss, s);
+}
+
+int mass_blocks() { return kMassBlocks; }
+
+cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, double *out,
+                        cudaStream_t s) {
+    cudaError_t e = HGB_DISPATCH(L, mass_impl, L, f, partials, s);
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<1, kBlock, 0, s>>>(partials, kMassBlocks, (double)L.n * (double)L.rho0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, gather_impl, L, f, out, s);
+}
+
+cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, scatter_impl, L, in, f, s);
+}
+
+cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s) {
+    const size_t elem = L.storage ? 2 : 4;
+    return cudaMemsetAsync(f, 0, elem * (size_t)L.q * (size_t)L.npad, s);
+}
+
+}  // namespace hemelb_gb300

@@ -1,0 +1,279 @@
+"""Python binding of libhemelb_gb300 (ctypes, argument marshalling only).
+
+Every call goes through the C ABI of ``include/lbm.h``; the names follow it
+(``lbm_links_build`` -> ``links_build``, ``lbm_create`` -> ``Lattice`` ...).
+PyTorch supplies device memory for outputs and the CUDA stream.  There is no
+CPU fallback: if the shared library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+STORE_FP32 = 0
+STORE_FP16 = 1
+MAX_IOLETS = 64
+
+_STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM",
+           4: "LBM_ERR_CUDA", 5: "LBM_ERR_UNSTABLE", 6: "LBM_ERR_STATE"}
+
+EXPORTED = (
+    "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
+    "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
+    "lbm_get_populations", "lbm_set_populations", "lbm_state_bytes", "lbm_get_state",
+    "lbm_set_state", "lbm_get_links", "lbm_info",
+)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class _Params(C.Structure):
+    _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("tau", C.c_double),
+                ("rho0", C.c_double), ("fp16_scale_log2", C.c_int32), ("n_iolets", C.c_int32),
+                ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
+                ("phase", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load (building if needed) libhemelb_gb300.so; raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise OSError("libhemelb_gb300.so is not built: %s" % path)
+        _build.build()
+    lib = C.CDLL(path)
+    P, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    sig = {
+        "lbm_links_build": [i32, i64, P, i64, P, P, P, P, P],
+        "lbm_create": [P, P, i64, P, P, P, P],
+        "lbm_destroy": [P],
+        "lbm_last_error": [P],
+        "lbm_set_stream": [P, P],
+        "lbm_step": [P, i64],
+        "lbm_step_driven": [P, i64, P, P],
+        "lbm_get_time": [P, P],
+        "lbm_set_time": [P, i64],
+        "lbm_macros": [P, P, P, P],
+        "lbm_mass": [P, P],
+        "lbm_get_populations": [P, P],
+        "lbm_set_populations": [P, P],
+        "lbm_state_bytes": [P, P],
+        "lbm_get_state": [P, P, C.c_size_t],
+        "lbm_set_state": [P, P, C.c_size_t],
+        "lbm_get_links": [P, P, P],
+        "lbm_info": [P, P, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        lib = load_library()
+        msg = lib.lbm_last_error(ctx).decode(errors="replace")
+        raise LbmError(st, msg)
+
+
+def links_build(q: int, xyz, io_xyz=None, io_id=None, periodic=(0, 0, 0)):
+    """Canonical neighbour table (int32 [q, n]) and link flags (uint8 [q, n])."""
+    lib = load_library()
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    n = xyz.shape[0]
+    io_xyz = np.ascontiguousarray(np.zeros((0, 3)) if io_xyz is None else io_xyz,
+                                  dtype=np.int32).reshape(-1, 3)
+    io_id = np.ascontiguousarray(np.zeros(0) if io_id is None else io_id, dtype=np.int32)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    nbr = np.empty((q, n), np.int32)
+    link = np.empty((q, n), np.uint8)
+    _check(lib.lbm_links_build(int(q), n, _p(xyz), io_xyz.shape[0], _p(io_xyz), _p(io_id),
+                               _p(per), _p(nbr), _p(link)))
+    return nbr, link
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Lattice:
+    """One simulation (``lbm_create`` ... ``lbm_destroy``) on the current GPU."""
+
+    def __init__(self, q: int, xyz, nbr, link, tau: float, storage: int = STORE_FP32,
+                 rho0: float = 1.0, fp16_scale_log2: int = 14,
+                 rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
+                 period: Sequence[float] = None, phase: Sequence[float] = None,
+                 stream=None):
+        self._lib = load_library()
+        self._ctx = C.c_void_p()
+        k = len(rho_mean)
+        z = [0.0] * k
+        self._io = [np.ascontiguousarray(v, dtype=np.float64) for v in
+                    (rho_mean, z if amp is None else amp, z if period is None else period,
+                     z if phase is None else phase)]
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        link = np.ascontiguousarray(link, dtype=np.uint8)
+        n = xyz.shape[0]
+        if nbr.shape != (q, n) or link.shape != (q, n):
+            raise ValueError("nbr and link must be [q, n]")
+        prm = _Params(int(q), int(storage), float(tau), float(rho0), int(fp16_scale_log2), k,
+                      *[(a.ctypes.data if k else None) for a in self._io])
+        self.q, self.n, self.tau, self.storage, self.rho0 = int(q), n, float(tau), int(storage), float(rho0)
+        self.n_iolets = k
+        st = self._lib.lbm_create(C.byref(self._ctx), C.byref(prm), n, _p(xyz), _p(nbr), _p(link),
+                                  _stream_handle(stream))
+        _check(st, None)
+
+    @classmethod
+    def from_geometry(cls, geom, q: int, tau: float, storage: int = STORE_FP32, **kw):
+        nbr, link = links_build(q, geom.xyz, geom.io_xyz, geom.io_id, geom.periodic)
+        return cls(q, geom.xyz, nbr, link, tau, storage=storage, rho_mean=geom.rho_mean,
+                   amp=geom.amp, period=geom.period, phase=geom.phase, **kw)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.lbm_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        _check(st, self._ctx)
+
+    # -- calls
+    def set_stream(self, stream):
+        self._ck(self._lib.lbm_set_stream(self._ctx, _stream_handle(stream)))
+
+    def step(self, nsteps: int = 1):
+        self._ck(self._lib.lbm_step(self._ctx, int(nsteps)))
+
+    def step_driven(self, rho_io, mass: bool = True):
+        """Steps with caller-supplied iolet densities rho_io [nsteps, K] (host
+        array, float64; may be a pinned torch tensor).  Returns the mass after
+        each step (float64 [nsteps]) or None."""
+        if hasattr(rho_io, "data_ptr"):
+            nsteps = int(rho_io.shape[0])
+            ptr = C.c_void_p(rho_io.data_ptr())
+            keep = rho_io
+        else:
+            keep = np.ascontiguousarray(rho_io, dtype=np.float64).reshape(-1, max(self.n_iolets, 1))
+            nsteps = keep.shape[0]
+            ptr = _p(keep)
+        out = np.empty(nsteps, np.float64) if mass else None
+        self._ck(self._lib.lbm_step_driven(self._ctx, nsteps, ptr, _p(out)))
+        del keep
+        return out
+
+    @property
+    def time(self) -> int:
+        t = C.c_int64()
+        self._ck(self._lib.lbm_get_time(self._ctx, C.byref(t)))
+        return t.value
+
+    def set_time(self, t: int):
+        self._ck(self._lib.lbm_set_time(self._ctx, int(t)))
+
+    def macros(self, rho=None, u=None, wss=None, want=("rho", "u", "wss")):
+        """rho [n], u [n, 3], wss [n] as float32 CUDA tensors (caller order)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if rho is None and "rho" in want:
+            rho = torch.empty(self.n, dtype=torch.float32, device=dev)
+        if u is None and "u" in want:
+            u = torch.empty(self.n, 3, dtype=torch.float32, device=dev)
+        if wss is None and "wss" in want:
+            wss = torch.empty(self.n, dtype=torch.float32, device=dev)
+        for t, shape in ((rho, (self.n,)), (u, (self.n, 3)), (wss, (self.n,))):
+            if t is not None:
+                if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() \
+                        or tuple(t.shape) != shape:
+                    raise ValueError("macros outputs must be contiguous float32 CUDA tensors")
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._ck(self._lib.lbm_macros(self._ctx, ptr(rho), ptr(u), ptr(wss)))
+        return rho, u, wss
+
+    def mass(self) -> float:
+        m = C.c_double()
+        self._ck(self._lib.lbm_mass(self._ctx, C.byref(m)))
+        return m.value
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((self.q, self.n), np.float64)
+        self._ck(self._lib.lbm_get_populations(self._ctx, _p(f)))
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (self.q, self.n):
+            raise ValueError("populations must be [q, n]")
+        self._ck(self._lib.lbm_set_populations(self._ctx, _p(f)))
+
+    def state_bytes(self) -> int:
+        b = C.c_size_t()
+        self._ck(self._lib.lbm_state_bytes(self._ctx, C.byref(b)))
+        return b.value
+
+    def get_state(self) -> np.ndarray:
+        buf = np.empty(self.state_bytes(), np.uint8)
+        self._ck(self._lib.lbm_get_state(self._ctx, _p(buf), buf.nbytes))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._ck(self._lib.lbm_set_state(self._ctx, _p(buf), buf.nbytes))
+
+    def get_links(self) -> Tuple[np.ndarray, np.ndarray]:
+        nbr = np.empty((self.q, self.n), np.int32)
+        link = np.empty((self.q, self.n), np.uint8)
+        self._ck(self._lib.lbm_get_links(self._ctx, _p(nbr), _p(link)))
+        return nbr, link
+
+    def info(self):
+        n, npad, b = C.c_int64(), C.c_int64(), C.c_size_t()
+        self._ck(self._lib.lbm_info(self._ctx, C.byref(n), C.byref(npad), C.byref(b)))
+        return dict(n=n.value, npad=npad.value, device_bytes=b.value)

@@ -1,0 +1,109 @@
+"""The C-ABI library loads, exports every declared entry point, and its
+host-only parts (link building, argument and table validation) behave as
+specified -- no GPU needed."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_11925_gb300 import geometry as G
+from paper_1906_11925_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|void|const char \*)\s*(lbm_\w+)\s*\(",
+                                 txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load_library()
+    syms = declared_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(lbm.EXPORTED) == syms
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("geom", ["tube", "mask_open", "mask_periodic", "slab", "aneurysm"])
+def test_links_bit_exact_vs_oracle(q, geom):
+    g = {"tube": lambda: G.tube(),
+         "mask_open": lambda: G.random_mask((7, 6, 5), p=0.5, seed=11, n_iolets=4),
+         "mask_periodic": lambda: G.random_mask((6, 5, 4), p=0.6, seed=12, periodic=True),
+         "slab": lambda: G.slab(16, 3, 5),
+         "aneurysm": lambda: G.aneurysm()}[geom]()
+    a = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    b = oracle.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+
+
+def test_links_empty():
+    nbr, link = lbm.links_build(19, np.zeros((0, 3)))
+    assert nbr.shape == (19, 0)
+
+
+@pytest.mark.parametrize("case", ["dup", "q", "io_id", "coord"])
+def test_links_errors(case):
+    xyz = np.array([[0, 0, 0], [1, 0, 0]])
+    kw = {}
+    q = 15
+    if case == "dup":
+        xyz = np.array([[0, 0, 0], [0, 0, 0]])
+    elif case == "q":
+        q = 27
+    elif case == "io_id":
+        kw = dict(io_xyz=np.array([[2, 0, 0]]), io_id=np.array([64]))
+    else:
+        xyz = np.array([[1 << 19, 0, 0]])
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.links_build(q, xyz, **kw)
+    assert ei.value.name == "LBM_ERR_ARG"
+
+
+def _create(q, g, nbr=None, link=None, **kw):
+    if nbr is None:
+        nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    args = dict(tau=0.8, rho_mean=g.rho_mean, amp=g.amp, period=g.period, phase=g.phase,
+                stream=0)
+    args.update(kw)
+    return lbm.Lattice(q, g.xyz, nbr, link, **args)
+
+
+@pytest.mark.parametrize("kw", [dict(tau=0.5), dict(tau=float("nan")), dict(storage=2),
+                                dict(rho0=0.0), dict(storage=1, fp16_scale_log2=30)])
+def test_create_rejects_bad_params_before_any_gpu_call(kw):
+    g = G.tube(radius=2, length=4, nx=5, ny=5)
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(15, g, **kw)
+    assert ei.value.name == "LBM_ERR_ARG"
+
+
+@pytest.mark.parametrize("corrupt", ["asym", "range", "flag", "rest", "iolet_id"])
+def test_create_rejects_bad_table(corrupt):
+    g = G.tube(radius=2, length=4, nx=5, ny=5)
+    nbr, link = lbm.links_build(15, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    nbr = nbr.copy()
+    link = link.copy()
+    x = int(np.nonzero(link[1] == 0)[0][0])
+    if corrupt == "asym":
+        nbr[1, x] = (nbr[1, x] + 1) % g.n
+    elif corrupt == "range":
+        nbr[1, x] = g.n
+    elif corrupt == "flag":
+        link[1, x] = 1
+    elif corrupt == "rest":
+        nbr[0, 0] = 1
+    else:
+        xs = np.nonzero(link[6] >= 2)[0]
+        link[6, xs[0]] = 2 + 7
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(15, g, nbr=nbr, link=link)
+    assert ei.value.name == "LBM_ERR_TABLE"

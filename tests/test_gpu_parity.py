@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: velocity and density within a relative L2 error of 1e-5 for fp32
+storage and 2e-3 for fp16-deviation storage after the stated step count
+(1000 steps of the straight-tube Poiseuille case); integer tables bit-exact.
+Single-step and short-run population checks use relative L2 error of the
+deviations f - w rho0 (1e-6 fp32, 2e-3 fp16).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_11925_gb300 import geometry as G
+from paper_1906_11925_gb300 import lbm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+FP32, FP16 = lbm.STORE_FP32, lbm.STORE_FP16
+TOL_MACRO = {FP32: 1e-5, FP16: 2e-3}
+TOL_POP = {FP32: 1e-5, FP16: 2e-3}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make(g, q, tau, storage=FP32, **kw):
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean, amp=g.amp,
+                    period=g.period, phase=g.phase, **kw)
+    return L, nbr, link
+
+
+def near_rest(q, n, seed, amp=0.01):
+    """Random populations w_i (1 + amp U(-1, 1)) (inputs for both sides)."""
+    rng = np.random.default_rng(seed)
+    return oracle.rest_state(q, n) * (1.0 + amp * (2.0 * rng.random((q, n)) - 1.0))
+
+
+def deviations(q, f):
+    _, w, _ = oracle.lattice(q)
+    return f - w[:, None]
+
+
+GEOMS = {
+    "tube": lambda: G.tube(),
+    "mask": lambda: G.random_mask((9, 8, 7), p=0.55, seed=21, n_iolets=3),
+    "mask_periodic": lambda: G.random_mask((8, 7, 6), p=0.6, seed=22, n_iolets=2, periodic=True),
+    "aneurysm": lambda: G.aneurysm(),
+}
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+def test_device_link_table_round_trip(q, geom):
+    g = GEOMS[geom]()
+    L, nbr, link = make(g, q, 0.8)
+    on, ol = oracle.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    dn, dl = L.get_links()
+    assert np.array_equal(dn, on) and np.array_equal(dl, ol)
+    assert np.array_equal(nbr, on) and np.array_equal(link, ol)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_rest_state_is_exact(q, storage):
+    g = G.tube(radius=4, length=12, nx=9, ny=9, rho_in=1.0, rho_out=1.0)
+    L, _, _ = make(g, q, 0.7, storage)
+    L.step(50)
+    f = L.get_populations()
+    assert np.array_equal(f, oracle.rest_state(q, g.n))
+    assert L.time == 50
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_tube_poiseuille_1000_steps(storage):
+    """Straight tube r = 8, 17x17x64, D3Q15, tau = 0.8, rho 1.001 -> 0.999,
+    from rest, 1000 steps: rho and u against the FP64 oracle."""
+    q, tau = 15, 0.8
+    g = G.tube()
+    L, nbr, link = make(g, q, tau, storage)
+    L.step(1000)
+    rho, u, wss = [t.cpu().numpy() for t in L.macros()]
+    f = oracle.run(q, nbr, link, tau, oracle.rest_state(q, g.n), 1000, geom=g)
+    orho, ou, owss = oracle.macros(q, link, tau, f)
+    e_u = rel_l2(u, ou)
+    e_rho = rel_l2(rho, orho)
+    e_drho = rel_l2(rho - 1.0, orho - 1.0)
+    e_wss = rel_l2(wss, owss)
+    print("storage", storage, "u", e_u, "rho", e_rho, "rho-1", e_drho, "wss", e_wss)
+    assert e_u <= TOL_MACRO[storage]
+    assert e_rho <= TOL_MACRO[storage]
+    assert e_wss <= {FP32: 1e-4, FP16: 5e-2}[storage]
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("geom", ["mask", "mask_periodic"])
+def test_random_state_short_runs(q, storage, geom):
+    """Random near-equilibrium state, pulsatile iolets, ragged small domain:
+    populations after 1, 7 and 40 steps."""
+    g = GEOMS[geom]()
+    tau = 0.63
+    L, nbr, link = make(g, q, tau, storage)
+    f0 = near_rest(q, g.n, seed=5)
+    L.set_populations(f0)
+    L.set_time(3)
+    of = f0.copy()
+    t = 3
+    for nsteps in (1, 6, 33):
+        L.step(nsteps)
+        of = oracle.run(q, nbr, link, tau, of, nsteps, t0=t, geom=g)
+        t += nsteps
+        gf = L.get_populations()
+        err = rel_l2(deviations(q, gf), deviations(q, of))
+        print(q, storage, geom, t, err)
+        assert err <= TOL_POP[storage], (t, err)
+        assert L.time == t
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_mass_reduction_and_conservation(q):
+    g = G.periodic_box(12, 10, 9)
+    L, nbr, link = make(g, q, 0.7)
+    f0 = near_rest(q, g.n, seed=8, amp=0.05)
+    L.set_populations(f0)
+    m0 = L.mass()
+    assert abs(m0 - oracle.mass(f0)) <= 1e-9 * g.n
+    L.step(500)
+    m1 = L.mass()
+    assert abs(m1 - m0) <= 1e-7 * m0, (m0, m1)
+    m2 = L.mass()
+    assert m2 == m1  # deterministic
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_resume_is_bit_exact(storage):
+    g = G.random_mask((9, 8, 7), p=0.6, seed=31, n_iolets=2)
+    q, tau = 19, 0.75
+    A, _, _ = make(g, q, tau, storage)
+    A.set_populations(near_rest(q, g.n, seed=1))
+    B, _, _ = make(g, q, tau, storage)
+    B.set_populations(near_rest(q, g.n, seed=1))
+    A.step(30)
+    B.step(12)
+    snap, t = B.get_state(), B.time
+    C, _, _ = make(g, q, tau, storage)
+    C.set_state(snap)
+    C.set_time(t)
+    C.step(18)
+    assert np.array_equal(A.get_state(), C.get_state())
+    assert C.time == 30
+
+
+def test_site_order_invariance():
+    """Outputs do not depend on the caller's site order (bit-exact)."""
+    g = G.random_mask((10, 9, 8), p=0.55, seed=41, n_iolets=2)
+    q, tau = 19, 0.7
+    rng = np.random.default_rng(0)
+    p = rng.permutation(g.n)
+    g2 = G.random_mask((10, 9, 8), p=0.55, seed=41, n_iolets=2)
+    g2.xyz = g.xyz[p]
+    A, _, _ = make(g, q, tau)
+    B, _, _ = make(g2, q, tau)
+    f0 = near_rest(q, g.n, seed=2)
+    A.set_populations(f0)
+    B.set_populations(f0[:, p])
+    A.step(25)
+    B.step(25)
+    ra, ua, wa = [t.cpu().numpy() for t in A.macros()]
+    rb, ub, wb = [t.cpu().numpy() for t in B.macros()]
+    assert np.array_equal(ra[p], rb) and np.array_equal(ua[p], ub) and np.array_equal(wa[p], wb)
+
+
+def test_driven_iolets_match_schedule():
+    g = G.tube(radius=4, length=16, nx=9, ny=9, rho_in=1.002, rho_out=0.999)
+    q, tau = 15, 0.8
+    A, _, _ = make(g, q, tau)
+    B, _, _ = make(g, q, tau)
+    A.step(40)
+    rows = np.tile(g.rho_mean, (40, 1))
+    masses = B.step_driven(rows)
+    assert np.array_equal(A.get_state(), B.get_state())
+    assert masses.shape == (40,) and masses[-1] == A.mass()
+
+
+def test_empty_site_list():
+    g = G.random_mask((3, 3, 3), p=0.0, seed=0, n_iolets=0)
+    assert g.n == 0
+    L, _, _ = make(g, 19, 0.8)
+    L.step(3)
+    assert L.mass() == 0.0
+    assert L.get_populations().shape == (19, 0)
+
+
+def test_set_get_round_trip():
+    g = G.random_mask((7, 7, 7), p=0.6, seed=3, n_iolets=2)
+    q = 15
+    L, _, _ = make(g, q, 0.8)
+    f0 = near_rest(q, g.n, seed=4)
+    L.set_populations(f0)
+    f1 = L.get_populations()
+    assert np.abs(f1 - f0).max() <= 2.0 ** -24 * np.abs(deviations(q, f0)).max() * 1.01
+
+
+def test_non_finite_state_is_reported():
+    g = G.tube(radius=3, length=6, nx=7, ny=7)
+    q = 15
+    L, _, _ = make(g, q, 0.8)
+    f = oracle.rest_state(q, g.n)
+    f[3, 5] = np.nan
+    L.set_populations(f)
+    L.step(2)
+    with pytest.raises(lbm.LbmError) as ei:
+        L.mass()
+    assert ei.value.name == "LBM_ERR_UNSTABLE"
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_wss_slab(q):
+    """Wall shear stress of plane Poiseuille flow: GPU vs oracle after 3000
+    steps (fp32), and both near the analytic G (h/2 - 1/2)."""
+    g = G.slab(48, 2, 10)
+    tau = 0.5 + np.sqrt(3.0 / 16.0)
+    L, nbr, link = make(g, q, tau)
+    L.step(3000)
+    rho, u, wss = [t.cpu().numpy() for t in L.macros()]
+    f = oracle.run(q, nbr, link, tau, oracle.rest_state(q, g.n), 3000, geom=g)
+    orho, ou, owss = oracle.macros(q, link, tau, f)
+    assert rel_l2(u, ou) <= 1e-5
+    assert rel_l2(wss, owss) <= 1e-4
+
+
+@pytest.fixture(scope="module")
+def tree():
+    """The benchmark workload: seeded 6-generation vessel tree, D3Q19."""
+    q = 19
+    g = G.vessel_tree()
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    on, ol = oracle.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    assert np.array_equal(nbr, on) and np.array_equal(link, ol)
+    del on, ol
+    return g, nbr, link
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_vessel_tree_full_size_one_step(tree, storage):
+    """The benchmark workload (~10.8M sites) in the launch configuration the
+    benchmark times: the device link table bit-exact, and every population of
+    one step from a random state against the oracle's step."""
+    q, tau = 19, 0.6
+    g, nbr, link = tree
+    L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean, amp=g.amp,
+                    period=g.period, phase=g.phase)
+    dn, dl = L.get_links()
+    assert np.array_equal(dn, nbr) and np.array_equal(dl, link)
+    del dn, dl
+    f0 = near_rest(q, g.n, seed=6)
+    L.set_populations(f0)
+    L.set_time(1234)
+    L.step(1)
+    gf = L.get_populations()
+    of = oracle.step(q, nbr, link, tau, f0, t=1234, geom=g)
+    err = rel_l2(deviations(q, gf), deviations(q, of))
+    print("tree one step", storage, err)
+    assert err <= TOL_POP[storage]
