@@ -58,6 +58,11 @@ def _bind(path: str):
     lib.orc_macros.argtypes = [i32, i64, P, f64, P, P, P, P]
     lib.orc_mass.argtypes = [i32, i64, P]
     lib.orc_mass.restype = f64
+    lib.orc_adjoint_step.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, P, P, P, P, P, P, P]
+    lib.orc_objective.argtypes = [i32, i64, P, f64, i32, P, P, f64, P, P]
+    lib.orc_objective.restype = f64
+    lib.orc_gradient.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, i32, P,
+                                 i64, i64, f64, P, P, P, P, P, P]
     lib.orc_num_threads.restype = i32
     lib.orc_set_threads.argtypes = [i32]
     return lib
@@ -171,6 +176,83 @@ class Oracle:
     def mass(self, f) -> float:
         f = _c(f, np.float64)
         return float(self.lib.orc_mass(f.shape[0], f.shape[1], _p(f)))
+
+    OBJ_WSS = 0
+    OBJ_DENSITY = 1
+
+    def adjoint_step(self, q, nbr, link, tau, f, lam_next, t=0, geom=None, **io):
+        """lam(t) = (dF_t/df)^T lam(t+1) at the state f = f(t); returns
+        (lam, dJ/dtau, dJ/dmean[K], dJ/damp[K], dJ/dphase[K]) of this step."""
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        f = _c(f, np.float64)
+        ln = _c(lam_next, np.float64)
+        n = f.shape[1]
+        I = _Iolets(geom, **io)
+        lam = np.empty_like(f)
+        dtau = np.zeros(1)
+        K = max(I.k, 1)
+        dm, da, dp = np.zeros(K), np.zeros(K), np.zeros(K)
+        r = self.lib.orc_adjoint_step(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean),
+                                      _p(I.amp), _p(I.period), _p(I.phase), int(t), _p(f), _p(ln),
+                                      _p(lam), _p(dtau), _p(dm), _p(da), _p(dp))
+        if r != 0:
+            raise ValueError("orc_adjoint_step failed")
+        return lam, float(dtau[0]), dm[:I.k], da[:I.k], dp[:I.k]
+
+    def objective(self, q, link, tau, kind, m, f, scale=1.0, grad=False):
+        """sum_x m_x q(x) of state f (kind 0 = wall shear stress, 1 = density);
+        with grad=True also (scale * d/df, scale * explicit d/dtau)."""
+        link = _c(link, np.uint8)
+        f = _c(f, np.float64)
+        m = _c(m, np.float64)
+        n = f.shape[1]
+        lam = np.zeros_like(f) if grad else None
+        dtau = np.zeros(1)
+        J = self.lib.orc_objective(q, n, _p(link), float(tau), int(kind), _p(m), _p(f),
+                                   float(scale), _p(lam), _p(dtau))
+        return (J, lam, float(dtau[0])) if grad else J
+
+    def gradient(self, q, nbr, link, tau, f0, nsteps, kind, m, t_begin, t_end, scale=1.0,
+                 t0=0, geom=None, want_lam0=False, **io):
+        """Objective J = scale * sum_{t_begin <= t < t_end} sum_x m_x q(x, t) over
+        the states of an nsteps run from f0 at time t0, and its gradient by the
+        discrete adjoint (every state stored).  Returns a dict with J, dtau,
+        dmean, damp, dphase (per iolet) and optionally lam0 = dJ/df0."""
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        f0 = _c(f0, np.float64)
+        m = _c(m, np.float64)
+        n = f0.shape[1]
+        I = _Iolets(geom, **io)
+        K = max(I.k, 1)
+        J, dtau = np.zeros(1), np.zeros(1)
+        dm, da, dp = np.zeros(K), np.zeros(K), np.zeros(K)
+        lam0 = np.zeros_like(f0) if want_lam0 else None
+        r = self.lib.orc_gradient(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
+                                  _p(I.period), _p(I.phase), int(t0), int(nsteps), _p(f0),
+                                  int(kind), _p(m), int(t_begin), int(t_end), float(scale),
+                                  _p(J), _p(dtau), _p(dm), _p(da), _p(dp), _p(lam0))
+        if r != 0:
+            raise ValueError("orc_gradient failed")
+        out = dict(J=float(J[0]), dtau=float(dtau[0]), dmean=dm[:I.k], damp=da[:I.k],
+                   dphase=dp[:I.k])
+        if want_lam0:
+            out["lam0"] = lam0
+        return out
+
+    def objective_run(self, q, nbr, link, tau, f0, nsteps, kind, m, t_begin, t_end, scale=1.0,
+                      t0=0, geom=None, **io):
+        """J alone, by running forward (used for finite differences)."""
+        f = np.array(f0, dtype=np.float64, copy=True)
+        J = 0.0
+        for s in range(nsteps + 1):
+            t = t0 + s
+            if t_begin <= t < t_end:
+                J += self.objective(q, link, tau, kind, m, f)
+            if s < nsteps:
+                f = self.step(q, nbr, link, tau, f, t=t, geom=geom, **io)
+        return scale * J
 
     def rest_state(self, q: int, n: int, rho0: float = 1.0) -> np.ndarray:
         """f_i = w_i rho0 at every site (fluid at rest)."""

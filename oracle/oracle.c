@@ -347,3 +347,226 @@ double orc_mass(int q, int64_t n, const double *f) {
         for (int i = 0; i < q; ++i) m += f[(int64_t)i * n + x];
     return m;
 }
+
+/* ---------------------------------------------------------------- adjoint
+ *
+ * Discrete adjoint of orc_step (reverse mode, float64).  With the step
+ * written as f(t+1) = F_t(f(t); tau, iolet schedule) and an objective
+ * J = scale * sum_{t in window} sum_x m_x q(x, t), the adjoint variable
+ * lam(t) = dJ/df(t) obeys lam(t) = (dF_t/df)^T lam(t+1) + dj_t/df(t).
+ *
+ * Per site x, with lam*_i the adjoint of the post-collision population:
+ *   fluid link i: lam*_i = lam_i(x + c_i, t+1);  wall link i: lam*_i =
+ *   lam_opp(i)(x, t+1);  iolet link i: lam*_i = 0 (f*_i leaves the domain)
+ *   and the returning population feq_opp(i)(rho_k(t), u) feeds back into u
+ *   and rho_k(t).
+ * Collision f*_i = (1 - w) f_i + w feq_i(rho, u), w = 1/tau, with
+ *   d feq_i / d rho = feq_i / rho,
+ *   d feq_i / d u   = w_i rho (3 c_i + 9 (c_i.u) c_i - 3 u),
+ *   d rho / d f_j = 1,  d u / d f_j = (c_j - u) / rho,
+ * gives lam_j(x, t) = (1 - w) lam*_j + w (a + b.(c_j - u)/rho)
+ *                     + g.(c_j - u)/rho,
+ *   a = sum_i lam*_i feq_i / rho,  b = sum_i lam*_i d feq_i / d u,
+ *   g = sum over iolet links i of lam_opp(i)(x, t+1) d feq_opp(i) / d u.
+ * Parameter derivatives accumulated here:
+ *   dJ/dtau      += sum_i lam*_i (f_i - feq_i) / tau^2,
+ *   dJ/drho_k(t) += sum over iolet-k links of lam_opp(i)(x, t+1) feq_opp(i)/rho_k,
+ * and, through rho_k(t) = mean + amp sin(2 pi t / period + phase), the
+ * derivatives with respect to mean, amp and phase of every iolet.
+ */
+
+static void dfeq_du(const lattice_t *L, int i, double rho, const double u[3], double out[3]) {
+    double cu = L->e[i][0] * u[0] + L->e[i][1] * u[1] + L->e[i][2] * u[2];
+    for (int a = 0; a < 3; ++a) out[a] = L->w[i] * rho * (3.0 * L->e[i][a] + 9.0 * cu * L->e[i][a] - 3.0 * u[a]);
+}
+
+int orc_adjoint_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                     int n_io, const double *rho_mean, const double *amp, const double *period,
+                     const double *phase, int64_t t, const double *f, const double *lam_next,
+                     double *lam, double *dtau, double *dmean, double *damp, double *dphase) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return -1;
+    const double om = 1.0 / tau;
+    double acc_tau = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        double g[19], feq[19], ls[19], rho, u[3];
+        for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
+        moments(&L, g, &rho, u);
+        equilibrium(&L, rho, u, feq);
+        double gu[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < q; ++i) {
+            int lk = link[(int64_t)i * n + x];
+            if (lk == 0) {
+                ls[i] = lam_next[(int64_t)i * n + nbr[(int64_t)i * n + x]];
+            } else if (lk == 1) {
+                ls[i] = lam_next[(int64_t)L.opp[i] * n + x];
+            } else {
+                int k = lk - 2, o = L.opp[i];
+                double lo = lam_next[(int64_t)o * n + x];
+                double rk = iolet_rho(k, t, rho_mean, amp, period, phase);
+                double feq_k[19], d[3];
+                equilibrium(&L, rk, u, feq_k);
+                dfeq_du(&L, o, rk, u, d);
+                for (int a = 0; a < 3; ++a) gu[a] += lo * d[a];
+                double drk = lo * feq_k[o] / rk;
+                dmean[k] += drk;
+                if (period[k] != 0.0 && amp[k] != 0.0) {
+                    double arg = 2.0 * M_PI * (double)t / period[k] + phase[k];
+                    damp[k] += drk * sin(arg);
+                    dphase[k] += drk * amp[k] * cos(arg);
+                } else if (period[k] != 0.0) {
+                    damp[k] += drk * sin(2.0 * M_PI * (double)t / period[k] + phase[k]);
+                }
+                ls[i] = 0.0;
+            }
+        }
+        double a = 0.0, b[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < q; ++i) {
+            double d[3];
+            a += ls[i] * feq[i] / rho;
+            dfeq_du(&L, i, rho, u, d);
+            for (int c = 0; c < 3; ++c) b[c] += ls[i] * d[c];
+            acc_tau += ls[i] * (g[i] - feq[i]) / (tau * tau);
+        }
+        for (int j = 0; j < q; ++j) {
+            double s = a, h = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double dj = (L.e[j][c] - u[c]) / rho;
+                s += b[c] * dj;
+                h += gu[c] * dj;
+            }
+            lam[(int64_t)j * n + x] = (1.0 - om) * ls[j] + om * s + h;
+        }
+    }
+    *dtau += acc_tau;
+    (void)n_io;
+    return 0;
+}
+
+/* Objective terms.  kind 0: wall shear stress (as orc_macros), kind 1:
+ * density.  q(x) is weighted by m[x]. */
+enum { ORC_OBJ_WSS = 0, ORC_OBJ_DENSITY = 1 };
+
+/* wall normal of site x (unit, from its wall links); returns 0 if none */
+static int wall_normal(const lattice_t *L, int64_t n, const uint8_t *link, int64_t x, double nv[3]) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < L->q; ++i)
+        if (link[(int64_t)i * n + x] == 1)
+            for (int a = 0; a < 3; ++a) s[a] += L->e[i][a];
+    double sn = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (sn == 0.0) return 0;
+    for (int a = 0; a < 3; ++a) nv[a] = -s[a] / sn;
+    return 1;
+}
+
+/* sum_x m_x q(x) of the state f; optional explicit d/dtau and d/df (both
+ * multiplied by scale and added to *dtau and lam) */
+double orc_objective(int q, int64_t n, const uint8_t *link, double tau, int kind,
+                     const double *m, const double *f, double scale, double *lam, double *dtau) {
+    lattice_t L;
+    if (get_lattice(q, &L)) return NAN;
+    double J = 0.0, jt = 0.0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (m[x] == 0.0) continue;
+        double g[19], feq[19], rho, u[3];
+        for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
+        moments(&L, g, &rho, u);
+        if (kind == ORC_OBJ_DENSITY) {
+            J += m[x] * rho;
+            if (lam)
+                for (int j = 0; j < q; ++j) lam[(int64_t)j * n + x] += scale * m[x];
+            continue;
+        }
+        double nv[3];
+        if (!wall_normal(&L, n, link, x, nv)) continue;
+        equilibrium(&L, rho, u, feq);
+        double pi[3][3] = {{0}};
+        for (int i = 0; i < q; ++i)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) pi[a][b] += (g[i] - feq[i]) * L.e[i][a] * L.e[i][b];
+        double coef = -(1.0 - 1.0 / (2.0 * tau));
+        double tr[3], tn = 0.0, v[3], w2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            tr[a] = 0.0;
+            for (int b = 0; b < 3; ++b) tr[a] += coef * pi[a][b] * nv[b];
+            tn += tr[a] * nv[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+            v[a] = tr[a] - tn * nv[a];
+            w2 += v[a] * v[a];
+        }
+        double wss = sqrt(w2);
+        J += m[x] * wss;
+        if (wss == 0.0) continue;
+        /* explicit tau dependence of the factor (1 - 1/(2 tau)) */
+        jt += m[x] * wss * (1.0 / (2.0 * tau * tau)) / (1.0 - 1.0 / (2.0 * tau));
+        if (!lam) continue;
+        /* d wss / d f_j = coef [M_j - (A + B.(c_j - u)/rho)],
+         * M_i = (c_i.vh)(c_i.n), A = sum M_i feq_i/rho, B = sum M_i dfeq_i/du */
+        double vh[3] = {v[0] / wss, v[1] / wss, v[2] / wss};
+        double M[19], A = 0.0, B[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < q; ++i) {
+            double cv = L.e[i][0] * vh[0] + L.e[i][1] * vh[1] + L.e[i][2] * vh[2];
+            double cn = L.e[i][0] * nv[0] + L.e[i][1] * nv[1] + L.e[i][2] * nv[2];
+            double d[3];
+            M[i] = cv * cn;
+            A += M[i] * feq[i] / rho;
+            dfeq_du(&L, i, rho, u, d);
+            for (int c = 0; c < 3; ++c) B[c] += M[i] * d[c];
+        }
+        for (int j = 0; j < q; ++j) {
+            double s = A;
+            for (int c = 0; c < 3; ++c) s += B[c] * (L.e[j][c] - u[c]) / rho;
+            lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);
+        }
+    }
+    if (dtau) *dtau += scale * jt;
+    return J;
+}
+
+/*
+ * Objective and its gradient by storing every state (small inputs only).
+ * Runs nsteps steps from f0 at time t0; J = scale * sum over the states
+ * f(t), t0 <= t <= t0 + nsteps, with t_begin <= t < t_end, of sum_x m_x q(x,t).
+ * Outputs: J, dJ/dtau, per-iolet dJ/dmean, dJ/damp, dJ/dphase ([n_io] each,
+ * overwritten) and, if lam0 != NULL, dJ/df(t0) ([q][n]).
+ */
+int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                 int n_io, const double *rho_mean, const double *amp, const double *period,
+                 const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
+                 const double *m, int64_t t_begin, int64_t t_end, double scale, double *J_out,
+                 double *dtau_out, double *dmean, double *damp, double *dphase, double *lam0) {
+    const size_t sz = (size_t)q * (size_t)n;
+    double *states = (double *)malloc(sizeof(double) * sz * (size_t)(nsteps + 1));
+    double *la = (double *)malloc(sizeof(double) * (sz ? sz : 1));
+    double *lb = (double *)malloc(sizeof(double) * (sz ? sz : 1));
+    if (!states || !la || !lb) { free(states); free(la); free(lb); return -5; }
+    memcpy(states, f0, sizeof(double) * sz);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int r = orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t0 + s,
+                         states + sz * (size_t)s, states + sz * (size_t)(s + 1));
+        if (r) { free(states); free(la); free(lb); return r; }
+    }
+    double J = 0.0, dtau = 0.0;
+    for (int k = 0; k < n_io; ++k) dmean[k] = damp[k] = dphase[k] = 0.0;
+    /* lam(t0 + nsteps) = dj/df at the last state */
+    memset(lb, 0, sizeof(double) * sz);
+    int64_t T = t0 + nsteps;
+    if (T >= t_begin && T < t_end)
+        J += orc_objective(q, n, link, tau, kind, m, states + sz * (size_t)nsteps, scale, lb, &dtau);
+    for (int64_t s = nsteps - 1; s >= 0; --s) {
+        int64_t t = t0 + s;
+        orc_adjoint_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t,
+                         states + sz * (size_t)s, lb, la, &dtau, dmean, damp, dphase);
+        if (t >= t_begin && t < t_end)
+            J += orc_objective(q, n, link, tau, kind, m, states + sz * (size_t)s, scale, la, &dtau);
+        double *tmp = la; la = lb; lb = tmp;
+    }
+    *J_out = scale * J;
+    *dtau_out = dtau;
+    if (lam0) memcpy(lam0, lb, sizeof(double) * sz);
+    free(states);
+    free(la);
+    free(lb);
+    return 0;
+}

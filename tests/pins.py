@@ -296,3 +296,79 @@ ALL_FAST = [
     ("iolet_time19", lambda o: pin_iolet_time(o, 19)),
     ("slab19", lambda o: pin_slab_poiseuille(o, 19, 3000)),
 ]
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _adj_setup(o, q, seed=5):
+    g = G.random_mask((7, 6, 5), p=0.6, seed=seed, n_iolets=3)
+    nbr, link = o.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    rng = np.random.default_rng(seed)
+    f0 = o.rest_state(q, g.n) * (1.0 + 0.02 * (2.0 * rng.random((q, g.n)) - 1.0))
+    return g, nbr, link, f0, rng
+
+
+def pin_adjoint_dot_product(o, q, tau=0.7):
+    """One step: <(dF/df)^T w, v> equals <w, dF/df v> from central differences
+    of the forward step (F is smooth; h = 1e-6, error O(h^2))."""
+    g, nbr, link, f0, rng = _adj_setup(o, q)
+    w = rng.standard_normal(f0.shape)
+    v = rng.standard_normal(f0.shape)
+    lam, _, _, _, _ = o.adjoint_step(q, nbr, link, tau, f0, w, t=4, geom=g)
+    h = 1e-6
+    Fp = o.step(q, nbr, link, tau, f0 + h * v, t=4, geom=g)
+    Fm = o.step(q, nbr, link, tau, f0 - h * v, t=4, geom=g)
+    a, b = float(np.sum(lam * v)), float(np.sum(w * (Fp - Fm) / (2 * h)))
+    assert abs(a - b) <= 1e-8 * abs(b), (a, b)
+
+
+def pin_adjoint_gradient(o, q, kind, tau=0.7, nsteps=8):
+    """Adjoint gradient of a windowed objective against central finite
+    differences of the FP64 forward run: d/dtau and d/d(mean, amp, phase) of
+    every iolet (h = 1e-6), and d/df0 along a random direction (h = 1e-8 for
+    the wall-shear-stress objective, whose |s| is not smooth where s = 0)."""
+    g, nbr, link, f0, rng = _adj_setup(o, q)
+    m = (rng.random(g.n) < 0.5).astype(np.float64)
+    args = dict(kind=kind, m=m, t_begin=3, t_end=nsteps + 1, scale=0.25)
+    rho, _, wss = o.macros(q, link, tau, f0)
+    q0 = o.objective(q, link, tau, kind, m, f0)
+    assert abs(q0 - float(np.sum(m * (wss if kind == 0 else rho)))) <= 1e-13 * abs(q0)
+    r = o.gradient(q, nbr, link, tau, f0, nsteps, geom=g, want_lam0=True, **args)
+    J = o.objective_run(q, nbr, link, tau, f0, nsteps, geom=g, **args)
+    assert abs(r["J"] - J) <= 1e-13 * abs(J)
+    h = 1e-6
+
+    def fd(**kw):
+        io = dict(rho_mean=g.rho_mean.copy(), amp=g.amp.copy(), period=g.period.copy(),
+                  phase=g.phase.copy())
+        t_ = kw.pop("tau", 0.0)
+        key, k = kw.get("key"), kw.get("k")
+        if key:
+            io[key][k] += h
+        Jp = o.objective_run(q, nbr, link, tau + t_ * h, f0, nsteps, **io, **args)
+        if key:
+            io[key][k] -= 2 * h
+        Jm = o.objective_run(q, nbr, link, tau - t_ * h, f0, nsteps, **io, **args)
+        return (Jp - Jm) / (2 * h)
+
+    scale = max(abs(r["dtau"]), 1e-30)
+    assert abs(r["dtau"] - fd(tau=1.0)) <= 1e-5 * scale, ("dtau", r["dtau"])
+    for k in range(g.n_iolets):
+        for nm, key in (("dmean", "rho_mean"), ("damp", "amp"), ("dphase", "phase")):
+            ref = fd(key=key, k=k)
+            tol = 1e-5 * max(abs(ref), 1e-3 * abs(r["dmean"][k]))
+            assert abs(r[nm][k] - ref) <= tol, (nm, k, r[nm][k], ref)
+    v = rng.standard_normal(f0.shape)
+    hv = 1e-8 if kind == 0 else 1e-6
+    Jp = o.objective_run(q, nbr, link, tau, f0 + hv * v, nsteps, geom=g, **args)
+    Jm = o.objective_run(q, nbr, link, tau, f0 - hv * v, nsteps, geom=g, **args)
+    ref = (Jp - Jm) / (2 * hv)
+    got = float(np.sum(r["lam0"] * v))
+    assert abs(got - ref) <= 1e-5 * abs(ref), ("lam0", got, ref)
+
+
+ALL_FAST += [
+    ("adjoint_dot19", lambda o: pin_adjoint_dot_product(o, 19)),
+    ("adjoint_wss15", lambda o: pin_adjoint_gradient(o, 15, 0)),
+    ("adjoint_density19", lambda o: pin_adjoint_gradient(o, 19, 1)),
+]

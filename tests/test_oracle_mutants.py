@@ -15,12 +15,27 @@ MUTANTS = {
                              "fout[(int64_t)i * n + x] = fs;"),
     "relaxation_tau_times": ("(g[i] - feq[i]) / tau", "(g[i] - feq[i]) * tau"),
     "collision_sign": ("g[i] - (g[i] - feq[i]) / tau", "g[i] + (g[i] - feq[i]) / tau"),
-    "iolet_time_plus_one": ("iolet_rho(k, t, rho_mean", "iolet_rho(k, t + 1, rho_mean"),
+    "iolet_time_plus_one": ("double feq_k[19];\n                double rk = iolet_rho(k, t, rho_mean",
+                            "double feq_k[19];\n                double rk = iolet_rho(k, t + 1, rho_mean"),
+    "adj_iolet_time": ("double rk = iolet_rho(k, t, rho_mean, amp, period, phase);\n                double feq_k[19], d[3];",
+                       "double rk = iolet_rho(k, t + 1, rho_mean, amp, period, phase);\n                double feq_k[19], d[3];"),
     "iolet_wrong_direction": ("= feq_k[L.opp[i]];", "= feq_k[i];"),
-    "wss_factor": ("-(1.0 - 1.0 / (2.0 * tau))", "-(1.0 - 1.0 / tau)"),
+    "wss_factor": ("double coef = -(1.0 - 1.0 / (2.0 * tau));\n        double tr[3];",
+                   "double coef = -(1.0 - 1.0 / tau);\n        double tr[3];"),
+    "objective_wss_factor": ("double coef = -(1.0 - 1.0 / (2.0 * tau));\n        double tr[3], tn",
+                             "double coef = -(1.0 - 1.0 / tau);\n        double tr[3], tn"),
     "velocity_not_divided": ("u[a] = j[a] / r;", "u[a] = j[a];"),
     "no_periodic_wrap": ("if (periodic && periodic[a] > 0) y[a] =", "if (0) y[a] ="),
     "iolet_id_off_by_one": ("(k >= 0 ? 2 + k : 1)", "(k >= 0 ? 1 + k : 1)"),
+    "adj_relaxation_sign": ("(1.0 - om) * ls[j]", "(1.0 + om) * ls[j]"),
+    "adj_dfeq_du_coeff": ("9.0 * cu * L->e[i][a]", "4.5 * cu * L->e[i][a]"),
+    "adj_drho_k_scale": ("feq_k[o] / rk;", "feq_k[o];"),
+    "adj_phase_cos": ("dphase[k] += drk * amp[k] * cos(arg);", "dphase[k] += drk * amp[k] * sin(arg);"),
+    "adj_tau_power": ("(g[i] - feq[i]) / (tau * tau);", "(g[i] - feq[i]) / tau;"),
+    "adj_wall_lambda": ("ls[i] = lam_next[(int64_t)L.opp[i] * n + x];", "ls[i] = lam_next[(int64_t)i * n + x];"),
+    "adj_velocity_term": ("double dj = (L.e[j][c] - u[c]) / rho;", "double dj = L.e[j][c] / rho;"),
+    "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
+                  "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }
 
 

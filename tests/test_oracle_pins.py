@@ -74,3 +74,14 @@ def test_empty_geometry(o):
     f = o.run(19, nbr, link, 0.8, np.zeros((19, 0)), 3)
     assert f.shape == (19, 0)
     assert o.mass(f) == 0.0
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_adjoint_dot_product(o, q):
+    pins.pin_adjoint_dot_product(o, q)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_adjoint_gradient_vs_central_differences(o, q, kind):
+    pins.pin_adjoint_gradient(o, q, kind)
