@@ -166,6 +166,23 @@ lbm_status lbm_mass(lbm_ctx *ctx, double *out);
 /* Populations f(t) as float64 [q][n], caller order (host memory).  Sync. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
 
+/* Same result as lbm_get_populations, for callers that cannot let the
+ * library call cudaMalloc or cudaFree (device memory owned by their own pool
+ * allocator, or a fixed memory budget; cudaFree would also synchronise the
+ * whole device).  The paper has no counterpart: this is a memory-management
+ * variant of the call above.  The float64 staging buffer is a static device
+ * array of 2^20 values (8 MiB, held by every GPU that loads the library until
+ * the process exits); q * n above 2^20 is rejected with LBM_ERR_ARG.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with the context's device made current for the lookup); make that first
+ * call before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (several contexts on different streams, or several
+ * threads) race on it and must be serialised by the caller.  Every call
+ * overwrites the first q * n values before reading them, so nothing needs
+ * clearing between calls.  Synchronous. */
+lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host);
+
 /* Replace the state by f (float64 [q][n], caller order, host memory),
  * rounded to the storage format.  Does not change t.  Synchronous. */
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host);

@@ -547,6 +547,35 @@ HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
     return LBM_OK;
 }
 
+HGB_API lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host) {
+    if (!ctx || (!f_host && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    const size_t count = (size_t)ctx->q * (size_t)ctx->n;
+    if (count > noalloc_max_values()) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "lbm_get_populations_noalloc: q*n = %zu values exceeds the static scratch of "
+                 "%zu float64 values; use lbm_get_populations",
+                 count, noalloc_max_values());
+        return fail(ctx, LBM_ERR_ARG, msg);
+    }
+    if (count == 0) return LBM_OK;
+    // the scratch address is per device: look it up with the context's device current
+    cudaPointerAttributes at{};
+    CK(ctx, cudaPointerGetAttributes(&at, ctx->f_cur));
+    int prev = 0;
+    CK(ctx, cudaGetDevice(&prev));
+    if (prev != at.device) CK(ctx, cudaSetDevice(at.device));
+    double *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e == cudaSuccess) e = launch_gather_f64(ctx->L, ctx->f_cur, scratch, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f_host, scratch, count * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (prev != at.device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_get_populations_noalloc");
+    return LBM_OK;
+}
+
 HGB_API lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
     *bytes = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage);

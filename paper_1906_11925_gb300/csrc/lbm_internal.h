@@ -65,6 +65,12 @@ cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out,
 // stored state from float64 [q][n] caller order (inverse of the gather).
 cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f,
                                cudaStream_t s);
+// Static float64 scratch of lbm_get_populations_noalloc (lbm_noalloc.cu):
+// its capacity in values, and its device address on the current device
+// (looked up on the first call per device).
+size_t noalloc_max_values();
+cudaError_t noalloc_scratch(double **out);
+
 // stored state of the rest fluid (all deviations zero).
 cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s);
 

@@ -25,7 +25,8 @@ _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM"
 EXPORTED = (
     "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
     "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
-    "lbm_get_populations", "lbm_set_populations", "lbm_state_bytes", "lbm_get_state",
+    "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
+    "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
 )
 
@@ -76,6 +77,7 @@ def load_library(build_if_missing: bool = True):
         "lbm_macros": [P, P, P, P],
         "lbm_mass": [P, P],
         "lbm_get_populations": [P, P],
+        "lbm_get_populations_noalloc": [P, P],
         "lbm_set_populations": [P, P],
         "lbm_state_bytes": [P, P],
         "lbm_get_state": [P, P, C.c_size_t],
@@ -245,6 +247,13 @@ class Lattice:
     def get_populations(self) -> np.ndarray:
         f = np.empty((self.q, self.n), np.float64)
         self._ck(self._lib.lbm_get_populations(self._ctx, _p(f)))
+        return f
+
+    def get_populations_noalloc(self) -> np.ndarray:
+        """As get_populations, staged in the library's static device array
+        instead of a cudaMalloc buffer (q * n <= 2^20)."""
+        f = np.empty((self.q, self.n), np.float64)
+        self._ck(self._lib.lbm_get_populations_noalloc(self._ctx, _p(f)))
         return f
 
     def set_populations(self, f):
