@@ -198,6 +198,60 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
  * form (nbr, link: [q][n] host memory), for verification.  Synchronous. */
 lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link);
 
+/* ------------------------------------------------------------------ adjoint
+ * Gradients of a time-windowed objective by the discrete adjoint of the step
+ * (reverse mode), with binomial checkpointing of raw state snapshots.  Not in
+ * the paper, whose method is the forward solver only (Section 2); this is
+ * the differentiation of that solver. */
+enum { LBM_OBJ_WSS = 0, LBM_OBJ_DENSITY = 1 };
+
+/* J = scale * sum over the states f(t) with t_begin <= t < t_end (t counted
+ * like lbm_get_time) of sum_x weight[x] q(x, t); q is the wall shear stress
+ * of lbm_macros (LBM_OBJ_WSS) or the density (LBM_OBJ_DENSITY).  weight is
+ * host memory, float64 [n], caller order. */
+typedef struct {
+    int32_t kind;
+    const double *weight;
+    int64_t t_begin;
+    int64_t t_end;
+    double scale;
+} lbm_objective;
+
+/* Run nsteps steps from the current state f(t0) (t0 = the context's time),
+ * accumulate J over the window, and compute by the discrete adjoint
+ *   dJ_dtau, dJ_dmean[k], dJ_damp[k], dJ_dphase[k] (k < n_iolets; derivatives
+ *   with respect to the parameters of rho_k(t) = mean + amp sin(2 pi t /
+ *   period + phase); amp and phase give 0 for a constant iolet), and
+ *   dJ_df0 = dJ/df(t0), float64 [q][n] caller order.
+ * Every output pointer except J may be NULL.  Forward arithmetic is that of
+ * lbm_step (fp32 or fp16 storage), the adjoint state is float32, and every
+ * time accumulation (J and all derivatives) is float64; results are bitwise
+ * reproducible and do not depend on n_snap.  n_snap >= 1 device snapshots of
+ * the stored state are used (one holds f(t0)); the schedule is Griewank's
+ * binomial checkpointing, lbm_revolve_steps forward steps in total.  Device
+ * memory: (n_snap + 1) state buffers + 2 float32 adjoint buffers + small;
+ * LBM_ERR_NOMEM before any allocation if it does not fit.  On return the
+ * context holds f(t0 + nsteps) and its time is t0 + nsteps, as after
+ * lbm_step(nsteps).  Synchronous. */
+lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, int64_t nsteps,
+                              int32_t n_snap, double *J, double *dJ_dtau, double *dJ_dmean,
+                              double *dJ_damp, double *dJ_dphase, double *dJ_df0);
+
+/* Forward steps lbm_objective_grad takes for nsteps steps and n_snap
+ * snapshots: r nsteps - C(n_snap + r, n_snap + 1) + 1 with r the smallest
+ * integer such that C(n_snap + r, n_snap) >= nsteps (the final state is
+ * formed once more).  Host only. */
+lbm_status lbm_revolve_steps(int64_t nsteps, int32_t n_snap, int64_t *forward_steps);
+
+/* Forward and adjoint steps of the last lbm_objective_grad call. */
+lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps);
+
+/* Change tau (> 0.5) or the iolet schedules (same n_iolets) of a context,
+ * e.g. between objective evaluations; the state is unchanged. */
+lbm_status lbm_set_tau(lbm_ctx *ctx, double tau);
+lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *rho_mean,
+                          const double *amp, const double *period, const double *phase);
+
 /* Sizes: number of sites, padded plane length, and device bytes held. */
 lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_t *device_bytes);
 

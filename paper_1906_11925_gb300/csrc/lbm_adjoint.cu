@@ -1,0 +1,368 @@
+// Discrete adjoint (reverse mode) of the fused collide-and-stream step, for
+// gradients of time-windowed objectives with respect to the relaxation time
+// and the iolet density schedules.
+//
+// Forward step (see lbm_kernels.cu), written in push form for one site x:
+//   f*_i = (1 - w) f_i + w feq_i(rho, u),   w = 1/tau,
+//   fluid link i: f_i(x + c_i, t+1) = f*_i;  wall link i: f_opp(i)(x, t+1) = f*_i;
+//   iolet link i: f_opp(i)(x, t+1) = feq_opp(i)(rho_k(t), u).
+// With lam(t) = dJ/df(t), the adjoint of the post-collision population is
+//   lam*_i = lam_i(x + c_i, t+1) (fluid), lam_opp(i)(x, t+1) (wall), 0 (iolet),
+// and the adjoint step is
+//   lam_j(x, t) = (1 - w) lam*_j + w (a + b.(c_j - u)/rho) + g.(c_j - u)/rho
+//                 + dj_t/df_j,
+//   a = sum_i lam*_i feq_i/rho,  b = sum_i lam*_i dfeq_i/du,
+//   dfeq_i/du = w_i rho (3 c_i + 9 (c_i.u) c_i - 3 u),
+//   g = sum over iolet links of lam_opp(i)(x, t+1) dfeq_opp(i)(rho_k, u)/du.
+// Parameter derivatives of step t:
+//   dJ/dtau      += sum_i lam*_i (f_i - feq_i) / tau^2,
+//   dJ/drho_k(t) += sum over iolet-k links of lam_opp(i)(x, t+1) feq_opp(i)/rho_k,
+// chained to mean, amp and phase of rho_k(t) = mean + amp sin(2 pi t/T + phase).
+//
+// The adjoint state is kept in site form, lam[i][x] (float32), so the
+// kernel is a pull like the forward step: lam*_i at x is read from the site
+// that the forward table lists as the source of population opp(i) (the site
+// x + c_i), or from x itself for wall and iolet links.  Arithmetic is float32;
+// the time accumulation of J and of every derivative is float64:
+//   - J and dJ/dtau: one float64 pair per thread block, added to by the same
+//     block at every step (a fixed grid, so the summation order is fixed);
+//   - iolet derivatives: one float64 slot per (iolet site, direction) and
+//     parameter, owned by one thread; reduced per iolet at the end.
+// Nothing uses atomics, so gradients are bitwise reproducible.
+#include <cuda_fp16.h>
+
+#include "lattice.h"
+#include "lbm_internal.h"
+
+namespace hemelb_gb300 {
+namespace {
+
+constexpr int kBlock = 256;
+
+template <bool HALF>
+struct AdjLoad;
+template <>
+struct AdjLoad<false> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+};
+template <>
+struct AdjLoad<true> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const __half *p, float inv) {
+        return __half2float(__ldg(p)) * inv;
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum in a fixed order; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double *part) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    v = threadIdx.x < kBlock / 32 ? part[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+template <int Q>
+__device__ __forceinline__ float cdot(int i, float ux, float uy, float uz) {
+    return cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
+          const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
+          const AdjObjective obj, double *__restrict__ acc_block, double *__restrict__ io_acc) {
+    using R = AdjLoad<HALF>;
+    __shared__ double part[kBlock / 32];
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    const bool valid = x < L.n;
+    const unsigned np = (unsigned)L.npad;
+    double j_site = 0.0, dtau_site = 0.0;
+    if (valid) {
+        int s[Q];
+        float d[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+        d[0] = R::ld(P + x, L.inv_scale);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
+                                         : (unsigned)opp(i) * np + (unsigned)x;
+            d[i] = R::ld(P + e, L.inv_scale);
+        }
+        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            drho += d[i];
+            jx += cdir<Q>(i, 0) * d[i];
+            jy += cdir<Q>(i, 1) * d[i];
+            jz += cdir<Q>(i, 2) * d[i];
+        }
+        const float rho = L.rho0 + drho;
+        const float ir = 1.0f / rho;
+        const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+        const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+        // equilibrium deviations and non-equilibrium parts
+        float ne[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float cu = cdot<Q>(i, ux, uy, uz);
+            const float deq = (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
+            ne[i] = d[i] - deq;
+        }
+        // adjoint of the post-collision populations
+        float ls[Q];
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        ls[0] = lam_next ? lam_next[x] : 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int sp = s[opp(i)];  // link i of x: >= 0 -> site x + c_i
+            if (!lam_next) {
+                ls[i] = 0.f;
+            } else if (sp >= 0) {
+                ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
+            } else {
+                const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+                if (sp == -1) {
+                    ls[i] = lo;
+                } else {
+                    ls[i] = 0.f;
+                    const int k = -2 - sp;
+                    const int o = opp(i);
+                    const float rk = st.io.rho[k];
+                    const float cu = cdot<Q>(o, ux, uy, uz);
+                    const float wo = (float)wdir<Q>(o);
+                    const float drk = lo * wo * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
+                    const float gc = lo * wo * rk;
+                    gx += gc * (3.0f * cdir<Q>(o, 0) + 9.0f * cu * cdir<Q>(o, 0) - 3.0f * ux);
+                    gy += gc * (3.0f * cdir<Q>(o, 1) + 9.0f * cu * cdir<Q>(o, 1) - 3.0f * uy);
+                    gz += gc * (3.0f * cdir<Q>(o, 2) + 9.0f * cu * cdir<Q>(o, 2) - 3.0f * uz);
+                    const size_t slot = (size_t)(x - L.n_bulk) * (Q - 1) + (i - 1);
+                    const size_t plane = (size_t)(L.n - L.n_bulk) * (Q - 1);
+                    io_acc[slot] += (double)drk;
+                    io_acc[plane + slot] += (double)drk * st.dsin[k];
+                    io_acc[2 * plane + slot] += (double)drk * st.dacos[k];
+                }
+            }
+        }
+        float a = 0.f, bx = 0.f, by = 0.f, bz = 0.f, dt = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float cu = cdot<Q>(i, ux, uy, uz);
+            const float wl = (float)wdir<Q>(i) * ls[i];
+            a += wl * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
+            const float br = wl * rho;
+            bx += br * (3.0f * cdir<Q>(i, 0) + 9.0f * cu * cdir<Q>(i, 0) - 3.0f * ux);
+            by += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
+            bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
+            dt += ls[i] * ne[i];
+        }
+        dtau_site = (double)dt / ((double)L.tau * (double)L.tau);
+        const float om = L.omega, omc = 1.0f - L.omega;
+        float lam[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
+                        vz = (cdir<Q>(j, 2) - uz) * ir;
+            lam[j] = omc * ls[j] + om * (a + bx * vx + by * vy + bz * vz) + gx * vx + gy * vy + gz * vz;
+        }
+        // explicit objective terms of the state f(t)
+        if (obj.active) {
+            const double mx = obj.weight[x];
+            if (mx != 0.0) {
+                const float sm = (float)(obj.scale * mx);
+                if (obj.kind == 1) {
+                    j_site = mx * (double)rho;
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) lam[j] += sm;
+                } else {
+                    int wn0 = 0, wn1 = 0, wn2 = 0;
+#pragma unroll
+                    for (int i = 1; i < Q; ++i)
+                        if (s[i] == -1) {
+                            wn0 += cdir<Q>(i, 0);
+                            wn1 += cdir<Q>(i, 1);
+                            wn2 += cdir<Q>(i, 2);
+                        }
+                    const float nn2 = (float)(wn0 * wn0 + wn1 * wn1 + wn2 * wn2);
+                    if (nn2 > 0.f) {
+                        const float inn = 1.0f / sqrtf(nn2);
+                        const float n0 = wn0 * inn, n1 = wn1 * inn, n2 = wn2 * inn;
+                        float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+                        for (int i = 1; i < Q; ++i) {
+                            const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
+                            pxx += cx * cx * ne[i];
+                            pyy += cy * cy * ne[i];
+                            pzz += cz * cz * ne[i];
+                            pxy += cx * cy * ne[i];
+                            pxz += cx * cz * ne[i];
+                            pyz += cy * cz * ne[i];
+                        }
+                        const float coef = -(1.0f - 0.5f / L.tau);
+                        const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
+                        const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
+                        const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
+                        const float tn = t0 * n0 + t1 * n1 + t2 * n2;
+                        const float v0 = t0 - tn * n0, v1 = t1 - tn * n1, v2 = t2 - tn * n2;
+                        const float wss = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+                        j_site = mx * (double)wss;
+                        if (wss > 0.f) {
+                            const double ht = 0.5 / ((double)L.tau * (double)L.tau);
+                            dtau_site += obj.scale * mx * (double)wss * ht / (1.0 - 0.5 / (double)L.tau);
+                            const float iv = 1.0f / wss;
+                            const float h0 = v0 * iv, h1 = v1 * iv, h2 = v2 * iv;
+                            float M[Q];
+                            float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) {
+                                const float cv = cdot<Q>(i, h0, h1, h2);
+                                const float cn = cdot<Q>(i, n0, n1, n2);
+                                M[i] = cv * cn;
+                                const float cu = cdot<Q>(i, ux, uy, uz);
+                                const float wm = (float)wdir<Q>(i) * M[i];
+                                A += wm * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
+                                const float br = wm * rho;
+                                Bx += br * (3.0f * cdir<Q>(i, 0) + 9.0f * cu * cdir<Q>(i, 0) - 3.0f * ux);
+                                By += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
+                                Bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
+                            }
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) {
+                                const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
+                                            vz = (cdir<Q>(j, 2) - uz) * ir;
+                                lam[j] += sm * coef * (M[j] - (A + Bx * vx + By * vy + Bz * vz));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) lam_out[(unsigned)j * np + (unsigned)x] = lam[j];
+    }
+    const double bj = block_sum(j_site, part);
+    const double bt = block_sum(dtau_site, part);
+    if (threadIdx.x == 0) {
+        acc_block[2 * blockIdx.x] += bj;
+        acc_block[2 * blockIdx.x + 1] += bt;
+    }
+}
+
+// J and dJ/dtau: sum of the per-block accumulators in a fixed order
+__global__ void __launch_bounds__(kBlock)
+k_acc_final(const double *__restrict__ acc_block, int nblocks, double *__restrict__ out) {
+    __shared__ double part[kBlock / 32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += kBlock) {
+        a += acc_block[2 * i];
+        b += acc_block[2 * i + 1];
+    }
+    a = block_sum(a, part);
+    b = block_sum(b, part);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// per-iolet derivatives: block k sums, over the iolet sites and the
+// directions whose link is iolet k, the three accumulated parameters
+template <int Q>
+__global__ void __launch_bounds__(kBlock)
+k_io_final(const DevLattice L, const double *__restrict__ io_acc, double *__restrict__ out) {
+    __shared__ double part[kBlock / 32];
+    const int k = blockIdx.x;
+    const int nio = L.n - L.n_bulk;
+    const size_t plane = (size_t)nio * (Q - 1);
+    const unsigned np = (unsigned)L.npad;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (size_t e = threadIdx.x; e < plane; e += kBlock) {
+        const int xi = (int)(e / (Q - 1));
+        const int i = (int)(e % (Q - 1)) + 1;
+        const int x = L.n_bulk + xi;
+        // link i of x is iolet k when the table entry of population opp(i) is -2 - k
+        if (L.tab[(unsigned)(opp(i) - 1) * np + (unsigned)x] == -2 - k) {
+            s0 += io_acc[e];
+            s1 += io_acc[plane + e];
+            s2 += io_acc[2 * plane + e];
+        }
+    }
+    s0 = block_sum(s0, part);
+    s1 = block_sum(s1, part);
+    s2 = block_sum(s2, part);
+    if (threadIdx.x == 0) {
+        out[k] = s0;
+        out[L.n_iolets + k] = s1;
+        out[2 * L.n_iolets + k] = s2;
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kBlock)
+k_lam_to_caller(const DevLattice L, const float *__restrict__ lam, double *__restrict__ out) {
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    const int64_t xc = L.perm[x];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = (double)lam[(int64_t)i * L.npad + x];
+}
+
+template <int Q, bool HALF>
+cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
+                         const AdjStep &st, const AdjObjective &obj, double *acc_block,
+                         double *io_acc, cudaStream_t s) {
+    using T = typename AdjLoad<HALF>::T;
+    k_adjoint<Q, HALF><<<adjoint_blocks(L), kBlock, 0, s>>>(L, (const T *)P, lam_next, lam_out, st,
+                                                             obj, acc_block, io_acc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int adjoint_blocks(const DevLattice &L) { return (L.n + kBlock - 1) / kBlock; }
+
+cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
+                           const AdjStep &st, const AdjObjective &obj, double *acc_block,
+                           double *io_acc, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    if (L.q == 15)
+        return L.storage ? adjoint_impl<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
+                         : adjoint_impl<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+    return L.storage ? adjoint_impl<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
+                     : adjoint_impl<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+}
+
+cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,
+                                 double *out, cudaStream_t s) {
+    k_acc_final<<<1, kBlock, 0, s>>>(acc_block, adjoint_blocks(L), out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.n_iolets == 0) return e;
+    if (L.q == 15)
+        k_io_final<15><<<L.n_iolets, kBlock, 0, s>>>(L, io_acc, out + 2);
+    else
+        k_io_final<19><<<L.n_iolets, kBlock, 0, s>>>(L, io_acc, out + 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lam_to_caller(const DevLattice &L, const float *lam, double *out, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    const unsigned g = (unsigned)((L.n + kBlock - 1) / kBlock);
+    if (L.q == 15)
+        k_lam_to_caller<15><<<g, kBlock, 0, s>>>(L, lam, out);
+    else
+        k_lam_to_caller<19><<<g, kBlock, 0, s>>>(L, lam, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hemelb_gb300

@@ -43,6 +43,7 @@ struct lbm_ctx {
     size_t mass_series_cap = 0;
     size_t device_bytes = 0;
     std::vector<int32_t> perm_host;
+    int64_t last_fwd_steps = 0, last_adj_steps = 0;
     std::string err;
 };
 
@@ -321,6 +322,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         if (xyz[i] < -lim || xyz[i] >= lim) return fail(nullptr, LBM_ERR_ARG, "coordinate out of range");
 
     const int64_t npad = std::max<int64_t>(128, (n + 127) / 128 * 128);
+    if ((int64_t)q * npad >= (1LL << 31))
+        return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     const size_t eb = elem_bytes(p->storage);
     const size_t need = 2 * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
                         (size_t)(mass_blocks() + 8) * 8;
@@ -333,8 +336,11 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         return fail(nullptr, LBM_ERR_NOMEM, msg);
     }
 
-    // Morton order of the sites
+    // Internal order: sites without iolet links in Morton order, then the
+    // sites with an iolet link in Morton order (the kernel tests x >= n_bulk
+    // instead of scanning the table for iolet entries).
     std::vector<int32_t> perm((size_t)n);
+    int64_t n_bulk = 0;
     {
         int64_t lo[3] = {0, 0, 0};
         if (n > 0)
@@ -343,12 +349,15 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
                 for (int64_t x = 0; x < n; ++x) lo[a] = std::min<int64_t>(lo[a], xyz[3 * x + a]);
             }
         std::vector<std::pair<uint64_t, int32_t>> keys((size_t)n);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(+ : n_bulk)
         for (int64_t x = 0; x < n; ++x) {
             uint64_t k = spread3((uint64_t)(xyz[3 * x] - lo[0])) |
                          (spread3((uint64_t)(xyz[3 * x + 1] - lo[1])) << 1) |
                          (spread3((uint64_t)(xyz[3 * x + 2] - lo[2])) << 2);
-            keys[(size_t)x] = {k, (int32_t)x};
+            bool io_site = false;
+            for (int i = 1; i < q; ++i) io_site |= link[(int64_t)i * n + x] >= 2;
+            if (!io_site) ++n_bulk;
+            keys[(size_t)x] = {k | ((uint64_t)io_site << 63), (int32_t)x};
         }
         std::sort(keys.begin(), keys.end());
         for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = keys[(size_t)i].second;
@@ -406,6 +415,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.q = q;
     L.storage = p->storage;
     L.n = (int)n;
+    L.n_bulk = (int)n_bulk;
     L.npad = npad;
     L.omega = (float)(1.0 / p->tau);
     L.tau = (float)p->tau;
@@ -619,6 +629,296 @@ HGB_API lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link) {
             link[(int64_t)j * n + x] = (uint8_t)(s >= 0 ? 0 : -s);
         }
     }
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------- adjoint
+
+namespace {
+
+// beta(s, r) = C(s + r, s): the number of steps that s checkpoints (the
+// start state included) can reverse when each step is advanced at most r
+// times (Griewank, "Achieving logarithmic growth of temporal and spatial
+// complexity in reverse automatic differentiation", 1992).  Saturates.
+int64_t binom_beta(int64_t s, int64_t r) {
+    if (s < 0 || r < 0) return 0;
+    const int64_t k = std::min(s, r), n = s + r;
+    const int64_t cap = int64_t(1) << 62;
+    int64_t v = 1;
+    for (int64_t i = 1; i <= k; ++i) {
+        // v = C(n - k + i, i), exact at every step
+        const __int128 w = (__int128)v * (n - k + i) / i;
+        if (w > cap) return cap;
+        v = (int64_t)w;
+    }
+    return v;
+}
+
+// smallest r with beta(f + 1, r) >= l (f free slots plus the start state)
+int64_t revolve_reps(int64_t l, int64_t f) {
+    int64_t r = 0;
+    while (binom_beta(f + 1, r) < l) ++r;
+    return r;
+}
+
+// First checkpoint position for reversing l >= 2 steps with f >= 1 free
+// slots: the smallest m with m <= beta(s, r-1) (the left part, already
+// advanced once, is reversed with r-1 more advances) and l - m <= beta(s-1, r)
+// (the right part with one slot less), raised to beta(s, r-2) so that the
+// left part needs all its r-1 advances; s = f + 1.  With this split the
+// total number of forward steps equals r l - beta(f + 2, r - 1), the minimum.
+int64_t revolve_split(int64_t l, int64_t f) {
+    const int64_t s = f + 1, r = revolve_reps(l, f);
+    int64_t m = std::max<int64_t>({1, l - binom_beta(s - 1, r), binom_beta(s, r - 2)});
+    return std::min<int64_t>(m, l - 1);
+}
+
+int64_t revolve_steps(int64_t l, int64_t f) {
+    if (l <= 1) return 0;
+    if (f == 0) return l * (l - 1) / 2;
+    const int64_t m = revolve_split(l, f);
+    return m + revolve_steps(l - m, f - 1) + revolve_steps(m, f);
+}
+
+struct AdjointRun {
+    lbm_ctx *c;
+    std::vector<void *> slots;
+    std::vector<int> free_slots;
+    void *W[2] = {nullptr, nullptr};
+    float *lam[2] = {nullptr, nullptr};
+    int lc = 0;
+    double *acc_block = nullptr, *io_acc = nullptr;
+    const double *weight = nullptr;
+    int kind = 0;
+    double scale = 1.0;
+    int64_t t_begin = 0, t_end = 0, t0 = 0, T = 0;
+    bool terminal_done = false;
+    int64_t fwd_steps = 0, adj_steps = 0;
+
+    AdjObjective objective_at(int64_t t) const {
+        AdjObjective o{};
+        o.active = (t >= t_begin && t < t_end) ? 1 : 0;
+        o.kind = kind;
+        o.scale = scale;
+        o.weight = weight;
+        return o;
+    }
+    AdjStep adj_step(int64_t t) const {
+        AdjStep a{};
+        a.io = iolet_step(c, t);
+        for (int k = 0; k < c->n_iolets; ++k) {
+            if (c->io_period[k] != 0.0) {
+                const double arg = 2.0 * M_PI * (double)t / c->io_period[k] + c->io_phase[k];
+                a.dsin[k] = std::sin(arg);
+                a.dacos[k] = c->io_amp[k] != 0.0 ? c->io_amp[k] * std::cos(arg) : 0.0;
+            }
+        }
+        return a;
+    }
+    cudaError_t step(const void *in, void *out, int64_t t) {
+        ++fwd_steps;
+        return launch_step(c->L, in, out, iolet_step(c, t), nullptr, c->stream);
+    }
+    // m steps from the state src of time a; the result lands in dst
+    cudaError_t advance(const void *src, int64_t a, int64_t m, void *dst) {
+        const void *in = src;
+        const bool dst_is_work = dst == W[0] || dst == W[1];
+        void *other = dst == W[0] ? W[1] : W[0];
+        for (int64_t k = 0; k < m; ++k) {
+            void *out;
+            if (k == m - 1) out = dst;
+            else if (dst_is_work) out = ((m - 1 - k) % 2 == 0) ? dst : other;
+            else out = W[k & 1];
+            cudaError_t e = step(in, out, a + k);
+            if (e != cudaSuccess) return e;
+            in = out;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t adjoint(const void *state, const float *next, float *out, int64_t t) {
+        return launch_adjoint(c->L, state, next, out, adj_step(t), objective_at(t), acc_block, io_acc,
+                              c->stream);
+    }
+    // adjoint of step k (state of time k in `state`); the first call also
+    // forms f(T) in the context's buffer and the terminal adjoint lam(T)
+    cudaError_t adjoint_at(int64_t k, const void *state) {
+        cudaError_t e;
+        if (!terminal_done) {
+            if ((e = step(state, c->f_cur, T - 1)) != cudaSuccess) return e;
+            if ((e = adjoint(c->f_cur, nullptr, lam[lc], T)) != cudaSuccess) return e;
+            terminal_done = true;
+        }
+        if ((e = adjoint(state, lam[lc], lam[1 - lc], k)) != cudaSuccess) return e;
+        lc = 1 - lc;
+        ++adj_steps;
+        return cudaSuccess;
+    }
+    // reverse the steps a .. b-1, the state of time a being in sa, with f free slots
+    cudaError_t reverse(int64_t a, int64_t b, void *sa, int64_t f) {
+        cudaError_t e;
+        if (b - a == 1) return adjoint_at(a, sa);
+        if (f == 0) {
+            for (int64_t k = b - 1; k > a; --k) {
+                if ((e = advance(sa, a, k - a, W[0])) != cudaSuccess) return e;
+                if ((e = adjoint_at(k, W[0])) != cudaSuccess) return e;
+            }
+            return adjoint_at(a, sa);
+        }
+        const int64_t m = revolve_split(b - a, f);
+        const int slot = free_slots.back();
+        free_slots.pop_back();
+        void *sm = slots[(size_t)slot];
+        if ((e = advance(sa, a, m, sm)) != cudaSuccess) return e;
+        if ((e = reverse(a + m, b, sm, f - 1)) != cudaSuccess) return e;
+        free_slots.push_back(slot);
+        return reverse(a, a + m, sa, f);
+    }
+};
+
+}  // namespace
+
+HGB_API lbm_status lbm_revolve_steps(int64_t nsteps, int32_t n_snap, int64_t *forward_steps) {
+    if (nsteps < 0 || n_snap < 1 || !forward_steps)
+        return fail(nullptr, LBM_ERR_ARG, "need nsteps >= 0, n_snap >= 1, forward_steps");
+    *forward_steps = nsteps == 0 ? 0 : revolve_steps(nsteps, n_snap - 1) + 1;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_tau(lbm_ctx *ctx, double tau) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(ctx, LBM_ERR_ARG, "tau must be finite and > 0.5");
+    ctx->tau = tau;
+    ctx->L.omega = (float)(1.0 / tau);
+    ctx->L.tau = (float)tau;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *rho_mean,
+                                  const double *amp, const double *period, const double *phase) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (n_iolets != ctx->n_iolets) return fail(ctx, LBM_ERR_ARG, "n_iolets differs from the context's");
+    lbm_params p{};
+    p.q = ctx->q;
+    p.storage = ctx->storage;
+    p.tau = ctx->tau;
+    p.rho0 = ctx->rho0;
+    p.fp16_scale_log2 = ctx->scale_log2;
+    p.n_iolets = n_iolets;
+    p.rho_mean = rho_mean;
+    p.amp = amp;
+    p.period = period;
+    p.phase = phase;
+    lbm_status st = validate_params(&p);
+    if (st != LBM_OK) return fail(ctx, st, g_err);
+    for (int k = 0; k < n_iolets; ++k) {
+        ctx->io_mean[k] = rho_mean[k];
+        ctx->io_amp[k] = amp[k];
+        ctx->io_period[k] = period[k];
+        ctx->io_phase[k] = phase[k];
+    }
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, int64_t nsteps,
+                                      int32_t n_snap, double *J, double *dJ_dtau, double *dJ_dmean,
+                                      double *dJ_damp, double *dJ_dphase, double *dJ_df0) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!obj || (obj->kind != LBM_OBJ_WSS && obj->kind != LBM_OBJ_DENSITY))
+        return fail(ctx, LBM_ERR_ARG, "objective kind must be LBM_OBJ_WSS or LBM_OBJ_DENSITY");
+    if (ctx->n > 0 && !obj->weight) return fail(ctx, LBM_ERR_ARG, "objective weight is NULL");
+    if (!std::isfinite(obj->scale)) return fail(ctx, LBM_ERR_ARG, "objective scale is not finite");
+    if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
+    if (!J) return fail(ctx, LBM_ERR_ARG, "J is NULL");
+    const int q = ctx->q, K = ctx->n_iolets;
+    const int64_t n = ctx->n, npad = ctx->npad;
+    const size_t sbytes = (size_t)q * npad * elem_bytes(ctx->storage);
+    const int64_t nblk = std::max(1, adjoint_blocks(ctx->L));
+    const int64_t nio = n - ctx->L.n_bulk;
+    const size_t need = (size_t)(n_snap + 1) * sbytes + 2 * (size_t)q * npad * 4 + (size_t)npad * 8 +
+                        (size_t)nblk * 16 + 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8 +
+                        (size_t)(2 + 3 * K) * 8 + (dJ_df0 ? (size_t)q * n * 8 : 0);
+    size_t free_b = 0, total_b = 0;
+    CK(ctx, cudaMemGetInfo(&free_b, &total_b));
+    if (need + (64u << 20) > free_b) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "adjoint needs %zu bytes of device memory (%d snapshots), %zu free",
+                 need, n_snap, free_b);
+        return fail(ctx, LBM_ERR_NOMEM, msg);
+    }
+    AdjointRun R;
+    R.c = ctx;
+    R.kind = obj->kind == LBM_OBJ_WSS ? 0 : 1;
+    R.scale = obj->scale;
+    R.t_begin = obj->t_begin;
+    R.t_end = obj->t_end;
+    R.t0 = ctx->t;
+    R.T = ctx->t + nsteps;
+    std::vector<void *> owned;
+    double *weight_dev = nullptr, *out_dev = nullptr, *lam0_dev = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t b) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(p, b ? b : 16);
+        if (e == cudaSuccess) owned.push_back(*p);
+    };
+    R.slots.resize((size_t)n_snap);
+    for (int i = 0; i < n_snap; ++i) alloc(&R.slots[(size_t)i], sbytes);
+    alloc(&R.W[1], sbytes);
+    R.W[0] = ctx->f_nxt;
+    alloc((void **)&R.lam[0], (size_t)q * npad * 4);
+    alloc((void **)&R.lam[1], (size_t)q * npad * 4);
+    alloc((void **)&weight_dev, (size_t)npad * 8);
+    alloc((void **)&R.acc_block, (size_t)nblk * 16);
+    alloc((void **)&R.io_acc, 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8);
+    alloc((void **)&out_dev, (size_t)(2 + 3 * K) * 8);
+    if (dJ_df0) alloc((void **)&lam0_dev, (size_t)q * std::max<int64_t>(n, 1) * 8);
+    std::vector<double> wint((size_t)npad, 0.0);
+    for (int64_t xi = 0; xi < n; ++xi) wint[(size_t)xi] = obj->weight[ctx->perm_host[(size_t)xi]];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(weight_dev, wint.data(), wint.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.acc_block, 0, (size_t)nblk * 16, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(R.io_acc, 0, 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out_dev, 0, (size_t)(2 + 3 * K) * 8, ctx->stream);
+    R.weight = weight_dev;
+    for (int i = n_snap - 1; i >= 1; --i) R.free_slots.push_back(i);
+    if (e == cudaSuccess) {
+        if (nsteps == 0) {
+            e = R.adjoint(ctx->f_cur, nullptr, R.lam[0], R.t0);
+            R.lc = 0;
+        } else {
+            e = cudaMemcpyAsync(R.slots[0], ctx->f_cur, sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e == cudaSuccess) e = R.reverse(R.t0, R.T, R.slots[0], n_snap - 1);
+        }
+    }
+    if (e == cudaSuccess) e = launch_adjoint_final(ctx->L, R.acc_block, R.io_acc, out_dev, ctx->stream);
+    if (e == cudaSuccess && dJ_df0) e = launch_lam_to_caller(ctx->L, R.lam[R.lc], lam0_dev, ctx->stream);
+    std::vector<double> out((size_t)(2 + 3 * K), 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.data(), out_dev, out.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && dJ_df0 && n > 0)
+        e = cudaMemcpyAsync(dJ_df0, lam0_dev, (size_t)q * n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    for (void *p : owned) cudaFree(p);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_objective_grad");
+    ctx->t = R.T;
+    ctx->last_fwd_steps = R.fwd_steps;
+    ctx->last_adj_steps = R.adj_steps;
+    *J = obj->scale * out[0];
+    if (dJ_dtau) *dJ_dtau = out[1];
+    for (int k = 0; k < K; ++k) {
+        if (dJ_dmean) dJ_dmean[k] = out[(size_t)(2 + k)];
+        if (dJ_damp) dJ_damp[k] = out[(size_t)(2 + K + k)];
+        if (dJ_dphase) dJ_dphase[k] = out[(size_t)(2 + 2 * K + k)];
+    }
+    if (!std::isfinite(*J)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite objective");
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (forward_steps) *forward_steps = ctx->last_fwd_steps;
+    if (adjoint_steps) *adjoint_steps = ctx->last_adj_steps;
     return LBM_OK;
 }
 

@@ -21,7 +21,8 @@ struct IoletStep {
 
 // Device-side description of one simulation, passed by value to launchers.
 //
-// Kernel table layout (internal Morton order, planes of length npad):
+// Kernel table layout (internal order: Morton order of the sites without
+// iolet links, then Morton order of those with one; planes of length npad):
 //   tab[(i - 1) * npad + x], i = 1..q-1, is the pull source of population i
 //   at site x: >= 0 -> population i of site tab (the site x - c_i);
 //   -1 -> wall link opp(i) at x (read own slot opp(i), halfway bounce-back);
@@ -33,6 +34,7 @@ struct DevLattice {
     int q;
     int storage;     // 0 fp32, 1 fp16
     int n;           // sites
+    int n_bulk;      // sites [0, n_bulk) have no iolet link; [n_bulk, n) have
     int64_t npad;    // plane length (multiple of 128)
     float omega;     // 1 / tau
     float tau;
@@ -65,6 +67,40 @@ cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out,
 // stored state from float64 [q][n] caller order (inverse of the gather).
 cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f,
                                cudaStream_t s);
+// ------------------------------------------------------------ adjoint
+// Per-step inputs of the adjoint kernel: the iolet densities of step t and
+// the chain factors d rho_k / d amp = sin(2 pi t / T_k + phase_k) and
+// d rho_k / d phase = amp_k cos(...), both 0 for a constant iolet.
+struct AdjStep {
+    IoletStep io;
+    double dsin[kMaxIolets];
+    double dacos[kMaxIolets];
+};
+
+// Objective term of one state f(t): when active, J += sum_x weight[x] q(x),
+// q = wall shear stress (kind 0) or density (kind 1); weight is float64 in
+// internal order; its state derivative enters the adjoint scaled by scale.
+struct AdjObjective {
+    int active;
+    int kind;
+    double scale;
+    const double *weight;
+};
+
+int adjoint_blocks(const DevLattice &L);
+// lam_out = adjoint of step t at the state P = stored state of time t, from
+// lam_next = lam(t+1) (null for the terminal state); accumulates J and
+// dJ/dtau into acc_block[2 * blocks] and iolet derivatives into io_acc
+// [3][n - n_bulk][q - 1].
+cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
+                           const AdjStep &st, const AdjObjective &obj, double *acc_block,
+                           double *io_acc, cudaStream_t s);
+// out[0] = sum J, out[1] = dJ/dtau, out[2 + c * K + k] = iolet derivative c of iolet k
+cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,
+                                 double *out, cudaStream_t s);
+// float32 site-form adjoint -> float64 [q][n] caller order
+cudaError_t launch_lam_to_caller(const DevLattice &L, const float *lam, double *out, cudaStream_t s);
+
 // Static float64 scratch of lbm_get_populations_noalloc (lbm_noalloc.cu):
 // its capacity in values, and its device address on the current device
 // (looked up on the first call per device).

@@ -13,7 +13,7 @@
 // the slot P_i(x) that the pull of step t reads; this is the post-collision
 // population f*_i(x, t-1) for fluid and wall links, and for an iolet link the
 // equilibrium population already evaluated at the iolet density.  Reading
-// the slots through the table (lattice_internal.h) is a permutation, so the
+// the slots through the table (lbm_internal.h) is a permutation, so the
 // gather reproduces f(t) exactly.  Values are deviations d = f - w_i rho0,
 // in float or in IEEE half scaled by 2^S.
 //
@@ -31,6 +31,14 @@ namespace hemelb_gb300 {
 namespace {
 
 constexpr int kBlock = 256;
+// resident blocks per SM requested from the register allocator for the step
+// kernel (fp32 storage, fp16 storage)
+#ifndef HGB_STEP_MINB_FP32
+#define HGB_STEP_MINB_FP32 4
+#endif
+#ifndef HGB_STEP_MINB_FP16
+#define HGB_STEP_MINB_FP16 5
+#endif
 constexpr int kMassBlocks = 2 * 152;  // fixed grid: deterministic reduction order
 
 template <bool HALF>
@@ -129,31 +137,98 @@ __device__ __forceinline__ float deq(int i, float drho, float rho, const Moments
     return (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - m.usq15));
 }
 
+// Raw stored values for the step kernel: fp16 values stay in their scaled
+// units (d * 2^S) through the whole update, so that no load or store pays a
+// multiplication; only rho and u are formed in real units.
+template <bool HALF>
+struct Raw;
+
+template <>
+struct Raw<false> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+};
+
+template <>
+struct Raw<true> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v) {
+        __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
+    }
+};
+
+// Fused pull collide-and-stream of one time step, one site per thread.
+//   gather   d_i = slot(i, x) through the table (coalesced table reads,
+//            gathered population reads, Morton order keeps them local);
+//   collide  LBGK toward the deviation equilibrium, written per opposite
+//            pair (i, opp i): with cu = c_i.u the equilibrium deviations are
+//            sym +- asym, sym = w (drho + rho (4.5 cu^2 - 1.5 u^2)),
+//            asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i;
+//   iolets   sites with iolet links come last in the internal order
+//            (x >= n_bulk); there the slot read back through an iolet link
+//            is overwritten by the equilibrium at the iolet density;
+//   stream   q coalesced streaming stores at the site's own slots.
+// All slot offsets are 32-bit (q * npad < 2^31 is checked at create).
 template <int Q, bool HALF>
-__global__ void __launch_bounds__(kBlock)
-k_step(const DevLattice L, const typename Store<HALF>::T *__restrict__ fin,
-       typename Store<HALF>::T *__restrict__ fout, const IoletStep io,
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
+k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
+       typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
        const double *__restrict__ rho_io) {
-    using S = Store<HALF>;
+    using R = Raw<HALF>;
     const int x = blockIdx.x * kBlock + threadIdx.x;
     if (x >= L.n) return;
-    float d[Q];
-    int wn[3];
-    const int minc = gather<Q, HALF, true>(L, fin, x, d, wn);
-    const Moments m = moments<Q>(d, L.rho0);
-    float out[Q];
+    const unsigned np = (unsigned)L.npad;
+    int s[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i] = d[i] - L.omega * (d[i] - deq<Q>(i, m.drho, m.rho, m));
-    if (minc <= -2) {
-        // iolet links (rare): the slot read back through an iolet link at the
-        // next step holds the equilibrium at the iolet density and the site's
-        // current velocity.
-        const int64_t np = L.npad;
+    for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    float d[Q];
+    d[0] = R::ld(fin + x);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
+                                     : (unsigned)opp(i) * np + (unsigned)x;
+        d[i] = R::ld(fin + e);
+    }
+    // moments, in stored units
+    float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sum = d[i] + d[i + 1], dif = d[i] - d[i + 1];
+        drs += sum;
+        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
+        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
+        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
+    }
+    const float rho = HALF ? fmaf(drs, L.inv_scale, L.rho0) : L.rho0 + drs;
+    const float ir = (HALF ? L.inv_scale : 1.0f) / rho;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
+    const float om = L.omega, omc = 1.0f - L.omega;
+    float out[Q];
+    {
+        const float w0 = (float)wdir<Q>(0);
+        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * usq15));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = (float)wdir<Q>(i);
+        const float cu = cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
+        const float t = fmaf(4.5f * cu, cu, -usq15);
+        const float sym = fmaf(om * w * rs, t, om * w * drs);
+        const float asym = (3.0f * om * w * rs) * cu;
+        out[i] = fmaf(omc, d[i], sym + asym);
+        out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
+    }
+    if (x >= L.n_bulk) {
+        // the slot read back through an iolet link at the next step holds the
+        // equilibrium at the iolet density and the site's current velocity
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const int s = L.tab[(int64_t)(i - 1) * np + x];
-            if (s <= -2) {
-                const int k = -2 - s;
+            if (s[i] <= -2) {
+                const int k = -2 - s[i];
                 float drk, rk;
                 if (rho_io) {
                     const double r = rho_io[k];
@@ -163,13 +238,17 @@ k_step(const DevLattice L, const typename Store<HALF>::T *__restrict__ fin,
                     drk = io.drho[k];
                     rk = io.rho[k];
                 }
-                out[opp(i)] = deq<Q>(i, drk, rk, m);
+                if (HALF) {
+                    drk *= L.scale;
+                    rk *= L.scale;
+                }
+                const float cu = cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
+                out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - usq15));
             }
         }
     }
-    const int64_t np = L.npad;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) S::store(fout + (int64_t)i * np + x, out[i], L.scale);
+    for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
 }
 
 template <int Q, bool HALF>
@@ -298,7 +377,7 @@ inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); 
 template <int Q, bool HALF>
 cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
                       const double *rho_io, cudaStream_t s) {
-    using T = typename Store<HALF>::T;
+    using T = typename Raw<HALF>::T;
     k_step<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
     return cudaGetLastError();
 }

@@ -28,7 +28,12 @@ EXPORTED = (
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
     "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
+    "lbm_objective_grad", "lbm_revolve_steps", "lbm_adjoint_counts", "lbm_set_tau",
+    "lbm_set_iolets",
 )
+
+OBJ_WSS = 0
+OBJ_DENSITY = 1
 
 
 class LbmError(RuntimeError):
@@ -36,6 +41,11 @@ class LbmError(RuntimeError):
         super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
         self.status = status
         self.name = _STATUS.get(status, str(status))
+
+
+class _Objective(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("weight", C.c_void_p), ("t_begin", C.c_int64),
+                ("t_end", C.c_int64), ("scale", C.c_double)]
 
 
 class _Params(C.Structure):
@@ -84,6 +94,11 @@ def load_library(build_if_missing: bool = True):
         "lbm_set_state": [P, P, C.c_size_t],
         "lbm_get_links": [P, P, P],
         "lbm_info": [P, P, P, P],
+        "lbm_objective_grad": [P, P, i64, i32, P, P, P, P, P, P],
+        "lbm_revolve_steps": [i64, i32, P],
+        "lbm_adjoint_counts": [P, P, P],
+        "lbm_set_tau": [P, C.c_double],
+        "lbm_set_iolets": [P, i32, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -120,6 +135,13 @@ def links_build(q: int, xyz, io_xyz=None, io_id=None, periodic=(0, 0, 0)):
     _check(lib.lbm_links_build(int(q), n, _p(xyz), io_xyz.shape[0], _p(io_xyz), _p(io_id),
                                _p(per), _p(nbr), _p(link)))
     return nbr, link
+
+
+def revolve_steps(nsteps: int, n_snap: int) -> int:
+    """Forward steps of a checkpointed gradient (``lbm_revolve_steps``)."""
+    out = C.c_int64()
+    _check(load_library().lbm_revolve_steps(int(nsteps), int(n_snap), C.byref(out)))
+    return out.value
 
 
 def _stream_handle(stream):
@@ -282,7 +304,114 @@ class Lattice:
         self._ck(self._lib.lbm_get_links(self._ctx, _p(nbr), _p(link)))
         return nbr, link
 
+    def set_tau(self, tau: float):
+        self._ck(self._lib.lbm_set_tau(self._ctx, float(tau)))
+        self.tau = float(tau)
+
+    def set_iolets(self, rho_mean, amp, period, phase):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho_mean, amp, period, phase)]
+        self._ck(self._lib.lbm_set_iolets(self._ctx, len(arrs[0]), *[_p(a) for a in arrs]))
+        self._io = arrs
+
+    def objective_grad(self, kind: int, weight, nsteps: int, t_begin: int, t_end: int,
+                       scale: float = 1.0, n_snap: int = 16, want_df0: bool = False):
+        """Run nsteps steps, return J and its gradient by the checkpointed
+        discrete adjoint (``lbm_objective_grad``): a dict with J, dtau and
+        per-iolet dmean, damp, dphase (float64), and dJ/df0 if asked."""
+        w = np.ascontiguousarray(weight, dtype=np.float64)
+        if w.shape != (self.n,):
+            raise ValueError("weight must be [n]")
+        obj = _Objective(int(kind), w.ctypes.data if self.n else None, int(t_begin), int(t_end),
+                         float(scale))
+        K = max(self.n_iolets, 1)
+        J, dt = C.c_double(), C.c_double()
+        dm, da, dp = np.zeros(K), np.zeros(K), np.zeros(K)
+        df0 = np.zeros((self.q, self.n)) if want_df0 else None
+        self._ck(self._lib.lbm_objective_grad(self._ctx, C.byref(obj), int(nsteps), int(n_snap),
+                                              C.byref(J), C.byref(dt), _p(dm), _p(da), _p(dp),
+                                              _p(df0)))
+        out = dict(J=J.value, dtau=dt.value, dmean=dm[:self.n_iolets], damp=da[:self.n_iolets],
+                   dphase=dp[:self.n_iolets])
+        if want_df0:
+            out["df0"] = df0
+        return out
+
+    def adjoint_counts(self):
+        f, a = C.c_int64(), C.c_int64()
+        self._ck(self._lib.lbm_adjoint_counts(self._ctx, C.byref(f), C.byref(a)))
+        return f.value, a.value
+
     def info(self):
         n, npad, b = C.c_int64(), C.c_int64(), C.c_size_t()
         self._ck(self._lib.lbm_info(self._ctx, C.byref(n), C.byref(npad), C.byref(b)))
         return dict(n=n.value, npad=npad.value, device_bytes=b.value)
+
+
+class HemeObjective:
+    """Time-windowed objective J(tau, mean, amp, phase) of a simulation as a
+    differentiable torch function.
+
+    ``HemeObjective(lattice, kind, weight, nsteps, t_begin, t_end, ...)``
+    snapshots the lattice's current state; calling it with torch tensors
+    (tau: scalar; mean, amp, phase: [K]) restarts from that state, runs the
+    forward solver and the discrete adjoint (``lbm_objective_grad``) in one
+    go, and returns J as a float64 tensor whose ``backward`` delivers the
+    adjoint gradient.  The solver state is not part of the graph.
+    """
+
+    def __init__(self, lattice: "Lattice", kind: int, weight, nsteps: int, t_begin: int,
+                 t_end: int, scale: float = 1.0, n_snap: int = 16, period=None):
+        self.L = lattice
+        self.kind, self.nsteps = int(kind), int(nsteps)
+        self.t_begin, self.t_end, self.scale, self.n_snap = int(t_begin), int(t_end), float(scale), int(n_snap)
+        self.weight = np.ascontiguousarray(weight, dtype=np.float64)
+        self.period = np.ascontiguousarray(lattice._io[2] if period is None else period, dtype=np.float64)
+        self.state0 = lattice.get_state()
+        self.t0 = lattice.time
+
+    def evaluate(self, tau: float, mean, amp, phase):
+        L = self.L
+        L.set_state(self.state0)
+        L.set_time(self.t0)
+        L.set_tau(tau)
+        L.set_iolets(mean, amp, self.period, phase)
+        return L.objective_grad(self.kind, self.weight, self.nsteps, self.t_begin, self.t_end,
+                                self.scale, self.n_snap)
+
+    def __call__(self, tau, mean, amp, phase):
+        import torch
+
+        fn = _objective_function()
+        return fn.apply(self, tau, mean, amp, phase)
+
+
+_FN = None
+
+
+def _objective_function():
+    global _FN
+    if _FN is not None:
+        return _FN
+    import torch
+
+    class _HemeObjectiveFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, obj, tau, mean, amp, phase):
+            r = obj.evaluate(float(tau.detach().cpu()), mean.detach().cpu().numpy(),
+                             amp.detach().cpu().numpy(), phase.detach().cpu().numpy())
+            f64 = dict(dtype=torch.float64)
+            ctx.grads = (torch.tensor(r["dtau"], **f64), torch.as_tensor(r["dmean"], **f64),
+                         torch.as_tensor(r["damp"], **f64), torch.as_tensor(r["dphase"], **f64))
+            ctx.devs = [t.device for t in (tau, mean, amp, phase)]
+            ctx.dtypes = [t.dtype for t in (tau, mean, amp, phase)]
+            return torch.tensor(r["J"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            out = [None]
+            for g, dev, dt in zip(ctx.grads, ctx.devs, ctx.dtypes):
+                out.append((gJ.to(torch.float64) * g).to(device=dev, dtype=dt))
+            return tuple(out)
+
+    _FN = _HemeObjectiveFn
+    return _FN

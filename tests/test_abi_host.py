@@ -107,3 +107,37 @@ def test_create_rejects_bad_table(corrupt):
     with pytest.raises(lbm.LbmError) as ei:
         _create(15, g, nbr=nbr, link=link)
     assert ei.value.name == "LBM_ERR_TABLE"
+
+
+def _dp_steps(l, f, memo={}):
+    """Brute-force minimum number of forward steps to reverse l steps with f
+    free snapshot slots (the start state stored), by dynamic programming."""
+    if l <= 1:
+        return 0
+    if f == 0:
+        return l * (l - 1) // 2
+    key = (l, f)
+    if key not in memo:
+        memo[key] = min(m + _dp_steps(l - m, f - 1) + _dp_steps(m, f) for m in range(1, l))
+    return memo[key]
+
+
+def test_revolve_schedule_is_optimal():
+    """lbm_revolve_steps (the schedule lbm_objective_grad executes) equals the
+    brute-force optimum plus the one extra step that forms the final state,
+    and Griewank's closed form r l - C(s + r, s + 1) (s = n_snap)."""
+    from math import comb
+    for l in range(1, 70):
+        for s in range(1, 8):
+            got = lbm.revolve_steps(l, s)
+            want = 0 if l == 0 else _dp_steps(l, s - 1) + 1
+            assert got == want, (l, s, got, want)
+            if l > 1:
+                r = 0
+                while comb(s + r, s) < l:
+                    r += 1
+                assert got == r * l - comb(s + r, s + 1) + 1, (l, s)
+    # the stated adjoint workloads: 4000 steps / 64 snapshots, 3000 steps / 40
+    assert lbm.revolve_steps(4000, 64) == 9789 + 1
+    assert lbm.revolve_steps(3000, 40) == 3 * 3000 - comb(43, 41) + 1
+    assert lbm.revolve_steps(5, 6) == 5
