@@ -248,10 +248,56 @@ def run_ours(args):
         L.close()
         return dict(seconds=dt, h2d=inner * K * 8, d2h=8)
 
+    def adjoint_leg():
+        # gradient of the inlet-to-outlet pressure drop, averaged over every
+        # state of the run, with respect to tau and the mean density of all 33
+        # iolets: fp16-deviation forward, float32 adjoint, float64 accumulation,
+        # binomial checkpointing with as many snapshots as fit in 150 GB
+        L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP16, rho_mean=g.rho_mean,
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+        nsteps = args.adjoint_steps
+        inlet = (link == 2).any(axis=0)
+        outlet = (link >= 3).any(axis=0)
+        weight = np.where(inlet, 1.0 / (3.0 * max(inlet.sum(), 1)), 0.0) - np.where(
+            outlet, 1.0 / (3.0 * max(outlet.sum(), 1)), 0.0)
+        state_bytes = L.state_bytes()
+        n_snap = int(max(2, min(nsteps + 1, (150 << 30) // state_bytes - 1)))
+        t0 = L.time
+        L.objective_grad(lbm.OBJ_DENSITY, weight, 20, t0, t0 + 21, n_snap=min(n_snap, 21))  # warm-up
+        t0 = L.time
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        r = L.objective_grad(lbm.OBJ_DENSITY, weight, nsteps, t0, t0 + nsteps + 1,
+                             scale=1.0 / (nsteps + 1), n_snap=n_snap)
+        wall = time.perf_counter() - w0
+        fw, ad = L.adjoint_counts()
+        sweep = L.adjoint_sweep_ms()
+        # forward step time of this context, for the adjoint/forward ratio
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.step(100)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = a.elapsed_time(b) / 100
+        L.close()
+        adj_ms = (sweep - fw * fwd_ms) / ad
+        return {"objective": "pressure drop, inlet-adjacent minus outlet-adjacent mean c_s^2 rho, "
+                             "averaged over all states",
+                "storage": "fp16 forward, fp32 adjoint, fp64 accumulation", "steps": nsteps,
+                "snapshots": n_snap, "snapshot_gb": round(n_snap * state_bytes / 2 ** 30, 1),
+                "forward_steps": fw, "adjoint_steps": ad, "sweep_ms": round(sweep, 2),
+                "wall_s": round(wall, 3), "fwd_step_ms": round(fwd_ms, 4),
+                "adjoint_step_ms": round(adj_ms, 4),
+                "adjoint_step_vs_fwd": round(adj_ms / fwd_ms, 3),
+                "gradient_vs_forward_run": round(sweep / (nsteps * fwd_ms), 3),
+                "J": r["J"], "dJ_dtau": r["dtau"], "n_gradients": 1 + len(r["dmean"]),
+                "finite": bool(np.isfinite(r["dtau"]) and np.all(np.isfinite(r["dmean"])))}
+
     sampler = ClockSampler(local_rank) if rank == 0 else None
     r32 = device_leg(lbm.STORE_FP32, sampler)
     r16 = device_leg(lbm.STORE_FP16) if "fp16" in legs else None
     e2e = e2e_leg() if "e2e" in legs else None
+    adj = adjoint_leg() if "adjoint" in legs else None
 
     n_lb = args.steps * inner
     value = world * metrics.msups(g.n, n_lb, r32["total_ms"] / 1e3)
@@ -301,6 +347,7 @@ def run_ours(args):
             "value": round(world * metrics.msups(g.n, n_lb, e2e["seconds"]), 2),
             "unit": "MSUPS", "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
             "path": "lbm_step_driven (host iolet densities, pinned) + lbm_mass (host)"},
+        "adjoint": adj,
         "gpu_launches": args.steps * (inner + 1 + 2),
         "clocks": r32["clocks"],
         "finite": r32["finite"] and (r16 is None or r16["finite"]),
@@ -380,8 +427,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
-    ap.add_argument("--legs", default="fp32,fp16,e2e",
-                    help="comma list of fp32 (always run), fp16, e2e")
+    ap.add_argument("--legs", default="fp32,fp16,e2e,adjoint",
+                    help="comma list of fp32 (always run), fp16, e2e, adjoint")
+    ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

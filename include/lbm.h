@@ -229,8 +229,10 @@ typedef struct {
  * reproducible and do not depend on n_snap.  n_snap >= 1 device snapshots of
  * the stored state are used (one holds f(t0)); the schedule is Griewank's
  * binomial checkpointing, lbm_revolve_steps forward steps in total.  Device
- * memory: (n_snap + 1) state buffers + 2 float32 adjoint buffers + small;
- * LBM_ERR_NOMEM before any allocation if it does not fit.  On return the
+ * memory: (n_snap + 1) state buffers + 2 float32 adjoint buffers + small,
+ * allocated on the first call and kept in the context for later calls
+ * (lbm_release_workspace); LBM_ERR_NOMEM before allocating if the part not
+ * yet held does not fit.  On return the
  * context holds f(t0 + nsteps) and its time is t0 + nsteps, as after
  * lbm_step(nsteps).  Synchronous. */
 lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, int64_t nsteps,
@@ -243,8 +245,15 @@ lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, int64_t ns
  * formed once more).  Host only. */
 lbm_status lbm_revolve_steps(int64_t nsteps, int32_t n_snap, int64_t *forward_steps);
 
-/* Forward and adjoint steps of the last lbm_objective_grad call. */
-lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps);
+/* Forward and adjoint steps of the last lbm_objective_grad call, and the
+ * device time of its forward-and-adjoint sweep (CUDA events on the context's
+ * stream, allocation and read-back excluded).  Any output may be NULL. */
+lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps,
+                              double *sweep_ms);
+
+/* lbm_objective_grad keeps its device workspace (snapshots, adjoint buffers)
+ * in the context for later calls; this frees it (lbm_destroy does too). */
+lbm_status lbm_release_workspace(lbm_ctx *ctx);
 
 /* Change tau (> 0.5) or the iolet schedules (same n_iolets) of a context,
  * e.g. between objective evaluations; the state is unchanged. */

@@ -63,6 +63,9 @@ def _bind(path: str):
     lib.orc_objective.restype = f64
     lib.orc_gradient.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, i32, P,
                                  i64, i64, f64, P, P, P, P, P, P]
+    lib.orc_objective_run.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, i32, P,
+                                      i64, i64, f64]
+    lib.orc_objective_run.restype = f64
     lib.orc_num_threads.restype = i32
     lib.orc_set_threads.argtypes = [i32]
     return lib
@@ -243,16 +246,16 @@ class Oracle:
 
     def objective_run(self, q, nbr, link, tau, f0, nsteps, kind, m, t_begin, t_end, scale=1.0,
                       t0=0, geom=None, **io):
-        """J alone, by running forward (used for finite differences)."""
-        f = np.array(f0, dtype=np.float64, copy=True)
-        J = 0.0
-        for s in range(nsteps + 1):
-            t = t0 + s
-            if t_begin <= t < t_end:
-                J += self.objective(q, link, tau, kind, m, f)
-            if s < nsteps:
-                f = self.step(q, nbr, link, tau, f, t=t, geom=geom, **io)
-        return scale * J
+        """J alone, by running forward in C (used for finite differences)."""
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        f0 = _c(f0, np.float64)
+        m = _c(m, np.float64)
+        I = _Iolets(geom, **io)
+        return float(self.lib.orc_objective_run(q, f0.shape[1], _p(nbr), _p(link), float(tau), I.k,
+                                                _p(I.mean), _p(I.amp), _p(I.period), _p(I.phase),
+                                                int(t0), int(nsteps), _p(f0), int(kind), _p(m),
+                                                int(t_begin), int(t_end), float(scale)))
 
     def rest_state(self, q: int, n: int, rho0: float = 1.0) -> np.ndarray:
         """f_i = w_i rho0 at every site (fluid at rest)."""

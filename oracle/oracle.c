@@ -466,6 +466,8 @@ double orc_objective(int q, int64_t n, const uint8_t *link, double tau, int kind
     lattice_t L;
     if (get_lattice(q, &L)) return NAN;
     double J = 0.0, jt = 0.0;
+    /* without a gradient the site loop is independent: sum it in parallel */
+#pragma omp parallel for schedule(static) reduction(+ : J, jt) if (lam == NULL)
     for (int64_t x = 0; x < n; ++x) {
         if (m[x] == 0.0) continue;
         double g[19], feq[19], rho, u[3];
@@ -569,4 +571,29 @@ int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, doub
     free(la);
     free(lb);
     return 0;
+}
+
+/* Objective alone, by running forward from f0 at time t0 for nsteps steps
+ * (for finite differences at sizes where storing every state is too big). */
+double orc_objective_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                         int n_io, const double *rho_mean, const double *amp, const double *period,
+                         const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
+                         const double *m, int64_t t_begin, int64_t t_end, double scale) {
+    const size_t sz = (size_t)q * (size_t)n;
+    double *a = (double *)malloc(sizeof(double) * (sz ? sz : 1));
+    double *b = (double *)malloc(sizeof(double) * (sz ? sz : 1));
+    if (!a || !b) { free(a); free(b); return NAN; }
+    memcpy(a, f0, sizeof(double) * sz);
+    double J = 0.0;
+    for (int64_t s = 0; s <= nsteps; ++s) {
+        int64_t t = t0 + s;
+        if (t >= t_begin && t < t_end) J += orc_objective(q, n, link, tau, kind, m, a, scale, NULL, NULL);
+        if (s < nsteps) {
+            orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t, a, b);
+            double *tmp = a; a = b; b = tmp;
+        }
+    }
+    free(a);
+    free(b);
+    return scale * J;
 }

@@ -38,6 +38,14 @@ namespace hemelb_gb300 {
 namespace {
 
 constexpr int kBlock = 256;
+// resident blocks per SM requested from the register allocator for the
+// adjoint kernel without and with the wall-shear-stress objective term
+#ifndef HGB_ADJ_MINB
+#define HGB_ADJ_MINB 4
+#endif
+#ifndef HGB_ADJ_MINB_WSS
+#define HGB_ADJ_MINB_WSS 2
+#endif
 
 template <bool HALF>
 struct AdjLoad;
@@ -77,66 +85,140 @@ __device__ __forceinline__ float cdot(int i, float ux, float uy, float uz) {
     return cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
 }
 
-template <int Q, bool HALF>
-__global__ void __launch_bounds__(kBlock)
+// Wall-shear-stress objective term at site x (only launched for steps in
+// the objective window): adds scale m d wss / d f_j to lam, returns m wss and
+// adds the explicit tau derivative to *dtau.
+template <int Q>
+__device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q], const float (&ne)[Q],
+                                           float rho, float ir, float ux, float uy, float uz,
+                                           float usq15, double mx, double scale, float (&lam)[Q],
+                                           double *dtau) {
+    int wn0 = 0, wn1 = 0, wn2 = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (s[i] == -1) {
+            wn0 += cdir<Q>(i, 0);
+            wn1 += cdir<Q>(i, 1);
+            wn2 += cdir<Q>(i, 2);
+        }
+    const float nn2 = (float)(wn0 * wn0 + wn1 * wn1 + wn2 * wn2);
+    if (nn2 == 0.f) return 0.0;
+    const float inn = 1.0f / sqrtf(nn2);
+    const float n0 = wn0 * inn, n1 = wn1 * inn, n2 = wn2 * inn;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
+        if (cx) pxx += ne[i];
+        if (cy) pyy += ne[i];
+        if (cz) pzz += ne[i];
+        if (cx * cy) pxy += (cx * cy) * ne[i];
+        if (cx * cz) pxz += (cx * cz) * ne[i];
+        if (cy * cz) pyz += (cy * cz) * ne[i];
+    }
+    const float coef = -(1.0f - 0.5f / L.tau);
+    const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
+    const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
+    const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
+    const float tn = t0 * n0 + t1 * n1 + t2 * n2;
+    const float v0 = t0 - tn * n0, v1 = t1 - tn * n1, v2 = t2 - tn * n2;
+    const float wss = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+    if (wss > 0.f) {
+        const double ht = 0.5 / ((double)L.tau * (double)L.tau);
+        *dtau += scale * mx * (double)wss * ht / (1.0 - 0.5 / (double)L.tau);
+        const float iv = 1.0f / wss;
+        const float h0 = v0 * iv, h1 = v1 * iv, h2 = v2 * iv;
+        float M[Q];
+        float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            M[i] = cdot<Q>(i, h0, h1, h2) * cdot<Q>(i, n0, n1, n2);
+            const float cu = cdot<Q>(i, ux, uy, uz);
+            const float wm = (float)wdir<Q>(i) * M[i];
+            A += wm * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
+            const float br = wm * rho;
+            Bx += br * (3.0f * cdir<Q>(i, 0) + 9.0f * cu * cdir<Q>(i, 0) - 3.0f * ux);
+            By += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
+            Bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
+        }
+        const float sc = (float)(scale * mx) * coef;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
+                        vz = (cdir<Q>(j, 2) - uz) * ir;
+            lam[j] += sc * (M[j] - (A + Bx * vx + By * vy + Bz * vz));
+        }
+    }
+    return mx * (double)wss;
+}
+
+// One adjoint step over the sites [x_begin, x_end): the bulk sites (no
+// iolet link, IO = false) or the iolet sites (IO = true).  WSS = the
+// wall-shear-stress objective term is active at this step.
+template <int Q, bool HALF, bool WSS, bool IO>
+__global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB)
 k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
-          const AdjObjective obj, double *__restrict__ acc_block, double *__restrict__ io_acc) {
+          const AdjObjective obj, int x_begin, int x_end, double *__restrict__ acc_block,
+          double *__restrict__ io_acc) {
     using R = AdjLoad<HALF>;
     __shared__ double part[kBlock / 32];
-    const int x = blockIdx.x * kBlock + threadIdx.x;
-    const bool valid = x < L.n;
+    const int x = x_begin + blockIdx.x * kBlock + threadIdx.x;
+    const bool valid = x < x_end;
     const unsigned np = (unsigned)L.npad;
     double j_site = 0.0, dtau_site = 0.0;
     if (valid) {
         int s[Q];
-        float d[Q];
+        float ne[Q];
 #pragma unroll
         for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
-        d[0] = R::ld(P + x, L.inv_scale);
+        ne[0] = R::ld(P + x, L.inv_scale);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
                                          : (unsigned)opp(i) * np + (unsigned)x;
-            d[i] = R::ld(P + e, L.inv_scale);
+            ne[i] = R::ld(P + e, L.inv_scale);
         }
-        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            drho += d[i];
-            jx += cdir<Q>(i, 0) * d[i];
-            jy += cdir<Q>(i, 1) * d[i];
-            jz += cdir<Q>(i, 2) * d[i];
+        for (int i = 1; i < Q; i += 2) {
+            const float sum = ne[i] + ne[i + 1], dif = ne[i] - ne[i + 1];
+            drho += sum;
+            if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
+            if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
+            if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
         }
         const float rho = L.rho0 + drho;
         const float ir = 1.0f / rho;
         const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
         const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        // equilibrium deviations and non-equilibrium parts
-        float ne[Q];
+        // non-equilibrium parts f_i - feq_i (in place of the deviations)
+        ne[0] -= (float)wdir<Q>(0) * (drho - rho * usq15);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = 1; i < Q; i += 2) {
+            const float w = (float)wdir<Q>(i);
             const float cu = cdot<Q>(i, ux, uy, uz);
-            const float deq = (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
-            ne[i] = d[i] - deq;
+            const float sym = w * (drho + rho * fmaf(4.5f * cu, cu, -usq15));
+            const float asym = 3.0f * w * rho * cu;
+            ne[i] -= sym + asym;
+            ne[i + 1] -= sym - asym;
         }
-        // adjoint of the post-collision populations
+        // adjoint of the post-collision populations, with the iolet terms
         float ls[Q];
         float gx = 0.f, gy = 0.f, gz = 0.f;
-        ls[0] = lam_next ? lam_next[x] : 0.f;
+        const bool has_next = lam_next != nullptr;
+        ls[0] = has_next ? lam_next[x] : 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const int sp = s[opp(i)];  // link i of x: >= 0 -> site x + c_i
-            if (!lam_next) {
-                ls[i] = 0.f;
-            } else if (sp >= 0) {
-                ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
-            } else {
-                const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
-                if (sp == -1) {
-                    ls[i] = lo;
+            const int sp = s[opp(i)];  // link i of x: >= 0 -> the site x + c_i
+            ls[i] = 0.f;
+            if (has_next) {
+                if (sp >= 0) {
+                    ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
+                } else if (!IO || sp == -1) {
+                    ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
                 } else {
-                    ls[i] = 0.f;
+                    const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
                     const int k = -2 - sp;
                     const int o = opp(i);
                     const float rk = st.io.rho[k];
@@ -155,107 +237,67 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
                 }
             }
         }
-        float a = 0.f, bx = 0.f, by = 0.f, bz = 0.f, dt = 0.f;
+        // a = sum_i lam*_i feq_i/rho, b = sum_i lam*_i dfeq_i/du (pairwise),
+        // dt = sum_i lam*_i (f_i - feq_i)
+        float a = (float)wdir<Q>(0) * ls[0] * (1.0f - usq15);
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        float sb = (float)wdir<Q>(0) * ls[0];
+        float dt = ls[0] * ne[0];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        for (int i = 1; i < Q; i += 2) {
+            const float w = (float)wdir<Q>(i);
             const float cu = cdot<Q>(i, ux, uy, uz);
-            const float wl = (float)wdir<Q>(i) * ls[i];
-            a += wl * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
-            const float br = wl * rho;
-            bx += br * (3.0f * cdir<Q>(i, 0) + 9.0f * cu * cdir<Q>(i, 0) - 3.0f * ux);
-            by += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
-            bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
-            dt += ls[i] * ne[i];
+            const float sum = ls[i] + ls[i + 1], dif = ls[i] - ls[i + 1];
+            a += w * fmaf(sum, 1.0f + fmaf(4.5f * cu, cu, -usq15), 3.0f * cu * dif);
+            const float bc = w * fmaf(9.0f * cu, sum, 3.0f * dif);
+            if (cdir<Q>(i, 0)) bx += cdir<Q>(i, 0) * bc;
+            if (cdir<Q>(i, 1)) by += cdir<Q>(i, 1) * bc;
+            if (cdir<Q>(i, 2)) bz += cdir<Q>(i, 2) * bc;
+            sb += w * sum;
+            dt = fmaf(ls[i], ne[i], dt);
+            dt = fmaf(ls[i + 1], ne[i + 1], dt);
         }
+        // b = rho (bc-sum - 3 u sb)
+        bx = rho * (bx - 3.0f * ux * sb);
+        by = rho * (by - 3.0f * uy * sb);
+        bz = rho * (bz - 3.0f * uz * sb);
         dtau_site = (double)dt / ((double)L.tau * (double)L.tau);
         const float om = L.omega, omc = 1.0f - L.omega;
+        // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
+        const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
+        const float base = om * a - (Bx * ux + By * uy + Bz * uz);
         float lam[Q];
+        lam[0] = fmaf(omc, ls[0], base);
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
-                        vz = (cdir<Q>(j, 2) - uz) * ir;
-            lam[j] = omc * ls[j] + om * (a + bx * vx + by * vy + bz * vz) + gx * vx + gy * vy + gz * vz;
+        for (int i = 1; i < Q; i += 2) {
+            const float bcj = cdot<Q>(i, Bx, By, Bz);
+            lam[i] = fmaf(omc, ls[i], base + bcj);
+            lam[i + 1] = fmaf(omc, ls[i + 1], base - bcj);
         }
         // explicit objective terms of the state f(t)
         if (obj.active) {
             const double mx = obj.weight[x];
             if (mx != 0.0) {
-                const float sm = (float)(obj.scale * mx);
-                if (obj.kind == 1) {
+                if (WSS) {
+                    j_site = wss_term<Q>(L, s, ne, rho, ir, ux, uy, uz, usq15, mx, obj.scale, lam,
+                                         &dtau_site);
+                } else if (obj.kind == 1) {
                     j_site = mx * (double)rho;
+                    const float sm = (float)(obj.scale * mx);
 #pragma unroll
                     for (int j = 0; j < Q; ++j) lam[j] += sm;
-                } else {
-                    int wn0 = 0, wn1 = 0, wn2 = 0;
-#pragma unroll
-                    for (int i = 1; i < Q; ++i)
-                        if (s[i] == -1) {
-                            wn0 += cdir<Q>(i, 0);
-                            wn1 += cdir<Q>(i, 1);
-                            wn2 += cdir<Q>(i, 2);
-                        }
-                    const float nn2 = (float)(wn0 * wn0 + wn1 * wn1 + wn2 * wn2);
-                    if (nn2 > 0.f) {
-                        const float inn = 1.0f / sqrtf(nn2);
-                        const float n0 = wn0 * inn, n1 = wn1 * inn, n2 = wn2 * inn;
-                        float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-#pragma unroll
-                        for (int i = 1; i < Q; ++i) {
-                            const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
-                            pxx += cx * cx * ne[i];
-                            pyy += cy * cy * ne[i];
-                            pzz += cz * cz * ne[i];
-                            pxy += cx * cy * ne[i];
-                            pxz += cx * cz * ne[i];
-                            pyz += cy * cz * ne[i];
-                        }
-                        const float coef = -(1.0f - 0.5f / L.tau);
-                        const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
-                        const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
-                        const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
-                        const float tn = t0 * n0 + t1 * n1 + t2 * n2;
-                        const float v0 = t0 - tn * n0, v1 = t1 - tn * n1, v2 = t2 - tn * n2;
-                        const float wss = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
-                        j_site = mx * (double)wss;
-                        if (wss > 0.f) {
-                            const double ht = 0.5 / ((double)L.tau * (double)L.tau);
-                            dtau_site += obj.scale * mx * (double)wss * ht / (1.0 - 0.5 / (double)L.tau);
-                            const float iv = 1.0f / wss;
-                            const float h0 = v0 * iv, h1 = v1 * iv, h2 = v2 * iv;
-                            float M[Q];
-                            float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) {
-                                const float cv = cdot<Q>(i, h0, h1, h2);
-                                const float cn = cdot<Q>(i, n0, n1, n2);
-                                M[i] = cv * cn;
-                                const float cu = cdot<Q>(i, ux, uy, uz);
-                                const float wm = (float)wdir<Q>(i) * M[i];
-                                A += wm * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
-                                const float br = wm * rho;
-                                Bx += br * (3.0f * cdir<Q>(i, 0) + 9.0f * cu * cdir<Q>(i, 0) - 3.0f * ux);
-                                By += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
-                                Bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
-                            }
-#pragma unroll
-                            for (int j = 0; j < Q; ++j) {
-                                const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
-                                            vz = (cdir<Q>(j, 2) - uz) * ir;
-                                lam[j] += sm * coef * (M[j] - (A + Bx * vx + By * vy + Bz * vz));
-                            }
-                        }
-                    }
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < Q; ++j) lam_out[(unsigned)j * np + (unsigned)x] = lam[j];
+        for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
     }
     const double bj = block_sum(j_site, part);
     const double bt = block_sum(dtau_site, part);
     if (threadIdx.x == 0) {
-        acc_block[2 * blockIdx.x] += bj;
-        acc_block[2 * blockIdx.x + 1] += bt;
+        const int b = (x_begin == 0 ? 0 : (L.n_bulk + kBlock - 1) / kBlock) + blockIdx.x;
+        acc_block[2 * b] += bj;
+        acc_block[2 * b + 1] += bt;
     }
 }
 
@@ -318,29 +360,46 @@ k_lam_to_caller(const DevLattice L, const float *__restrict__ lam, double *__res
     for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = (double)lam[(int64_t)i * L.npad + x];
 }
 
-template <int Q, bool HALF>
+template <int Q, bool HALF, bool WSS>
 cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                          const AdjStep &st, const AdjObjective &obj, double *acc_block,
                          double *io_acc, cudaStream_t s) {
     using T = typename AdjLoad<HALF>::T;
-    k_adjoint<Q, HALF><<<adjoint_blocks(L), kBlock, 0, s>>>(L, (const T *)P, lam_next, lam_out, st,
-                                                             obj, acc_block, io_acc);
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (nb > 0)
+        k_adjoint<Q, HALF, WSS, false><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+            L, (const T *)P, lam_next, lam_out, st, obj, 0, nb, acc_block, io_acc);
+    if (ni > 0)
+        k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+            L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);
     return cudaGetLastError();
+}
+
+template <int Q, bool HALF>
+cudaError_t adjoint_q(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
+                      const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
+                      cudaStream_t s) {
+    if (obj.active && obj.kind == 0)
+        return adjoint_impl<Q, HALF, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+    return adjoint_impl<Q, HALF, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
 }
 
 }  // namespace
 
-int adjoint_blocks(const DevLattice &L) { return (L.n + kBlock - 1) / kBlock; }
+// blocks of the bulk launch plus blocks of the iolet-site launch
+int adjoint_blocks(const DevLattice &L) {
+    return (L.n_bulk + kBlock - 1) / kBlock + (L.n - L.n_bulk + kBlock - 1) / kBlock;
+}
 
 cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                            const AdjStep &st, const AdjObjective &obj, double *acc_block,
                            double *io_acc, cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
     if (L.q == 15)
-        return L.storage ? adjoint_impl<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
-                         : adjoint_impl<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
-    return L.storage ? adjoint_impl<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
-                     : adjoint_impl<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+        return L.storage ? adjoint_q<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
+                         : adjoint_q<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+    return L.storage ? adjoint_q<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
+                     : adjoint_q<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
 }
 
 cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,

@@ -43,7 +43,18 @@ struct lbm_ctx {
     size_t mass_series_cap = 0;
     size_t device_bytes = 0;
     std::vector<int32_t> perm_host;
+    // adjoint workspace, kept between lbm_objective_grad calls (grown on demand)
+    struct Workspace {
+        std::vector<void *> slots;
+        void *W1 = nullptr;
+        float *lam[2] = {nullptr, nullptr};
+        double *weight = nullptr, *acc_block = nullptr, *io_acc = nullptr, *out = nullptr;
+        double *lam0 = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+    } ws;
     int64_t last_fwd_steps = 0, last_adj_steps = 0;
+    double last_sweep_ms = 0.0;
     std::string err;
 };
 
@@ -283,8 +294,27 @@ lbm_status validate_tables(int q, int n_iolets, int64_t n, const int32_t *nbr, c
     return LBM_OK;
 }
 
+void free_workspace(lbm_ctx *c) {
+    auto &w = c->ws;
+    for (void *p : w.slots) cudaFree(p);
+    w.slots.clear();
+    cudaFree(w.W1);
+    cudaFree(w.lam[0]);
+    cudaFree(w.lam[1]);
+    cudaFree(w.weight);
+    cudaFree(w.acc_block);
+    cudaFree(w.io_acc);
+    cudaFree(w.out);
+    cudaFree(w.lam0);
+    for (auto &e : w.ev)
+        if (e) cudaEventDestroy(e);
+    c->device_bytes -= w.bytes;
+    w = lbm_ctx::Workspace{};
+}
+
 void free_ctx(lbm_ctx *c) {
     if (!c) return;
+    free_workspace(c);
     cudaFree(c->f_cur);
     cudaFree(c->f_nxt);
     cudaFree(c->tab);
@@ -834,12 +864,13 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     const size_t sbytes = (size_t)q * npad * elem_bytes(ctx->storage);
     const int64_t nblk = std::max(1, adjoint_blocks(ctx->L));
     const int64_t nio = n - ctx->L.n_bulk;
-    const size_t need = (size_t)(n_snap + 1) * sbytes + 2 * (size_t)q * npad * 4 + (size_t)npad * 8 +
-                        (size_t)nblk * 16 + 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8 +
-                        (size_t)(2 + 3 * K) * 8 + (dJ_df0 ? (size_t)q * n * 8 : 0);
+    const size_t need_all = (size_t)(n_snap + 1) * sbytes + 2 * (size_t)q * npad * 4 + (size_t)npad * 8 +
+                            (size_t)nblk * 16 + 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8 +
+                            (size_t)(2 + 3 * LBM_MAX_IOLETS) * 8 + (dJ_df0 ? (size_t)q * n * 8 : 0);
+    const size_t need = need_all > ctx->ws.bytes ? need_all - ctx->ws.bytes : 0;
     size_t free_b = 0, total_b = 0;
     CK(ctx, cudaMemGetInfo(&free_b, &total_b));
-    if (need + (64u << 20) > free_b) {
+    if (need > 0 && need + (64u << 20) > free_b) {
         char msg[200];
         snprintf(msg, sizeof msg, "adjoint needs %zu bytes of device memory (%d snapshots), %zu free",
                  need, n_snap, free_b);
@@ -853,25 +884,48 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     R.t_end = obj->t_end;
     R.t0 = ctx->t;
     R.T = ctx->t + nsteps;
-    std::vector<void *> owned;
-    double *weight_dev = nullptr, *out_dev = nullptr, *lam0_dev = nullptr;
     cudaError_t e = cudaSuccess;
-    auto alloc = [&](void **p, size_t b) {
-        if (e != cudaSuccess) return;
+    auto &ws = ctx->ws;
+    auto grow = [&](void **p, size_t b) {
+        if (e != cudaSuccess || *p) return;
         e = cudaMalloc(p, b ? b : 16);
-        if (e == cudaSuccess) owned.push_back(*p);
+        if (e == cudaSuccess) {
+            ws.bytes += b;
+            ctx->device_bytes += b;
+        }
     };
-    R.slots.resize((size_t)n_snap);
-    for (int i = 0; i < n_snap; ++i) alloc(&R.slots[(size_t)i], sbytes);
-    alloc(&R.W[1], sbytes);
+    // the per-context sizes of everything but the snapshots never change
+    grow(&ws.W1, sbytes);
+    grow((void **)&ws.lam[0], (size_t)q * npad * 4);
+    grow((void **)&ws.lam[1], (size_t)q * npad * 4);
+    grow((void **)&ws.weight, (size_t)npad * 8);
+    grow((void **)&ws.acc_block, (size_t)nblk * 16);
+    grow((void **)&ws.io_acc, 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8);
+    grow((void **)&ws.out, (size_t)(2 + 3 * LBM_MAX_IOLETS) * 8);
+    if (dJ_df0) grow((void **)&ws.lam0, (size_t)q * std::max<int64_t>(n, 1) * 8);
+    while (e == cudaSuccess && ws.slots.size() < (size_t)n_snap) {
+        void *p = nullptr;
+        e = cudaMalloc(&p, sbytes);
+        if (e == cudaSuccess) {
+            ws.slots.push_back(p);
+            ws.bytes += sbytes;
+            ctx->device_bytes += sbytes;
+        }
+    }
+    for (auto &ev : ws.ev)
+        if (e == cudaSuccess && !ev) e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+        free_workspace(ctx);
+        return cuda_fail(ctx, e, "lbm_objective_grad workspace");
+    }
+    R.slots.assign(ws.slots.begin(), ws.slots.begin() + n_snap);
+    R.W[1] = ws.W1;
     R.W[0] = ctx->f_nxt;
-    alloc((void **)&R.lam[0], (size_t)q * npad * 4);
-    alloc((void **)&R.lam[1], (size_t)q * npad * 4);
-    alloc((void **)&weight_dev, (size_t)npad * 8);
-    alloc((void **)&R.acc_block, (size_t)nblk * 16);
-    alloc((void **)&R.io_acc, 3 * (size_t)std::max<int64_t>(nio, 1) * (q - 1) * 8);
-    alloc((void **)&out_dev, (size_t)(2 + 3 * K) * 8);
-    if (dJ_df0) alloc((void **)&lam0_dev, (size_t)q * std::max<int64_t>(n, 1) * 8);
+    R.lam[0] = ws.lam[0];
+    R.lam[1] = ws.lam[1];
+    R.acc_block = ws.acc_block;
+    R.io_acc = ws.io_acc;
+    double *weight_dev = ws.weight, *out_dev = ws.out, *lam0_dev = ws.lam0;
     std::vector<double> wint((size_t)npad, 0.0);
     for (int64_t xi = 0; xi < n; ++xi) wint[(size_t)xi] = obj->weight[ctx->perm_host[(size_t)xi]];
     if (e == cudaSuccess)
@@ -882,6 +936,7 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (e == cudaSuccess) e = cudaMemsetAsync(out_dev, 0, (size_t)(2 + 3 * K) * 8, ctx->stream);
     R.weight = weight_dev;
     for (int i = n_snap - 1; i >= 1; --i) R.free_slots.push_back(i);
+    if (e == cudaSuccess) e = cudaEventRecord(ws.ev[0], ctx->stream);
     if (e == cudaSuccess) {
         if (nsteps == 0) {
             e = R.adjoint(ctx->f_cur, nullptr, R.lam[0], R.t0);
@@ -891,6 +946,7 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
             if (e == cudaSuccess) e = R.reverse(R.t0, R.T, R.slots[0], n_snap - 1);
         }
     }
+    if (e == cudaSuccess) e = cudaEventRecord(ws.ev[1], ctx->stream);
     if (e == cudaSuccess) e = launch_adjoint_final(ctx->L, R.acc_block, R.io_acc, out_dev, ctx->stream);
     if (e == cudaSuccess && dJ_df0) e = launch_lam_to_caller(ctx->L, R.lam[R.lc], lam0_dev, ctx->stream);
     std::vector<double> out((size_t)(2 + 3 * K), 0.0);
@@ -899,8 +955,10 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (e == cudaSuccess && dJ_df0 && n > 0)
         e = cudaMemcpyAsync(dJ_df0, lam0_dev, (size_t)q * n * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    for (void *p : owned) cudaFree(p);
+    float sweep_ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&sweep_ms, ws.ev[0], ws.ev[1]);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_objective_grad");
+    ctx->last_sweep_ms = sweep_ms;
     ctx->t = R.T;
     ctx->last_fwd_steps = R.fwd_steps;
     ctx->last_adj_steps = R.adj_steps;
@@ -915,10 +973,19 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     return LBM_OK;
 }
 
-HGB_API lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps) {
+HGB_API lbm_status lbm_adjoint_counts(const lbm_ctx *ctx, int64_t *forward_steps, int64_t *adjoint_steps,
+                                      double *sweep_ms) {
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (forward_steps) *forward_steps = ctx->last_fwd_steps;
     if (adjoint_steps) *adjoint_steps = ctx->last_adj_steps;
+    if (sweep_ms) *sweep_ms = ctx->last_sweep_ms;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_release_workspace(lbm_ctx *ctx) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    free_workspace(ctx);
     return LBM_OK;
 }
 

@@ -28,8 +28,8 @@ EXPORTED = (
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
     "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
-    "lbm_objective_grad", "lbm_revolve_steps", "lbm_adjoint_counts", "lbm_set_tau",
-    "lbm_set_iolets",
+    "lbm_objective_grad", "lbm_revolve_steps", "lbm_adjoint_counts", "lbm_release_workspace",
+    "lbm_set_tau", "lbm_set_iolets",
 )
 
 OBJ_WSS = 0
@@ -96,7 +96,8 @@ def load_library(build_if_missing: bool = True):
         "lbm_info": [P, P, P, P],
         "lbm_objective_grad": [P, P, i64, i32, P, P, P, P, P, P],
         "lbm_revolve_steps": [i64, i32, P],
-        "lbm_adjoint_counts": [P, P, P],
+        "lbm_adjoint_counts": [P, P, P, P],
+        "lbm_release_workspace": [P],
         "lbm_set_tau": [P, C.c_double],
         "lbm_set_iolets": [P, i32, P, P, P, P],
     }
@@ -337,9 +338,19 @@ class Lattice:
         return out
 
     def adjoint_counts(self):
-        f, a = C.c_int64(), C.c_int64()
-        self._ck(self._lib.lbm_adjoint_counts(self._ctx, C.byref(f), C.byref(a)))
+        """(forward steps, adjoint steps) of the last objective_grad call."""
+        f, a, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._ck(self._lib.lbm_adjoint_counts(self._ctx, C.byref(f), C.byref(a), C.byref(ms)))
         return f.value, a.value
+
+    def adjoint_sweep_ms(self) -> float:
+        """Device time of the last objective_grad sweep (forward + adjoint)."""
+        ms = C.c_double()
+        self._ck(self._lib.lbm_adjoint_counts(self._ctx, None, None, C.byref(ms)))
+        return ms.value
+
+    def release_workspace(self):
+        self._ck(self._lib.lbm_release_workspace(self._ctx))
 
     def info(self):
         n, npad, b = C.c_int64(), C.c_int64(), C.c_size_t()
