@@ -183,9 +183,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def device_leg(storage, sampler=None):
+    def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL):
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
-                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream,
+                        streaming=streaming)
         rho = torch.empty(g.n, dtype=torch.float32, device="cuda")
         u = torch.empty(g.n, 3, dtype=torch.float32, device="cuda")
         wss = torch.empty(g.n, dtype=torch.float32, device="cuda")
@@ -262,6 +263,8 @@ def run_ours(args):
             outlet, 1.0 / (3.0 * max(outlet.sum(), 1)), 0.0)
         state_bytes = L.state_bytes()
         n_snap = int(max(2, min(nsteps + 1, (150 << 30) // state_bytes - 1)))
+        if args.adjoint_snapshots:
+            n_snap = args.adjoint_snapshots
         t0 = L.time
         L.objective_grad(lbm.OBJ_DENSITY, weight, 20, t0, t0 + 21, n_snap=min(n_snap, 21))  # warm-up
         t0 = L.time
@@ -296,6 +299,8 @@ def run_ours(args):
     sampler = ClockSampler(local_rank) if rank == 0 else None
     r32 = device_leg(lbm.STORE_FP32, sampler)
     r16 = device_leg(lbm.STORE_FP16) if "fp16" in legs else None
+    raa32 = device_leg(lbm.STORE_FP32, streaming=lbm.STREAM_AA) if "aa" in legs else None
+    raa16 = device_leg(lbm.STORE_FP16, streaming=lbm.STREAM_AA) if "aa" in legs else None
     e2e = e2e_leg() if "e2e" in legs else None
     adj = adjoint_leg() if "adjoint" in legs else None
 
@@ -303,8 +308,8 @@ def run_ours(args):
     value = world * metrics.msups(g.n, n_lb, r32["total_ms"] / 1e3)
     peak, peak_kind = read_peaks()
 
-    def roofline(res, storage):
-        bps = metrics.bytes_per_site_update(q, storage)
+    def roofline(res, storage, streaming="pull"):
+        bps = metrics.bytes_per_site_update(q, storage, streaming)
         per_launch_s = res["step_kernel_ms"] / 1e3 / n_lb
         achieved = bps * g.n / per_launch_s / 1e9
         return dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
@@ -347,10 +352,18 @@ def run_ours(args):
             "value": round(world * metrics.msups(g.n, n_lb, e2e["seconds"]), 2),
             "unit": "MSUPS", "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
             "path": "lbm_step_driven (host iolet densities, pinned) + lbm_mass (host)"},
+        "aa": None if not raa32 else {
+            "streaming": "AA pattern, one population buffer updated in place",
+            "fp32": {"value": round(world * metrics.msups(g.n, n_lb, raa32["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(raa32["total_ms"] / args.steps, 4),
+                     "roofline": roofline(raa32, "fp32", "aa")},
+            "fp16": {"value": round(world * metrics.msups(g.n, n_lb, raa16["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(raa16["total_ms"] / args.steps, 4),
+                     "roofline": roofline(raa16, "fp16", "aa")}},
         "adjoint": adj,
         "gpu_launches": args.steps * (inner + 1 + 2),
         "clocks": r32["clocks"],
-        "finite": r32["finite"] and (r16 is None or r16["finite"]),
+        "finite": all(r is None or r["finite"] for r in (r32, r16, raa32, raa16)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, g, nbr, link, q, tau,
@@ -427,9 +440,11 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
-    ap.add_argument("--legs", default="fp32,fp16,e2e,adjoint",
-                    help="comma list of fp32 (always run), fp16, e2e, adjoint")
+    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint",
+                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
+    ap.add_argument("--adjoint-snapshots", type=int, default=0,
+                    help="snapshot count (default: as many as fit in 150 GB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -65,6 +65,7 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1 };
+enum { LBM_STREAM_PULL = 0, LBM_STREAM_AA = 1 };
 enum { LBM_MAX_IOLETS = 64 };
 
 typedef struct lbm_ctx lbm_ctx; /* opaque */
@@ -80,7 +81,13 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              rest state, > 0.
  *   fp16_scale_log2  S in [0, 24]; ignored for LBM_STORE_FP32.
  *   n_iolets   K in [0, LBM_MAX_IOLETS]; the four arrays hold K doubles each
- *              (host memory, may be NULL when K = 0). */
+ *              (host memory, may be NULL when K = 0).
+ *   streaming  LBM_STREAM_PULL: two population buffers, every step gathers
+ *              through the neighbour table.  LBM_STREAM_AA: one buffer updated
+ *              in place by the AA pattern (even steps touch only a site's own
+ *              slots, odd steps gather and scatter through the table): half
+ *              the population memory and half the table traffic; identical
+ *              results (the same collision arithmetic). */
 typedef struct {
     int32_t q;
     int32_t storage;
@@ -92,6 +99,7 @@ typedef struct {
     const double *amp;
     const double *period;
     const double *phase;
+    int32_t streaming;
 } lbm_params;
 
 /* Neighbour-link table of a sparse site list (Section 2: every fluid site
@@ -188,8 +196,10 @@ lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host);
 
 /* Raw stored state (checkpoint/resume): lbm_state_bytes gives the size of
- * the stored population buffer; get/set copy it to/from host memory
- * byte-for-byte, so that a resumed run is bit-identical.  Synchronous. */
+ * the blob, the stored population buffer plus an 8-byte trailer holding the
+ * AA layout phase; get/set copy it to/from host memory byte-for-byte, so
+ * that a resumed run is bit-identical.  A blob is only valid for a context
+ * with the same q, n, storage and streaming.  Synchronous. */
 lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes);
 lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
 lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);

@@ -29,6 +29,8 @@ struct lbm_ctx {
     int scale_log2 = 0;
     double tau = 0, rho0 = 1;
     int n_iolets = 0;
+    int streaming = LBM_STREAM_PULL;
+    bool aa_swapped = false;  // AA mode: the buffer holds the swapped layout
     int64_t n = 0, npad = 0;
     int64_t t = 0;
     cudaStream_t stream = nullptr;
@@ -46,7 +48,7 @@ struct lbm_ctx {
     // adjoint workspace, kept between lbm_objective_grad calls (grown on demand)
     struct Workspace {
         std::vector<void *> slots;
-        void *W1 = nullptr;
+        void *W0 = nullptr, *W1 = nullptr, *final_buf = nullptr;  // W0, final: AA mode only
         float *lam[2] = {nullptr, nullptr};
         double *weight = nullptr, *acc_block = nullptr, *io_acc = nullptr, *out = nullptr;
         double *lam0 = nullptr;
@@ -166,6 +168,25 @@ IoletStep iolet_step(const lbm_ctx *c, int64_t t) {
     return s;
 }
 
+// Layout of the current state buffer.
+int cur_layout(const lbm_ctx *c) {
+    if (c->streaming == LBM_STREAM_PULL) return LAYOUT_PULL;
+    return c->aa_swapped ? LAYOUT_AA_SWAPPED : LAYOUT_NATURAL;
+}
+
+// One time step of the context's state (pull: two buffers; AA: in place).
+cudaError_t advance_one(lbm_ctx *c, const IoletStep &io, const double *rho_io) {
+    cudaError_t e;
+    if (c->streaming == LBM_STREAM_AA) {
+        e = launch_step_aa(c->L, c->f_cur, c->aa_swapped, io, rho_io, c->stream);
+        if (e == cudaSuccess) c->aa_swapped = !c->aa_swapped;
+    } else {
+        e = launch_step(c->L, c->f_cur, c->f_nxt, io, rho_io, c->stream);
+        if (e == cudaSuccess) std::swap(c->f_cur, c->f_nxt);
+    }
+    return e;
+}
+
 }  // namespace
 
 HGB_API const char *lbm_last_error(const lbm_ctx *ctx) {
@@ -243,6 +264,8 @@ lbm_status validate_params(const lbm_params *p) {
         return fail(nullptr, LBM_ERR_ARG, "rho0 must be finite and > 0");
     if (p->storage == LBM_STORE_FP16 && (p->fp16_scale_log2 < 0 || p->fp16_scale_log2 > 24))
         return fail(nullptr, LBM_ERR_ARG, "fp16_scale_log2 must be in [0, 24]");
+    if (p->streaming != LBM_STREAM_PULL && p->streaming != LBM_STREAM_AA)
+        return fail(nullptr, LBM_ERR_ARG, "streaming must be LBM_STREAM_PULL or LBM_STREAM_AA");
     if (p->n_iolets < 0 || p->n_iolets > LBM_MAX_IOLETS)
         return fail(nullptr, LBM_ERR_ARG, "n_iolets out of range");
     if (p->n_iolets > 0 && (!p->rho_mean || !p->amp || !p->period || !p->phase))
@@ -298,7 +321,9 @@ void free_workspace(lbm_ctx *c) {
     auto &w = c->ws;
     for (void *p : w.slots) cudaFree(p);
     w.slots.clear();
+    cudaFree(w.W0);
     cudaFree(w.W1);
+    cudaFree(w.final_buf);
     cudaFree(w.lam[0]);
     cudaFree(w.lam[1]);
     cudaFree(w.weight);
@@ -355,7 +380,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     if ((int64_t)q * npad >= (1LL << 31))
         return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     const size_t eb = elem_bytes(p->storage);
-    const size_t need = 2 * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
+    const size_t nbuf = p->streaming == LBM_STREAM_AA ? 1 : 2;
+    const size_t need = nbuf * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
                         (size_t)(mass_blocks() + 8) * 8;
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
@@ -414,6 +440,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     c->tau = p->tau;
     c->rho0 = p->rho0;
     c->n_iolets = p->n_iolets;
+    c->streaming = p->streaming;
     c->n = n;
     c->npad = npad;
     c->stream = (cudaStream_t)cuda_stream;
@@ -434,7 +461,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     } while (0)
     const size_t fbytes = (size_t)q * npad * eb;
     CKC(dmalloc(c, &c->f_cur, fbytes));
-    CKC(dmalloc(c, &c->f_nxt, fbytes));
+    if (c->streaming == LBM_STREAM_PULL) CKC(dmalloc(c, &c->f_nxt, fbytes));
     CKC(dmalloc(c, &c->tab, tab.size() * 4));
     CKC(dmalloc(c, &c->perm, (size_t)n * 4));
     CKC(dmalloc(c, &c->partials, (size_t)mass_blocks() * 8));
@@ -456,7 +483,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.tab = c->tab;
     L.perm = c->perm;
     CKC(launch_zero(L, c->f_cur, c->stream));
-    CKC(launch_zero(L, c->f_nxt, c->stream));
+    if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
 #undef CKC
     c->perm_host.swap(perm);
@@ -480,9 +507,7 @@ HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     for (int64_t s = 0; s < nsteps; ++s) {
-        CK(ctx, launch_step(ctx->L, ctx->f_cur, ctx->f_nxt, iolet_step(ctx, ctx->t), nullptr,
-                            ctx->stream));
-        std::swap(ctx->f_cur, ctx->f_nxt);
+        CK(ctx, advance_one(ctx, iolet_step(ctx, ctx->t), nullptr));
         ++ctx->t;
     }
     return LBM_OK;
@@ -514,9 +539,7 @@ HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *r
         CK(ctx, cudaMemcpyAsync(ctx->rho_io, rho_io_host, (size_t)nsteps * K * 8,
                                 cudaMemcpyHostToDevice, ctx->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
-        CK(ctx, launch_step(ctx->L, ctx->f_cur, ctx->f_nxt, IoletStep{}, ctx->rho_io + s * K,
-                            ctx->stream));
-        std::swap(ctx->f_cur, ctx->f_nxt);
+        CK(ctx, advance_one(ctx, IoletStep{}, ctx->rho_io + s * K));
         ++ctx->t;
         if (mass_host)
             CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_series + s, ctx->stream));
@@ -546,7 +569,7 @@ HGB_API lbm_status lbm_set_time(lbm_ctx *ctx, int64_t t) {
 
 HGB_API lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d) {
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
-    CK(ctx, launch_macros(ctx->L, ctx->f_cur, rho_d, u_d, wss_d, ctx->stream));
+    CK(ctx, launch_macros(ctx->L, ctx->f_cur, cur_layout(ctx), rho_d, u_d, wss_d, ctx->stream));
     return LBM_OK;
 }
 
@@ -565,7 +588,7 @@ HGB_API lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host) {
     const size_t bytes = (size_t)ctx->q * ctx->n * 8;
     double *tmp = nullptr;
     CK(ctx, cudaMalloc((void **)&tmp, bytes));
-    cudaError_t e = launch_gather_f64(ctx->L, ctx->f_cur, tmp, ctx->stream);
+    cudaError_t e = launch_gather_f64(ctx->L, ctx->f_cur, cur_layout(ctx), tmp, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(tmp);
@@ -580,7 +603,7 @@ HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
     double *tmp = nullptr;
     CK(ctx, cudaMalloc((void **)&tmp, bytes));
     cudaError_t e = cudaMemcpyAsync(tmp, f_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = launch_scatter_f64(ctx->L, tmp, ctx->f_cur, ctx->stream);
+    if (e == cudaSuccess) e = launch_scatter_f64(ctx->L, tmp, cur_layout(ctx), ctx->f_cur, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_populations");
@@ -607,7 +630,7 @@ HGB_API lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host) {
     if (prev != at.device) CK(ctx, cudaSetDevice(at.device));
     double *scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
-    if (e == cudaSuccess) e = launch_gather_f64(ctx->L, ctx->f_cur, scratch, ctx->stream);
+    if (e == cudaSuccess) e = launch_gather_f64(ctx->L, ctx->f_cur, cur_layout(ctx), scratch, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f_host, scratch, count * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -616,27 +639,36 @@ HGB_API lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host) {
     return LBM_OK;
 }
 
+// The state blob is the raw stored buffer followed by an 8-byte trailer that
+// records the AA layout phase (always 0 for pull streaming).
 HGB_API lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes) {
     if (!ctx || !bytes) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
-    *bytes = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage);
+    *bytes = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage) + 8;
     return LBM_OK;
 }
 
 HGB_API lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes) {
     if (!ctx || !host) return fail(ctx, LBM_ERR_ARG, "NULL argument");
-    if (bytes != (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage))
-        return fail(ctx, LBM_ERR_ARG, "wrong state size");
-    CK(ctx, cudaMemcpyAsync(host, ctx->f_cur, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    const size_t raw = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage);
+    if (bytes != raw + 8) return fail(ctx, LBM_ERR_ARG, "wrong state size");
+    CK(ctx, cudaMemcpyAsync(host, ctx->f_cur, raw, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t phase = ctx->aa_swapped ? 1 : 0;
+    memcpy(static_cast<char *>(host) + raw, &phase, 8);
     return LBM_OK;
 }
 
 HGB_API lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
     if (!ctx || !host) return fail(ctx, LBM_ERR_ARG, "NULL argument");
-    if (bytes != (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage))
-        return fail(ctx, LBM_ERR_ARG, "wrong state size");
-    CK(ctx, cudaMemcpyAsync(ctx->f_cur, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    const size_t raw = (size_t)ctx->q * ctx->npad * elem_bytes(ctx->storage);
+    if (bytes != raw + 8) return fail(ctx, LBM_ERR_ARG, "wrong state size");
+    int64_t phase = 0;
+    memcpy(&phase, static_cast<const char *>(host) + raw, 8);
+    if (phase != 0 && (phase != 1 || ctx->streaming != LBM_STREAM_AA))
+        return fail(ctx, LBM_ERR_ARG, "state blob phase does not match the context's streaming");
+    CK(ctx, cudaMemcpyAsync(ctx->f_cur, host, raw, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->aa_swapped = phase == 1;
     return LBM_OK;
 }
 
@@ -722,6 +754,7 @@ struct AdjointRun {
     int kind = 0;
     double scale = 1.0;
     int64_t t_begin = 0, t_end = 0, t0 = 0, T = 0;
+    void *final_buf = nullptr;  // receives f(T), pull layout
     bool terminal_done = false;
     int64_t fwd_steps = 0, adj_steps = 0;
 
@@ -774,8 +807,8 @@ struct AdjointRun {
     cudaError_t adjoint_at(int64_t k, const void *state) {
         cudaError_t e;
         if (!terminal_done) {
-            if ((e = step(state, c->f_cur, T - 1)) != cudaSuccess) return e;
-            if ((e = adjoint(c->f_cur, nullptr, lam[lc], T)) != cudaSuccess) return e;
+            if ((e = step(state, final_buf, T - 1)) != cudaSuccess) return e;
+            if ((e = adjoint(final_buf, nullptr, lam[lc], T)) != cudaSuccess) return e;
             terminal_done = true;
         }
         if ((e = adjoint(state, lam[lc], lam[1 - lc], k)) != cudaSuccess) return e;
@@ -895,7 +928,12 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
         }
     };
     // the per-context sizes of everything but the snapshots never change
+    const bool aa = ctx->streaming == LBM_STREAM_AA;
     grow(&ws.W1, sbytes);
+    if (aa) {
+        grow(&ws.W0, sbytes);
+        grow(&ws.final_buf, sbytes);
+    }
     grow((void **)&ws.lam[0], (size_t)q * npad * 4);
     grow((void **)&ws.lam[1], (size_t)q * npad * 4);
     grow((void **)&ws.weight, (size_t)npad * 8);
@@ -920,7 +958,8 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     }
     R.slots.assign(ws.slots.begin(), ws.slots.begin() + n_snap);
     R.W[1] = ws.W1;
-    R.W[0] = ctx->f_nxt;
+    R.W[0] = aa ? ws.W0 : ctx->f_nxt;
+    R.final_buf = aa ? ws.final_buf : ctx->f_cur;
     R.lam[0] = ws.lam[0];
     R.lam[1] = ws.lam[1];
     R.acc_block = ws.acc_block;
@@ -937,15 +976,26 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     R.weight = weight_dev;
     for (int i = n_snap - 1; i >= 1; --i) R.free_slots.push_back(i);
     if (e == cudaSuccess) e = cudaEventRecord(ws.ev[0], ctx->stream);
+    // the sweep works on pull-layout states; slot 0 receives f(t0)
+    if (e == cudaSuccess) {
+        if (aa)
+            e = launch_relayout(ctx->L, ctx->f_cur, cur_layout(ctx), R.slots[0], LAYOUT_PULL, ctx->stream);
+        else
+            e = cudaMemcpyAsync(R.slots[0], ctx->f_cur, sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
     if (e == cudaSuccess) {
         if (nsteps == 0) {
-            e = R.adjoint(ctx->f_cur, nullptr, R.lam[0], R.t0);
+            e = R.adjoint(R.slots[0], nullptr, R.lam[0], R.t0);
             R.lc = 0;
+            if (e == cudaSuccess && !aa)
+                e = cudaMemcpyAsync(ctx->f_cur, R.slots[0], sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
         } else {
-            e = cudaMemcpyAsync(R.slots[0], ctx->f_cur, sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
-            if (e == cudaSuccess) e = R.reverse(R.t0, R.T, R.slots[0], n_snap - 1);
+            e = R.reverse(R.t0, R.T, R.slots[0], n_snap - 1);
         }
     }
+    // AA mode: the final state back into the single buffer, natural layout
+    if (e == cudaSuccess && aa && nsteps > 0)
+        e = launch_relayout(ctx->L, R.final_buf, LAYOUT_PULL, ctx->f_cur, LAYOUT_NATURAL, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ws.ev[1], ctx->stream);
     if (e == cudaSuccess) e = launch_adjoint_final(ctx->L, R.acc_block, R.io_acc, out_dev, ctx->stream);
     if (e == cudaSuccess && dJ_df0) e = launch_lam_to_caller(ctx->L, R.lam[R.lc], lam0_dev, ctx->stream);
@@ -960,6 +1010,7 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_objective_grad");
     ctx->last_sweep_ms = sweep_ms;
     ctx->t = R.T;
+    if (aa && nsteps > 0) ctx->aa_swapped = false;
     ctx->last_fwd_steps = R.fwd_steps;
     ctx->last_adj_steps = R.adj_steps;
     *J = obj->scale * out[0];

@@ -11,6 +11,9 @@ namespace hemelb_gb300 {
 
 constexpr int kMaxIolets = 64;
 
+// Where population i of site x is stored (see src_slot in lbm_kernels.cu).
+enum Layout { LAYOUT_PULL = 0, LAYOUT_NATURAL = 1, LAYOUT_AA_SWAPPED = 2 };
+
 // Iolet densities of one step, evaluated on the host in float64 and passed
 // by value: drho[k] = rho_k(t) - rho0 (rounded once to float, so that the
 // small pressure differences keep their relative precision), rho[k] = rho_k(t).
@@ -52,8 +55,17 @@ struct DevLattice {
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
                         const double *rho_io, cudaStream_t s);
 
+// One in-place AA-pattern step on the single buffer A: the even kernel
+// (A in natural layout -> swapped) or the odd kernel (swapped -> natural).
+cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
+                           const double *rho_io, cudaStream_t s);
+
+// Exact copy of a stored state between layouts.
+cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,
+                            int dst_layout, cudaStream_t s);
+
 // rho, u, wss of the state held in f (any output may be null), caller order.
-cudaError_t launch_macros(const DevLattice &L, const void *f, float *rho, float *u,
+cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float *rho, float *u,
                           float *wss, cudaStream_t s);
 
 // Deterministic float64 mass: partial sums into partials[nblk], final into out.
@@ -62,10 +74,10 @@ cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, do
                         cudaStream_t s);
 
 // f(t) as float64 [q][n] caller order (gather of the stored state).
-cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out,
+cudaError_t launch_gather_f64(const DevLattice &L, const void *f, int layout, double *out,
                               cudaStream_t s);
 // stored state from float64 [q][n] caller order (inverse of the gather).
-cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f,
+cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, int layout, void *f,
                                cudaStream_t s);
 // ------------------------------------------------------------ adjoint
 // Per-step inputs of the adjoint kernel: the iolet densities of step t and

@@ -70,9 +70,15 @@ struct Store<true> {
     }
 };
 
-// Pull source slot of population i at site x for table entry s.
-__device__ __forceinline__ int64_t src_slot(int i, int s, int x, int64_t np) {
-    return s >= 0 ? (int64_t)i * np + s : (int64_t)opp(i) * np + x;
+// Slot holding population i of site x (table entry s) in each layout:
+//   pull        P[i][s] (the site x - c_i), or P[opp(i)][x] for a wall/iolet link;
+//   natural     A[i][x] (AA pattern after an odd step);
+//   AA swapped  A[opp(i)][s], or A[i][x] for a wall/iolet link (after an even step).
+__device__ __forceinline__ int64_t src_slot(int layout, int i, int s, int x, int64_t np) {
+    if (layout == LAYOUT_NATURAL) return (int64_t)i * np + x;
+    const int a = layout == LAYOUT_PULL ? i : opp(i);
+    const int b = layout == LAYOUT_PULL ? opp(i) : i;
+    return s >= 0 ? (int64_t)a * np + s : (int64_t)b * np + x;
 }
 
 // Gather the q deviations of site x (pre-collision populations f(t) - w rho0).
@@ -80,7 +86,7 @@ __device__ __forceinline__ int64_t src_slot(int i, int s, int x, int64_t np) {
 // and, through wall_n, the sum of c_i over entries == -1.
 template <int Q, bool HALF, bool STREAM_TAB>
 __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<HALF>::T *__restrict__ f,
-                                      int x, float (&d)[Q], int (&wn)[3]) {
+                                      int layout, int x, float (&d)[Q], int (&wn)[3]) {
     using S = Store<HALF>;
     const int64_t np = L.npad;
     int minc = 0;
@@ -94,7 +100,7 @@ __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<
     d[0] = S::load(f + x, L.inv_scale);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        d[i] = S::load(f + src_slot(i, s[i], x, np), L.inv_scale);
+        d[i] = S::load(f + src_slot(layout, i, s[i], x, np), L.inv_scale);
         minc = min(minc, s[i]);
         if (s[i] == -1) {
             wn[0] += cdir<Q>(i, 0);
@@ -143,42 +149,142 @@ __device__ __forceinline__ float deq(int i, float drho, float rho, const Moments
 template <bool HALF>
 struct Raw;
 
+// Cache policy of the in-place AA kernels: 1 = evict-first (.cs), 0 = default
+#ifndef HGB_AA_LD_CS
+#define HGB_AA_LD_CS 0
+#endif
+#ifndef HGB_AA_ST_CS
+#define HGB_AA_ST_CS 1
+#endif
+
 template <>
 struct Raw<false> {
     using T = float;
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_rw(const float *p) { return HGB_AA_LD_CS ? __ldcs(p) : *p; }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+    static __device__ __forceinline__ void st_rw(float *p, float v) {
+        if (HGB_AA_ST_CS) __stcs(p, v);
+        else *p = v;
+    }
 };
 
 template <>
 struct Raw<true> {
     using T = __half;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_rw(const __half *p) {
+        return HGB_AA_LD_CS ? __half2float(__short_as_half(__ldcs(reinterpret_cast<const short *>(p))))
+                            : __half2float(*p);
+    }
+    static __device__ __forceinline__ void st_rw(__half *p, float v) {
+        if (HGB_AA_ST_CS) __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
+        else *p = __float2half_rn(v);
+    }
     static __device__ __forceinline__ void st(__half *p, float v) {
         __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
     }
 };
 
+// Velocity moments of one site after its collision (for the iolet values).
+struct Velocity {
+    float ux, uy, uz, usq15;
+};
+
+// LBGK collision of one site in stored units (deviations, times 2^S for
+// fp16), written per opposite pair (i, opp i): with cu = c_i.u the
+// equilibrium deviations are sym +- asym, sym = w (drho + rho (4.5 cu^2 -
+// 1.5 u^2)), asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i.
+// Every step kernel (pull, AA even, AA odd) uses this one function, so all
+// streaming forms give bitwise identical populations.
+template <int Q, bool HALF>
+__device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d)[Q], float (&out)[Q]) {
+    float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sum = d[i] + d[i + 1], dif = d[i] - d[i + 1];
+        drs += sum;
+        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
+        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
+        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
+    }
+    const float rho = HALF ? fmaf(drs, L.inv_scale, L.rho0) : L.rho0 + drs;
+    const float ir = (HALF ? L.inv_scale : 1.0f) / rho;
+    Velocity v;
+    v.ux = jx * ir;
+    v.uy = jy * ir;
+    v.uz = jz * ir;
+    v.usq15 = 1.5f * (v.ux * v.ux + v.uy * v.uy + v.uz * v.uz);
+    const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
+    const float om = L.omega, omc = 1.0f - L.omega;
+    {
+        const float w0 = (float)wdir<Q>(0);
+        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * v.usq15));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = (float)wdir<Q>(i);
+        const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
+        const float t = fmaf(4.5f * cu, cu, -v.usq15);
+        const float sym = fmaf(om * w * rs, t, om * w * drs);
+        const float asym = (3.0f * om * w * rs) * cu;
+        out[i] = fmaf(omc, d[i], sym + asym);
+        out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
+    }
+    return v;
+}
+
+// Iolet links of a site with an iolet link (x >= n_bulk): for every i whose
+// table entry s[i] = -2 - k marks link opp(i) as iolet k, the population
+// that re-enters the site as population i at the next step is the
+// equilibrium at the iolet density and the site's current velocity; it
+// replaces the outgoing f*_opp(i), which leaves the domain.
+template <int Q, bool HALF>
+__device__ __forceinline__ void iolet_override(const DevLattice &L, const int (&s)[Q], const Velocity &v,
+                                               const IoletStep &io, const double *__restrict__ rho_io,
+                                               float (&out)[Q]) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (s[i] <= -2) {
+            const int k = -2 - s[i];
+            float drk, rk;
+            if (rho_io) {
+                const double r = rho_io[k];
+                drk = (float)(r - (double)L.rho0);
+                rk = (float)r;
+            } else {
+                drk = io.drho[k];
+                rk = io.rho[k];
+            }
+            if (HALF) {
+                drk *= L.scale;
+                rk *= L.scale;
+            }
+            const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
+            out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - v.usq15));
+        }
+    }
+}
+
 // Fused pull collide-and-stream of one time step, one site per thread.
 //   gather   d_i = slot(i, x) through the table (coalesced table reads,
 //            gathered population reads, Morton order keeps them local);
-//   collide  LBGK toward the deviation equilibrium, written per opposite
-//            pair (i, opp i): with cu = c_i.u the equilibrium deviations are
-//            sym +- asym, sym = w (drho + rho (4.5 cu^2 - 1.5 u^2)),
-//            asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i;
+//   collide  collide() above;
 //   iolets   sites with iolet links come last in the internal order
-//            (x >= n_bulk); there the slot read back through an iolet link
-//            is overwritten by the equilibrium at the iolet density;
+//            (x >= n_bulk): iolet_override() above;
 //   stream   q coalesced streaming stores at the site's own slots.
 // All slot offsets are 32-bit (q * npad < 2^31 is checked at create).
-template <int Q, bool HALF>
+// IO = false: the bulk sites [0, n_bulk); IO = true: the sites with an
+// iolet link [n_bulk, n), launched separately so that the bulk kernel carries
+// no iolet code (and no register cost for it).
+template <int Q, bool HALF, bool IO>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
 k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
        typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
        const double *__restrict__ rho_io) {
     using R = Raw<HALF>;
-    const int x = blockIdx.x * kBlock + threadIdx.x;
-    if (x >= L.n) return;
+    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
+    if (x >= (IO ? L.n : L.n_bulk)) return;
     const unsigned np = (unsigned)L.npad;
     int s[Q];
 #pragma unroll
@@ -191,75 +297,78 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
                                      : (unsigned)opp(i) * np + (unsigned)x;
         d[i] = R::ld(fin + e);
     }
-    // moments, in stored units
-    float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float sum = d[i] + d[i + 1], dif = d[i] - d[i + 1];
-        drs += sum;
-        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
-        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
-        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
-    }
-    const float rho = HALF ? fmaf(drs, L.inv_scale, L.rho0) : L.rho0 + drs;
-    const float ir = (HALF ? L.inv_scale : 1.0f) / rho;
-    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
-    const float om = L.omega, omc = 1.0f - L.omega;
     float out[Q];
-    {
-        const float w0 = (float)wdir<Q>(0);
-        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * usq15));
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float w = (float)wdir<Q>(i);
-        const float cu = cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
-        const float t = fmaf(4.5f * cu, cu, -usq15);
-        const float sym = fmaf(om * w * rs, t, om * w * drs);
-        const float asym = (3.0f * om * w * rs) * cu;
-        out[i] = fmaf(omc, d[i], sym + asym);
-        out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
-    }
-    if (x >= L.n_bulk) {
-        // the slot read back through an iolet link at the next step holds the
-        // equilibrium at the iolet density and the site's current velocity
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (s[i] <= -2) {
-                const int k = -2 - s[i];
-                float drk, rk;
-                if (rho_io) {
-                    const double r = rho_io[k];
-                    drk = (float)(r - (double)L.rho0);
-                    rk = (float)r;
-                } else {
-                    drk = io.drho[k];
-                    rk = io.rho[k];
-                }
-                if (HALF) {
-                    drk *= L.scale;
-                    rk *= L.scale;
-                }
-                const float cu = cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
-                out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - usq15));
-            }
-        }
-    }
+    const Velocity v = collide<Q, HALF>(L, d, out);
+    if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
 }
 
+// AA-pattern in-place step on one population buffer A (Bailey et al.,
+// "Accelerating lattice Boltzmann fluid flow simulations using graphics
+// processors", ICPP 2009).  Population i of site x is read from its slot and
+// the post-collision population opp(i) is written back into that same slot,
+// so every slot is read and written by one thread only:
+//   even step: slot_i = A[i][x]                  (own site, no table for bulk sites)
+//   odd step:  slot_i = A[opp(i)][x - c_i]       (through the table), or
+//              A[i][x] for a wall or iolet link opp(i).
+// After an even step A holds the populations of time t+1 in swapped slots;
+// after an odd step they are back in natural order, A[i][x] = f_i(x).
+#ifndef HGB_AA_MINB_FP32
+#define HGB_AA_MINB_FP32 3
+#endif
+#ifndef HGB_AA_MINB_FP16
+#define HGB_AA_MINB_FP16 3
+#endif
+template <int Q, bool HALF, bool ODD, bool IO>
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
+k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const IoletStep io,
+          const double *__restrict__ rho_io) {
+    using R = Raw<HALF>;
+    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
+    if (x >= (IO ? L.n : L.n_bulk)) return;
+    const unsigned np = (unsigned)L.npad;
+    int s[Q];
+    s[0] = 0;
+    if (ODD || IO) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    }
+    float d[Q];
+    float out[Q];
+    if (!ODD) {
+        // own slots: one base pointer, plane stride np
+        typename Raw<HALF>::T *a = A + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+        const Velocity v = collide<Q, HALF>(L, d, out);
+        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
+    } else {
+        // slot of population i (32-bit element offset)
+        auto slot = [&](int i) -> unsigned {
+            if (i == 0) return (unsigned)x;
+            return s[i] >= 0 ? (unsigned)opp(i) * np + (unsigned)s[i] : (unsigned)i * np + (unsigned)x;
+        };
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
+        const Velocity v = collide<Q, HALF>(L, d, out);
+        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
+    }
+}
+
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock)
-k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, float *__restrict__ rho,
-         float *__restrict__ u, float *__restrict__ wss) {
+k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
+         float *__restrict__ rho, float *__restrict__ u, float *__restrict__ wss) {
     const int x = blockIdx.x * kBlock + threadIdx.x;
     if (x >= L.n) return;
     float d[Q];
     int wn[3];
-    gather<Q, HALF, false>(L, f, x, d, wn);
+    gather<Q, HALF, false>(L, f, layout, x, d, wn);
     const Moments m = moments<Q>(d, L.rho0);
     const int xc = L.perm[x];
     if (rho) rho[xc] = m.rho;
@@ -325,10 +434,8 @@ k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
     using S = Store<HALF>;
     double acc = 0.0;
     for (int x = blockIdx.x * kBlock + threadIdx.x; x < L.n; x += gridDim.x * kBlock) {
-        float s = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) s += S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
-        acc += (double)s;
+        for (int i = 0; i < Q; ++i) acc += (double)S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -344,12 +451,13 @@ k_mass_final(const double *__restrict__ partials, int nparts, double base, doubl
 
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock)
-k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, double *__restrict__ out) {
+k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
+             double *__restrict__ out) {
     const int x = blockIdx.x * kBlock + threadIdx.x;
     if (x >= L.n) return;
     float d[Q];
     int wn[3];
-    gather<Q, HALF, false>(L, f, x, d, wn);
+    gather<Q, HALF, false>(L, f, layout, x, d, wn);
     const int64_t xc = L.perm[x];
 #pragma unroll
     for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = wdir<Q>(i) * (double)L.rho0 + (double)d[i];
@@ -357,7 +465,8 @@ k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, 
 
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock)
-k_scatter_f64(const DevLattice L, const double *__restrict__ in, typename Store<HALF>::T *__restrict__ f) {
+k_scatter_f64(const DevLattice L, const double *__restrict__ in, int layout,
+              typename Store<HALF>::T *__restrict__ f) {
     using S = Store<HALF>;
     const int x = blockIdx.x * kBlock + threadIdx.x;
     if (x >= L.n) return;
@@ -368,17 +477,51 @@ k_scatter_f64(const DevLattice L, const double *__restrict__ in, typename Store<
     for (int i = 1; i < Q; ++i) {
         const int s = L.tab[(int64_t)(i - 1) * np + x];
         const double v = in[(int64_t)i * L.n + xc] - wdir<Q>(i) * (double)L.rho0;
-        S::store_plain(f + src_slot(i, s, x, np), (float)v, L.scale);
+        S::store_plain(f + src_slot(layout, i, s, x, np), (float)v, L.scale);
+    }
+}
+
+// Exact copy of the stored state from one layout to another (a permutation of
+// the stored elements; no arithmetic).
+template <typename T, int Q>
+__global__ void __launch_bounds__(kBlock)
+k_relayout(const DevLattice L, const T *__restrict__ src, int src_layout, T *__restrict__ dst,
+           int dst_layout) {
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    const int64_t np = L.npad;
+    dst[x] = src[x];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int s = L.tab[(int64_t)(i - 1) * np + x];
+        dst[src_slot(dst_layout, i, s, x, np)] = src[src_slot(src_layout, i, s, x, np)];
     }
 }
 
 inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 template <int Q, bool HALF>
+cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
+                         const double *rho_io, cudaStream_t s) {
+    using T = typename Raw<HALF>::T;
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (odd) {
+        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+    } else {
+        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, bool HALF>
 cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
                       const double *rho_io, cudaStream_t s) {
     using T = typename Raw<HALF>::T;
-    k_step<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (nb) k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    if (ni) k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
     return cudaGetLastError();
 }
 
@@ -394,12 +537,35 @@ cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const 
     return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
 }
 
+cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
+                           const double *rho_io, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s);
+}
+
+cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,
+                            int dst_layout, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    if (L.storage) {
+        if (L.q == 15)
+            k_relayout<short, 15><<<grid_for(L.n), kBlock, 0, s>>>(L, (const short *)src, src_layout, (short *)dst, dst_layout);
+        else
+            k_relayout<short, 19><<<grid_for(L.n), kBlock, 0, s>>>(L, (const short *)src, src_layout, (short *)dst, dst_layout);
+    } else {
+        if (L.q == 15)
+            k_relayout<float, 15><<<grid_for(L.n), kBlock, 0, s>>>(L, (const float *)src, src_layout, (float *)dst, dst_layout);
+        else
+            k_relayout<float, 19><<<grid_for(L.n), kBlock, 0, s>>>(L, (const float *)src, src_layout, (float *)dst, dst_layout);
+    }
+    return cudaGetLastError();
+}
+
 namespace {
 template <int Q, bool HALF>
-cudaError_t macros_impl(const DevLattice &L, const void *f, float *rho, float *u, float *wss,
+cudaError_t macros_impl(const DevLattice &L, const void *f, int layout, float *rho, float *u, float *wss,
                         cudaStream_t s) {
     using T = typename Store<HALF>::T;
-    k_macros<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, rho, u, wss);
+    k_macros<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, rho, u, wss);
     return cudaGetLastError();
 }
 template <int Q, bool HALF>
@@ -409,23 +575,23 @@ cudaError_t mass_impl(const DevLattice &L, const void *f, double *partials, cuda
     return cudaGetLastError();
 }
 template <int Q, bool HALF>
-cudaError_t gather_impl(const DevLattice &L, const void *f, double *out, cudaStream_t s) {
+cudaError_t gather_impl(const DevLattice &L, const void *f, int layout, double *out, cudaStream_t s) {
     using T = typename Store<HALF>::T;
-    k_gather_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, out);
+    k_gather_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, out);
     return cudaGetLastError();
 }
 template <int Q, bool HALF>
-cudaError_t scatter_impl(const DevLattice &L, const double *in, void *f, cudaStream_t s) {
+cudaError_t scatter_impl(const DevLattice &L, const double *in, int layout, void *f, cudaStream_t s) {
     using T = typename Store<HALF>::T;
-    k_scatter_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, in, (T *)f);
+    k_scatter_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, in, layout, (T *)f);
     return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_macros(const DevLattice &L, const void *f, float *rho, float *u, float *wss,
-                          cudaStream_t s) {
+cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float *rho, float *u,
+                          float *wss, cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, macros_impl, L, f, rho, u, wss, s);
+    return HGB_DISPATCH(L, macros_impl, L, f, layout, rho, u, wss, s);
 }
 
 int mass_blocks() { return kMassBlocks; }
@@ -438,14 +604,16 @@ cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, do
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_f64(const DevLattice &L, const void *f, double *out, cudaStream_t s) {
+cudaError_t launch_gather_f64(const DevLattice &L, const void *f, int layout, double *out,
+                              cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, gather_impl, L, f, out, s);
+    return HGB_DISPATCH(L, gather_impl, L, f, layout, out, s);
 }
 
-cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, void *f, cudaStream_t s) {
+cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, int layout, void *f,
+                               cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, scatter_impl, L, in, f, s);
+    return HGB_DISPATCH(L, scatter_impl, L, in, layout, f, s);
 }
 
 cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s) {

@@ -17,6 +17,8 @@ from . import build as _build
 
 STORE_FP32 = 0
 STORE_FP16 = 1
+STREAM_PULL = 0
+STREAM_AA = 1
 MAX_IOLETS = 64
 
 _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM",
@@ -52,7 +54,7 @@ class _Params(C.Structure):
     _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("tau", C.c_double),
                 ("rho0", C.c_double), ("fp16_scale_log2", C.c_int32), ("n_iolets", C.c_int32),
                 ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
-                ("phase", C.c_void_p)]
+                ("phase", C.c_void_p), ("streaming", C.c_int32)]
 
 
 _lib = None
@@ -161,7 +163,7 @@ class Lattice:
                  rho0: float = 1.0, fp16_scale_log2: int = 14,
                  rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
                  period: Sequence[float] = None, phase: Sequence[float] = None,
-                 stream=None):
+                 stream=None, streaming: int = STREAM_PULL):
         self._lib = load_library()
         self._ctx = C.c_void_p()
         k = len(rho_mean)
@@ -176,7 +178,8 @@ class Lattice:
         if nbr.shape != (q, n) or link.shape != (q, n):
             raise ValueError("nbr and link must be [q, n]")
         prm = _Params(int(q), int(storage), float(tau), float(rho0), int(fp16_scale_log2), k,
-                      *[(a.ctypes.data if k else None) for a in self._io])
+                      *[(a.ctypes.data if k else None) for a in self._io], int(streaming))
+        self.streaming = int(streaming)
         self.q, self.n, self.tau, self.storage, self.rho0 = int(q), n, float(tau), int(storage), float(rho0)
         self.n_iolets = k
         st = self._lib.lbm_create(C.byref(self._ctx), C.byref(prm), n, _p(xyz), _p(nbr), _p(link),

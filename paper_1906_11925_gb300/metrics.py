@@ -17,10 +17,13 @@ def msups(n_sites: int, steps: int, seconds: float) -> float:
     return sups(n_sites, steps, seconds) / 1e6
 
 
-def bytes_per_site_update(q: int, storage: str) -> int:
-    """Algorithmic HBM bytes of one fused pull collide-and-stream update:
+def bytes_per_site_update(q: int, storage: str, streaming: str = "pull") -> int:
+    """Algorithmic HBM bytes of one fused collide-and-stream update:
     q populations read and q written (4 B each in fp32, 2 B in fp16
-    deviation storage) plus q - 1 int32 neighbour entries (the rest
-    population needs none)."""
+    deviation storage) plus the int32 neighbour entries (q - 1; the rest
+    population needs none).  Pull streaming reads the table every step; the
+    AA pattern only on odd steps, so its average over a step pair is
+    (q - 1) * 2 B."""
     elem = {"fp32": 4, "fp16": 2}[storage]
-    return 2 * q * elem + 4 * (q - 1)
+    table = {"pull": 4 * (q - 1), "aa": 2 * (q - 1)}[streaming]
+    return 2 * q * elem + table

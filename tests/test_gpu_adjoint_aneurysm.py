@@ -90,7 +90,8 @@ def test_aneurysm_full_run_gradient_vs_gpu_central_differences(aneurysm):
         return r["J"]
 
     assert J() == got["J"]  # bitwise reproducible
-    ht, ha, hp = 1e-4, 1e-6, 1e-3
+    # the fp32 forward is rounding-noisy in tau below h ~ 3e-4 over 4000 steps
+    ht, ha, hp = 1e-3, 1e-6, 1e-3
     d_tau = (J(tau=TAU + ht) - J(tau=TAU - ht)) / (2 * ht)
     d_amp = (J(amp=g.amp + [ha, 0]) - J(amp=g.amp - [ha, 0])) / (2 * ha)
     d_phase = (J(phase=g.phase + [hp, 0]) - J(phase=g.phase - [hp, 0])) / (2 * hp)

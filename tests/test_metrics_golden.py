@@ -19,3 +19,5 @@ def test_bytes_per_site_update():
     assert metrics.bytes_per_site_update(15, "fp16") == 116
     assert metrics.bytes_per_site_update(19, "fp32") == 224
     assert metrics.bytes_per_site_update(19, "fp16") == 148
+    assert metrics.bytes_per_site_update(19, "fp32", "aa") == 188
+    assert metrics.bytes_per_site_update(19, "fp16", "aa") == 112
