@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1906_11925_gb300 import geometry as G  # noqa: E402
 from paper_1906_11925_gb300 import metrics  # noqa: E402
+from paper_1906_11925_gb300 import replicas  # noqa: E402
 
 LB_STEPS_PER_BENCH_STEP = 100
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md")
@@ -68,9 +69,7 @@ def make_geometry(name: str):
     return g
 
 
-def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
-            int(os.environ.get("WORLD_SIZE", "1")))
+dist_env = replicas.rank_env
 
 
 def read_peaks():
@@ -172,16 +171,11 @@ def run_ours(args):
     legs = set(args.legs.split(","))
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, world, device="cuda")
 
     def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL):
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
