@@ -38,7 +38,7 @@ from paper_1906_11925_gb300 import replicas  # noqa: E402
 
 LB_STEPS_PER_BENCH_STEP = 100
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_kernels.cu")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_step.cu")
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {

@@ -218,18 +218,13 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         // (no ordering fence here: overlapping the forward-state and adjoint
         // gathers is worth more than the registers it costs; fencing them
         // apart measured 1.50 ms per step against 1.06 ms)
-        // adjoint of the post-collision populations, with the iolet terms,
-        // accumulated per opposite pair as they arrive:
-        //   a = sum_i lam*_i feq_i/rho, b = sum_i lam*_i dfeq_i/du,
-        //   dt = sum_i lam*_i (f_i - feq_i)
+        // adjoint of the post-collision populations, with the iolet terms
+        // (all gathers issued first, then the pairwise sums: keeping the loads
+        // back to back measured faster than accumulating as they arrive)
         float ls[Q];
         float gx = 0.f, gy = 0.f, gz = 0.f;
         const bool has_next = lam_next != nullptr;
         ls[0] = has_next ? lam_next[x] : 0.f;
-        float a = (float)wdir<Q>(0) * ls[0] * (1.0f - usq15);
-        float bx = 0.f, by = 0.f, bz = 0.f;
-        float sb = (float)wdir<Q>(0) * ls[0];
-        float dt = ls[0] * ne[0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int sp = s[opp(i)];  // link i of x: >= 0 -> the site x + c_i
@@ -258,21 +253,26 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
                     io_acc[2 * plane + slot] += (double)drk * st.dacos[k];
                 }
             }
-            if ((i & 1) == 0) {
-                // pair (i - 1, i) complete
-                const int p = i - 1;
-                const float w = (float)wdir<Q>(p);
-                const float cu = cdot<Q>(p, ux, uy, uz);
-                const float sum = ls[p] + ls[i], dif = ls[p] - ls[i];
-                a += w * fmaf(sum, 1.0f + fmaf(4.5f * cu, cu, -usq15), 3.0f * cu * dif);
-                const float bc = w * fmaf(9.0f * cu, sum, 3.0f * dif);
-                if (cdir<Q>(p, 0)) bx += cdir<Q>(p, 0) * bc;
-                if (cdir<Q>(p, 1)) by += cdir<Q>(p, 1) * bc;
-                if (cdir<Q>(p, 2)) bz += cdir<Q>(p, 2) * bc;
-                sb += w * sum;
-                dt = fmaf(ls[p], ne[p], dt);
-                dt = fmaf(ls[i], ne[i], dt);
-            }
+        }
+        // a = sum_i lam*_i feq_i/rho, b = sum_i lam*_i dfeq_i/du (pairwise),
+        // dt = sum_i lam*_i (f_i - feq_i)
+        float a = (float)wdir<Q>(0) * ls[0] * (1.0f - usq15);
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        float sb = (float)wdir<Q>(0) * ls[0];
+        float dt = ls[0] * ne[0];
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float w = (float)wdir<Q>(i);
+            const float cu = cdot<Q>(i, ux, uy, uz);
+            const float sum = ls[i] + ls[i + 1], dif = ls[i] - ls[i + 1];
+            a += w * fmaf(sum, 1.0f + fmaf(4.5f * cu, cu, -usq15), 3.0f * cu * dif);
+            const float bc = w * fmaf(9.0f * cu, sum, 3.0f * dif);
+            if (cdir<Q>(i, 0)) bx += cdir<Q>(i, 0) * bc;
+            if (cdir<Q>(i, 1)) by += cdir<Q>(i, 1) * bc;
+            if (cdir<Q>(i, 2)) bz += cdir<Q>(i, 2) * bc;
+            sb += w * sum;
+            dt = fmaf(ls[i], ne[i], dt);
+            dt = fmaf(ls[i + 1], ne[i + 1], dt);
         }
         // b = rho (bc-sum - 3 u sb)
         bx = rho * (bx - 3.0f * ux * sb);

@@ -39,6 +39,7 @@ struct lbm_ctx {
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
     double *partials = nullptr, *mass_dev = nullptr;
+    int *err_flag = nullptr;
     double *rho_io = nullptr;  // driven iolet densities, grown on demand
     size_t rho_io_cap = 0;
     double *mass_series = nullptr;
@@ -345,6 +346,7 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->tab);
     cudaFree(c->perm);
     cudaFree(c->partials);
+    cudaFree(c->err_flag);
     cudaFree(c->mass_dev);
     cudaFree(c->rho_io);
     cudaFree(c->mass_series);
@@ -466,6 +468,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(dmalloc(c, &c->perm, (size_t)n * 4));
     CKC(dmalloc(c, &c->partials, (size_t)mass_blocks() * 8));
     CKC(dmalloc(c, &c->mass_dev, 8));
+    CKC(dmalloc(c, &c->err_flag, 16));
+    CKC(cudaMemsetAsync(c->err_flag, 0, 16, c->stream));
     CKC(cudaMemcpyAsync(c->tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
     if (n) CKC(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
     DevLattice &L = c->L;
@@ -482,6 +486,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.n_iolets = p->n_iolets;
     L.tab = c->tab;
     L.perm = c->perm;
+    L.err = c->err_flag;
     CKC(launch_zero(L, c->f_cur, c->stream));
     if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
@@ -575,9 +580,12 @@ HGB_API lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss
 
 HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    int flag = 0;
     CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_dev, ctx->stream));
     CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&flag, ctx->err_flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag) return fail(ctx, LBM_ERR_CUDA, "a step kernel gave up waiting for its table copies");
     if (!std::isfinite(*out)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite mass");
     return LBM_OK;
 }

@@ -47,6 +47,7 @@ struct DevLattice {
     int n_iolets;
     const int32_t *tab;           // [q-1][npad]
     const int32_t *perm;          // [n] internal -> caller index
+    int *err;                     // device flag: a bounded wait in a kernel timed out
 };
 
 // One fused pull collide-and-stream step from fin into fout.  The iolet

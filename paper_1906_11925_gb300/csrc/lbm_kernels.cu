@@ -1,7 +1,8 @@
-// CUDA kernels of libhemelb_gb300 (sm_103a): the fused pull collide-and-stream
-// step over the sparse, Morton-ordered site list, the macroscopic fields and
-// wall shear stress, the float64 mass reduction, and the gather/scatter that
-// convert the stored state to and from caller-order float64 populations.
+// CUDA kernels of libhemelb_gb300 (sm_103a) around the step (the step
+// kernels themselves are in lbm_step.cu): the macroscopic fields and wall
+// shear stress, the float64 mass reduction, the gather/scatter that convert
+// the stored state to and from caller-order float64 populations, and the
+// exact layout conversion between pull and AA storage.
 //
 // The method (arXiv 1906.11925, Section 2): collision then propagation of a
 // single-particle distribution on a sparse lattice of fluid sites, D3Q19
@@ -24,6 +25,8 @@
 // and streamed.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lattice.h"
 #include "lbm_internal.h"
 
@@ -31,16 +34,7 @@ namespace hemelb_gb300 {
 namespace {
 
 constexpr int kBlock = 256;
-// resident blocks per SM requested from the register allocator for the step
-// kernel (fp32 storage, fp16 storage)
-#ifndef HGB_STEP_MINB_FP32
-#define HGB_STEP_MINB_FP32 4
-#endif
-#ifndef HGB_STEP_MINB_FP16
-#define HGB_STEP_MINB_FP16 5
-#endif
 constexpr int kMassBlocks = 2 * 152;  // fixed grid: deterministic reduction order
-
 template <bool HALF>
 struct Store;
 
@@ -143,223 +137,6 @@ __device__ __forceinline__ float deq(int i, float drho, float rho, const Moments
     return (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - m.usq15));
 }
 
-// Raw stored values for the step kernel: fp16 values stay in their scaled
-// units (d * 2^S) through the whole update, so that no load or store pays a
-// multiplication; only rho and u are formed in real units.
-template <bool HALF>
-struct Raw;
-
-// Cache policy of the in-place AA kernels: 1 = evict-first (.cs), 0 = default
-#ifndef HGB_AA_LD_CS
-#define HGB_AA_LD_CS 0
-#endif
-#ifndef HGB_AA_ST_CS
-#define HGB_AA_ST_CS 1
-#endif
-
-template <>
-struct Raw<false> {
-    using T = float;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-    static __device__ __forceinline__ float ld_rw(const float *p) { return HGB_AA_LD_CS ? __ldcs(p) : *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
-    static __device__ __forceinline__ void st_rw(float *p, float v) {
-        if (HGB_AA_ST_CS) __stcs(p, v);
-        else *p = v;
-    }
-};
-
-template <>
-struct Raw<true> {
-    using T = __half;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ float ld_rw(const __half *p) {
-        return HGB_AA_LD_CS ? __half2float(__short_as_half(__ldcs(reinterpret_cast<const short *>(p))))
-                            : __half2float(*p);
-    }
-    static __device__ __forceinline__ void st_rw(__half *p, float v) {
-        if (HGB_AA_ST_CS) __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
-        else *p = __float2half_rn(v);
-    }
-    static __device__ __forceinline__ void st(__half *p, float v) {
-        __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
-    }
-};
-
-// Velocity moments of one site after its collision (for the iolet values).
-struct Velocity {
-    float ux, uy, uz, usq15;
-};
-
-// LBGK collision of one site in stored units (deviations, times 2^S for
-// fp16), written per opposite pair (i, opp i): with cu = c_i.u the
-// equilibrium deviations are sym +- asym, sym = w (drho + rho (4.5 cu^2 -
-// 1.5 u^2)), asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i.
-// Every step kernel (pull, AA even, AA odd) uses this one function, so all
-// streaming forms give bitwise identical populations.
-template <int Q, bool HALF>
-__device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d)[Q], float (&out)[Q]) {
-    float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float sum = d[i] + d[i + 1], dif = d[i] - d[i + 1];
-        drs += sum;
-        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
-        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
-        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
-    }
-    const float rho = HALF ? fmaf(drs, L.inv_scale, L.rho0) : L.rho0 + drs;
-    const float ir = (HALF ? L.inv_scale : 1.0f) / rho;
-    Velocity v;
-    v.ux = jx * ir;
-    v.uy = jy * ir;
-    v.uz = jz * ir;
-    v.usq15 = 1.5f * (v.ux * v.ux + v.uy * v.uy + v.uz * v.uz);
-    const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
-    const float om = L.omega, omc = 1.0f - L.omega;
-    {
-        const float w0 = (float)wdir<Q>(0);
-        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * v.usq15));
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float w = (float)wdir<Q>(i);
-        const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
-        const float t = fmaf(4.5f * cu, cu, -v.usq15);
-        const float sym = fmaf(om * w * rs, t, om * w * drs);
-        const float asym = (3.0f * om * w * rs) * cu;
-        out[i] = fmaf(omc, d[i], sym + asym);
-        out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
-    }
-    return v;
-}
-
-// Iolet links of a site with an iolet link (x >= n_bulk): for every i whose
-// table entry s[i] = -2 - k marks link opp(i) as iolet k, the population
-// that re-enters the site as population i at the next step is the
-// equilibrium at the iolet density and the site's current velocity; it
-// replaces the outgoing f*_opp(i), which leaves the domain.
-template <int Q, bool HALF>
-__device__ __forceinline__ void iolet_override(const DevLattice &L, const int (&s)[Q], const Velocity &v,
-                                               const IoletStep &io, const double *__restrict__ rho_io,
-                                               float (&out)[Q]) {
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        if (s[i] <= -2) {
-            const int k = -2 - s[i];
-            float drk, rk;
-            if (rho_io) {
-                const double r = rho_io[k];
-                drk = (float)(r - (double)L.rho0);
-                rk = (float)r;
-            } else {
-                drk = io.drho[k];
-                rk = io.rho[k];
-            }
-            if (HALF) {
-                drk *= L.scale;
-                rk *= L.scale;
-            }
-            const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
-            out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - v.usq15));
-        }
-    }
-}
-
-// Fused pull collide-and-stream of one time step, one site per thread.
-//   gather   d_i = slot(i, x) through the table (coalesced table reads,
-//            gathered population reads, Morton order keeps them local);
-//   collide  collide() above;
-//   iolets   sites with iolet links come last in the internal order
-//            (x >= n_bulk): iolet_override() above;
-//   stream   q coalesced streaming stores at the site's own slots.
-// All slot offsets are 32-bit (q * npad < 2^31 is checked at create).
-// IO = false: the bulk sites [0, n_bulk); IO = true: the sites with an
-// iolet link [n_bulk, n), launched separately so that the bulk kernel carries
-// no iolet code (and no register cost for it).
-template <int Q, bool HALF, bool IO>
-__global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
-k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
-       typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
-       const double *__restrict__ rho_io) {
-    using R = Raw<HALF>;
-    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
-    if (x >= (IO ? L.n : L.n_bulk)) return;
-    const unsigned np = (unsigned)L.npad;
-    int s[Q];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
-    float d[Q];
-    d[0] = R::ld(fin + x);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
-                                     : (unsigned)opp(i) * np + (unsigned)x;
-        d[i] = R::ld(fin + e);
-    }
-    float out[Q];
-    const Velocity v = collide<Q, HALF>(L, d, out);
-    if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
-}
-
-// AA-pattern in-place step on one population buffer A (Bailey et al.,
-// "Accelerating lattice Boltzmann fluid flow simulations using graphics
-// processors", ICPP 2009).  Population i of site x is read from its slot and
-// the post-collision population opp(i) is written back into that same slot,
-// so every slot is read and written by one thread only:
-//   even step: slot_i = A[i][x]                  (own site, no table for bulk sites)
-//   odd step:  slot_i = A[opp(i)][x - c_i]       (through the table), or
-//              A[i][x] for a wall or iolet link opp(i).
-// After an even step A holds the populations of time t+1 in swapped slots;
-// after an odd step they are back in natural order, A[i][x] = f_i(x).
-#ifndef HGB_AA_MINB_FP32
-#define HGB_AA_MINB_FP32 3
-#endif
-#ifndef HGB_AA_MINB_FP16
-#define HGB_AA_MINB_FP16 3
-#endif
-template <int Q, bool HALF, bool ODD, bool IO>
-__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
-k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const IoletStep io,
-          const double *__restrict__ rho_io) {
-    using R = Raw<HALF>;
-    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
-    if (x >= (IO ? L.n : L.n_bulk)) return;
-    const unsigned np = (unsigned)L.npad;
-    int s[Q];
-    s[0] = 0;
-    if (ODD || IO) {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
-    }
-    float d[Q];
-    float out[Q];
-    if (!ODD) {
-        // own slots: one base pointer, plane stride np
-        typename Raw<HALF>::T *a = A + x;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
-        const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
-    } else {
-        // slot of population i (32-bit element offset)
-        auto slot = [&](int i) -> unsigned {
-            if (i == 0) return (unsigned)x;
-            return s[i] >= 0 ? (unsigned)opp(i) * np + (unsigned)s[i] : (unsigned)i * np + (unsigned)x;
-        };
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
-        const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
-    }
-}
-
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock)
 k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
@@ -434,8 +211,13 @@ k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
     using S = Store<HALF>;
     double acc = 0.0;
     for (int x = blockIdx.x * kBlock + threadIdx.x; x < L.n; x += gridDim.x * kBlock) {
+        // the q slots of a site are summed in float (deviations, ~1e-3 of
+        // the density), the sites in float64: float64 per slot costs q double
+        // additions per site, several times the time of reading the slots
+        float s = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) acc += (double)S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
+        for (int i = 0; i < Q; ++i) s += S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
+        acc += (double)s;
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -500,48 +282,11 @@ k_relayout(const DevLattice L, const T *__restrict__ src, int src_layout, T *__r
 
 inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-template <int Q, bool HALF>
-cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                         const double *rho_io, cudaStream_t s) {
-    using T = typename Raw<HALF>::T;
-    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
-    if (odd) {
-        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-    } else {
-        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-    }
-    return cudaGetLastError();
-}
-
-template <int Q, bool HALF>
-cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                      const double *rho_io, cudaStream_t s) {
-    using T = typename Raw<HALF>::T;
-    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
-    if (nb) k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
-    if (ni) k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 #define HGB_DISPATCH(L, FN, ...)                                                         \
     ((L).q == 15 ? ((L).storage ? FN<15, true>(__VA_ARGS__) : FN<15, false>(__VA_ARGS__)) \
                  : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
-
-cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                        const double *rho_io, cudaStream_t s) {
-    if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
-}
-
-cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                           const double *rho_io, cudaStream_t s) {
-    if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s);
-}
 
 cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,
                             int dst_layout, cudaStream_t s) {

@@ -1,0 +1,459 @@
+// Step kernels of libhemelb_gb300 (sm_103a): the fused collide-and-stream
+// update of the sparse, Morton-ordered site list in its three forms (pull,
+// table-staged persistent pull, AA in place), all built on one collision
+// function.
+//
+// The method (arXiv 1906.11925, Section 2): collision then propagation of a
+// single-particle distribution on a sparse lattice of fluid sites, D3Q19
+// (Fig. 1); simple bounce-back walls (Section 4).  Collision is LBGK with the
+// compressible second-order equilibrium; iolets impose a density through the
+// equilibrium populations entering from the iolet (see lbm.h).
+//
+// Pull storage: the buffer read at step t holds, for every site x and
+// direction i, the slot P_i(x) that the pull of step t reads; this is the
+// post-collision population f*_i(x, t-1) for fluid and wall links, and for
+// an iolet link the equilibrium population already evaluated at the iolet
+// density.  Reading the slots through the table (lbm_internal.h) is a
+// permutation, so the gather reproduces f(t) exactly.  Values are
+// deviations d = f - w_i rho0, in float or in IEEE half scaled by 2^S.
+//
+// The step is a bandwidth-bound sparse stencil (about one flop per byte): no
+// tensor cores.  One site per thread; the q - 1 table entries are coalesced
+// (or staged in shared memory by bulk asynchronous copies); the q population
+// reads are gathers through the read-only path, made local by the Morton
+// order; the q stores are coalesced and streamed.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "lattice.h"
+#include "lbm_internal.h"
+
+namespace hemelb_gb300 {
+namespace {
+
+constexpr int kBlock = 256;
+// resident blocks per SM requested from the register allocator for the step
+// kernel (fp32 storage, fp16 storage)
+#ifndef HGB_STEP_MINB_FP32
+#define HGB_STEP_MINB_FP32 3
+#endif
+#ifndef HGB_STEP_MINB_FP16
+#define HGB_STEP_MINB_FP16 4
+#endif
+
+inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// Raw stored values for the step kernel: fp16 values stay in their scaled
+// units (d * 2^S) through the whole update, so that no load or store pays a
+// multiplication; only rho and u are formed in real units.
+template <bool HALF>
+struct Raw;
+
+// Cache policy of the in-place AA kernels: 1 = evict-first (.cs), 0 = default
+#ifndef HGB_AA_LD_CS
+#define HGB_AA_LD_CS 0
+#endif
+#ifndef HGB_AA_ST_CS
+#define HGB_AA_ST_CS 1
+#endif
+
+template <>
+struct Raw<false> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_rw(const float *p) { return HGB_AA_LD_CS ? __ldcs(p) : *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+    static __device__ __forceinline__ void st_rw(float *p, float v) {
+        if (HGB_AA_ST_CS) __stcs(p, v);
+        else *p = v;
+    }
+};
+
+template <>
+struct Raw<true> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_rw(const __half *p) {
+        return HGB_AA_LD_CS ? __half2float(__short_as_half(__ldcs(reinterpret_cast<const short *>(p))))
+                            : __half2float(*p);
+    }
+    static __device__ __forceinline__ void st_rw(__half *p, float v) {
+        if (HGB_AA_ST_CS) __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
+        else *p = __float2half_rn(v);
+    }
+    static __device__ __forceinline__ void st(__half *p, float v) {
+        __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
+    }
+};
+
+// Velocity moments of one site after its collision (for the iolet values).
+struct Velocity {
+    float ux, uy, uz, usq15;
+};
+
+// LBGK collision of one site in stored units (deviations, times 2^S for
+// fp16), written per opposite pair (i, opp i): with cu = c_i.u the
+// equilibrium deviations are sym +- asym, sym = w (drho + rho (4.5 cu^2 -
+// 1.5 u^2)), asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i.
+// Every step kernel (pull, AA even, AA odd) uses this one function, so all
+// streaming forms give bitwise identical populations.
+template <int Q, bool HALF>
+__device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d)[Q], float (&out)[Q]) {
+    float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sum = d[i] + d[i + 1], dif = d[i] - d[i + 1];
+        drs += sum;
+        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
+        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
+        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
+    }
+    const float rho = HALF ? fmaf(drs, L.inv_scale, L.rho0) : L.rho0 + drs;
+    const float ir = (HALF ? L.inv_scale : 1.0f) / rho;
+    Velocity v;
+    v.ux = jx * ir;
+    v.uy = jy * ir;
+    v.uz = jz * ir;
+    v.usq15 = 1.5f * (v.ux * v.ux + v.uy * v.uy + v.uz * v.uz);
+    const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
+    const float om = L.omega, omc = 1.0f - L.omega;
+    {
+        const float w0 = (float)wdir<Q>(0);
+        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * v.usq15));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = (float)wdir<Q>(i);
+        const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
+        const float t = fmaf(4.5f * cu, cu, -v.usq15);
+        const float sym = fmaf(om * w * rs, t, om * w * drs);
+        const float asym = (3.0f * om * w * rs) * cu;
+        out[i] = fmaf(omc, d[i], sym + asym);
+        out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
+    }
+    return v;
+}
+
+// Iolet links of a site with an iolet link (x >= n_bulk): for every i whose
+// table entry s[i] = -2 - k marks link opp(i) as iolet k, the population
+// that re-enters the site as population i at the next step is the
+// equilibrium at the iolet density and the site's current velocity; it
+// replaces the outgoing f*_opp(i), which leaves the domain.
+template <int Q, bool HALF>
+__device__ __forceinline__ void iolet_override(const DevLattice &L, const int (&s)[Q], const Velocity &v,
+                                               const IoletStep &io, const double *__restrict__ rho_io,
+                                               float (&out)[Q]) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (s[i] <= -2) {
+            const int k = -2 - s[i];
+            float drk, rk;
+            if (rho_io) {
+                const double r = rho_io[k];
+                drk = (float)(r - (double)L.rho0);
+                rk = (float)r;
+            } else {
+                drk = io.drho[k];
+                rk = io.rho[k];
+            }
+            if (HALF) {
+                drk *= L.scale;
+                rk *= L.scale;
+            }
+            const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
+            out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - v.usq15));
+        }
+    }
+}
+
+// Fused pull collide-and-stream of one time step, one site per thread.
+//   gather   d_i = slot(i, x) through the table (coalesced table reads,
+//            gathered population reads, Morton order keeps them local);
+//   collide  collide() above;
+//   iolets   sites with iolet links come last in the internal order
+//            (x >= n_bulk): iolet_override() above;
+//   stream   q coalesced streaming stores at the site's own slots.
+// All slot offsets are 32-bit (q * npad < 2^31 is checked at create).
+// IO = false: the bulk sites [0, n_bulk); IO = true: the sites with an
+// iolet link [n_bulk, n), launched separately so that the bulk kernel carries
+// no iolet code (and no register cost for it).
+template <int Q, bool HALF, bool IO>
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
+k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
+       typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
+       const double *__restrict__ rho_io) {
+    using R = Raw<HALF>;
+    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
+    if (x >= (IO ? L.n : L.n_bulk)) return;
+    const unsigned np = (unsigned)L.npad;
+    int s[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    float d[Q];
+    d[0] = R::ld(fin + x);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
+                                     : (unsigned)opp(i) * np + (unsigned)x;
+        d[i] = R::ld(fin + e);
+    }
+    float out[Q];
+    const Velocity v = collide<Q, HALF>(L, d, out);
+    if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Table-staged persistent variant of the pull step (bulk sites only).  Each
+// CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; one thread
+// copies the q - 1 table rows of a tile (256 int32 each) into shared memory
+// with bulk asynchronous copies completing on an mbarrier, two tiles ahead,
+// so the table reads leave the threads' load path and arrive while the
+// previous tile computes.  Every wait is bounded: on a timeout the CTA sets
+// *err, waits (bounded) for its other copy in flight, and returns.
+#ifndef HGB_STEP_STAGED
+#define HGB_STEP_STAGED 1
+#endif
+#ifndef HGB_STAGES
+#define HGB_STAGES 2
+#endif
+constexpr int kStages = HGB_STAGES;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
+k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
+              typename Raw<HALF>::T *__restrict__ fout, int *__restrict__ err) {
+    using R = Raw<HALF>;
+    constexpr int NE = Q - 1;
+    extern __shared__ __align__(128) int32_t stab[];  // [kStages][NE][kBlock]
+    __shared__ __align__(8) uint64_t bar[kStages];
+    __shared__ int ok;
+    const int tid = threadIdx.x;
+    const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
+    const unsigned np = (unsigned)L.npad;
+    auto issue = [&](int stage, int tile) {
+        // ragged last tile: round the row up to 16 bytes (stays inside the
+        // plane: npad is a multiple of 128 and >= n_bulk)
+        const int count = min(kBlock, L.n_bulk - tile * kBlock);
+        const unsigned bytes = ((unsigned)count * 4u + 15u) & ~15u;
+        mbar_expect_tx(&bar[stage], bytes * NE);
+#pragma unroll 1
+        for (int i = 0; i < NE; ++i)
+            bulk_g2s(stab + (stage * NE + i) * kBlock, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes,
+                     &bar[stage]);
+    };
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int st = 0; st < kStages; ++st) {
+            const int tile = blockIdx.x + st * gridDim.x;
+            if (tile < ntiles) issue(st, tile);
+        }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int stage = k % kStages;
+        const unsigned parity = (unsigned)(k / kStages) & 1u;
+        if (tid == 0) ok = mbar_wait_bounded(&bar[stage], parity) ? 1 : 0;
+        __syncthreads();
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // the other stage's copy, if one is in flight
+                const int other = tile + gridDim.x;
+                if (other < ntiles) mbar_wait_bounded(&bar[(k + 1) % kStages], (unsigned)((k + 1) / kStages) & 1u);
+            }
+            return;
+        }
+        const int x = tile * kBlock + tid;
+        if (x < L.n_bulk) {
+            int s[Q];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) s[i] = stab[(stage * NE + i - 1) * kBlock + tid];
+            float d[Q];
+            d[0] = R::ld(fin + x);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
+                                             : (unsigned)opp(i) * np + (unsigned)x;
+                d[i] = R::ld(fin + e);
+            }
+            float out[Q];
+            collide<Q, HALF>(L, d, out);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
+        }
+        __syncthreads();  // every thread is done with this stage's rows
+        if (tid == 0) {
+            const int nt = tile + kStages * gridDim.x;
+            if (nt < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(stage, nt);
+            }
+        }
+    }
+}
+
+// AA-pattern in-place step on one population buffer A (Bailey et al.,
+// "Accelerating lattice Boltzmann fluid flow simulations using graphics
+// processors", ICPP 2009).  Population i of site x is read from its slot and
+// the post-collision population opp(i) is written back into that same slot,
+// so every slot is read and written by one thread only:
+//   even step: slot_i = A[i][x]                  (own site, no table for bulk sites)
+//   odd step:  slot_i = A[opp(i)][x - c_i]       (through the table), or
+//              A[i][x] for a wall or iolet link opp(i).
+// After an even step A holds the populations of time t+1 in swapped slots;
+// after an odd step they are back in natural order, A[i][x] = f_i(x).
+#ifndef HGB_AA_MINB_FP32
+#define HGB_AA_MINB_FP32 3
+#endif
+#ifndef HGB_AA_MINB_FP16
+#define HGB_AA_MINB_FP16 3
+#endif
+template <int Q, bool HALF, bool ODD, bool IO>
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
+k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const IoletStep io,
+          const double *__restrict__ rho_io) {
+    using R = Raw<HALF>;
+    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
+    if (x >= (IO ? L.n : L.n_bulk)) return;
+    const unsigned np = (unsigned)L.npad;
+    int s[Q];
+    s[0] = 0;
+    if (ODD || IO) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    }
+    float d[Q];
+    float out[Q];
+    if (!ODD) {
+        // own slots: one base pointer, plane stride np
+        typename Raw<HALF>::T *a = A + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+        const Velocity v = collide<Q, HALF>(L, d, out);
+        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
+    } else {
+        // slot of population i (32-bit element offset)
+        auto slot = [&](int i) -> unsigned {
+            if (i == 0) return (unsigned)x;
+            return s[i] >= 0 ? (unsigned)opp(i) * np + (unsigned)s[i] : (unsigned)i * np + (unsigned)x;
+        };
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
+        const Velocity v = collide<Q, HALF>(L, d, out);
+        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
+    }
+}
+
+template <int Q, bool HALF>
+cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
+                         const double *rho_io, cudaStream_t s) {
+    using T = typename Raw<HALF>::T;
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (odd) {
+        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+    } else {
+        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, bool HALF>
+cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
+                      const double *rho_io, cudaStream_t s) {
+    using T = typename Raw<HALF>::T;
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (nb) {
+        if (HGB_STEP_STAGED && L.err) {
+            static int grid_cache[2] = {0, 0};
+            const size_t smem = (size_t)kStages * (Q - 1) * kBlock * 4;
+            int &g = grid_cache[HALF ? 1 : 0];
+            if (g == 0) {
+                int dev = 0, sms = 0, per = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (smem > 48 * 1024) {
+                    cudaError_t e = cudaFuncSetAttribute(k_step_staged<Q, HALF>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return e;
+                }
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_staged<Q, HALF>, kBlock, smem);
+                g = std::max(1, sms * std::max(per, 1));
+            }
+            const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
+            k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, (T *)fout, L.err);
+        } else {
+            k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+        }
+    }
+    if (ni) k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HGB_DISPATCH(L, FN, ...)                                                         \
+    ((L).q == 15 ? ((L).storage ? FN<15, true>(__VA_ARGS__) : FN<15, false>(__VA_ARGS__)) \
+                 : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
+
+cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
+                        const double *rho_io, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
+}
+
+cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
+                           const double *rho_io, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s);
+}
+
+}  // namespace hemelb_gb300

@@ -46,8 +46,9 @@ def test_aa_is_bitwise_equal_to_pull(q, storage):
         ra, ua, wa = [t.cpu().numpy() for t in A.macros()]
         rp, up, wp = [t.cpu().numpy() for t in P.macros()]
         assert np.array_equal(ra, rp) and np.array_equal(ua, up) and np.array_equal(wa, wp)
-        # the mass sums raw slots per site, grouped differently in each layout
-        assert abs(A.mass() - P.mass()) <= 1e-12 * P.mass()
+        # the mass sums raw slots per site (in float, then float64 over the
+        # sites), and the slots of a site are grouped differently in each layout
+        assert abs(A.mass() - P.mass()) <= 1e-9 * P.mass()
         assert np.array_equal(A.get_populations_noalloc(), P.get_populations())
     A.step(1)  # even count again
     P.step(1)
