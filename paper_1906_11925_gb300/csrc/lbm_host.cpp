@@ -36,6 +36,9 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     void *f_cur = nullptr, *f_nxt = nullptr;
     int32_t *tab = nullptr, *perm = nullptr;
+    uint8_t *c16_rec = nullptr;
+    int32_t *c16_esc = nullptr;
+    uint32_t *c16_off = nullptr, *c16_cnt = nullptr;
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
     double *partials = nullptr, *mass_dev = nullptr;
@@ -153,6 +156,86 @@ inline uint64_t spread3(uint64_t v) {
     v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
     v = (v | v << 2) & 0x1249249249249249ULL;
     return v;
+}
+
+// Compressed table of the bulk sites [0, n_bulk) (format in lbm_internal.h).
+struct CompressedTable {
+    std::vector<uint8_t> rec;
+    std::vector<int32_t> esc;
+    std::vector<uint32_t> off, cnt;
+};
+
+bool compress_table(int q, int64_t npad, int64_t n_bulk, const std::vector<int32_t> &tab,
+                    CompressedTable &ct) {
+    const int ne = q - 1;
+    const int64_t tiles = (n_bulk + kTile - 1) / kTile;
+    const size_t rb = (size_t)tile_record_bytes(q);
+    ct.rec.assign((size_t)tiles * rb, 0);
+    ct.off.assign((size_t)tiles, 0);
+    ct.cnt.assign((size_t)tiles, 0);
+    std::vector<std::vector<int32_t>> tile_esc((size_t)tiles);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < tiles; ++t) {
+        int16_t *r16 = reinterpret_cast<int16_t *>(ct.rec.data() + (size_t)t * rb);
+        uint16_t *pre = reinterpret_cast<uint16_t *>(ct.rec.data() + (size_t)t * rb + (size_t)ne * kTile * 2);
+        std::vector<int32_t> &e = tile_esc[(size_t)t];
+        for (int i = 0; i < ne; ++i) {
+            for (int w = 0; w < kTile / 32; ++w) {
+                pre[i * 8 + w] = (uint16_t)std::min<size_t>(e.size(), 0xffff);
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t x = t * kTile + w * 32 + l;
+                    int code = 0;
+                    if (x < n_bulk) {
+                        const int32_t v = tab[(size_t)i * npad + x];
+                        const int64_t d = (int64_t)v - x;
+                        if (v == -1) code = kCodeWall;
+                        else if (v >= 0 && d >= -32766 && d <= 32767) code = (int)d;
+                        else {
+                            code = kCodeEscape;
+                            e.push_back(v);
+                        }
+                    }
+                    r16[(size_t)i * kTile + w * 32 + l] = (int16_t)code;
+                }
+            }
+        }
+    }
+    for (int64_t t = 0; t < tiles; ++t) {
+        std::vector<int32_t> &e = tile_esc[(size_t)t];
+        if (e.size() > (size_t)kEscapeCap) {
+            ct.cnt[(size_t)t] = kTileFallback;
+            ct.off[(size_t)t] = 0;
+            continue;
+        }
+        while (e.size() % 4) e.push_back(0);  // 16-byte segments
+        ct.off[(size_t)t] = (uint32_t)ct.esc.size();
+        ct.cnt[(size_t)t] = (uint32_t)e.size();
+        ct.esc.insert(ct.esc.end(), e.begin(), e.end());
+    }
+    if (ct.esc.empty()) ct.esc.assign(4, 0);
+    // decode every entry and compare (lossless by construction; checked anyway)
+    bool ok = true;
+#pragma omp parallel for schedule(static) reduction(&& : ok)
+    for (int64_t t = 0; t < tiles; ++t) {
+        if (ct.cnt[(size_t)t] == kTileFallback) continue;
+        const int16_t *r16 = reinterpret_cast<const int16_t *>(ct.rec.data() + (size_t)t * rb);
+        const uint16_t *pre =
+            reinterpret_cast<const uint16_t *>(ct.rec.data() + (size_t)t * rb + (size_t)ne * kTile * 2);
+        for (int i = 0; i < ne; ++i)
+            for (int w = 0; w < kTile / 32; ++w) {
+                int rank = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t x = t * kTile + w * 32 + l;
+                    const int code = r16[(size_t)i * kTile + w * 32 + l];
+                    int64_t v;
+                    if (code == kCodeEscape) v = ct.esc[ct.off[(size_t)t] + pre[i * 8 + w] + rank++];
+                    else if (code == kCodeWall) v = -1;
+                    else v = x + code;
+                    if (x < n_bulk && v != tab[(size_t)i * npad + x]) ok = false;
+                }
+            }
+    }
+    return ok;
 }
 
 // Iolet densities of step t: rho_k(t) = mean + amp sin(2 pi t / period + phase),
@@ -344,6 +427,10 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->f_cur);
     cudaFree(c->f_nxt);
     cudaFree(c->tab);
+    cudaFree(c->c16_rec);
+    cudaFree(c->c16_esc);
+    cudaFree(c->c16_off);
+    cudaFree(c->c16_cnt);
     cudaFree(c->perm);
     cudaFree(c->partials);
     cudaFree(c->err_flag);
@@ -384,6 +471,9 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     const size_t eb = elem_bytes(p->storage);
     const size_t nbuf = p->streaming == LBM_STREAM_AA ? 1 : 2;
     const size_t need = nbuf * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
+                        (kUseCompressedTable ? ((size_t)npad / kTile + 1) * (size_t)tile_record_bytes(q) +
+                                                   (size_t)npad * 8
+                                             : 0) +
                         (size_t)(mass_blocks() + 8) * 8;
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
@@ -435,6 +525,10 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         }
     }
 
+    CompressedTable ct;
+    if (kUseCompressedTable && !compress_table(q, npad, n_bulk, tab, ct))
+        return fail(nullptr, LBM_ERR_TABLE, "internal error: compressed table does not decode");
+
     lbm_ctx *c = new lbm_ctx();
     c->q = q;
     c->storage = p->storage;
@@ -471,6 +565,19 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(dmalloc(c, &c->err_flag, 16));
     CKC(cudaMemsetAsync(c->err_flag, 0, 16, c->stream));
     CKC(cudaMemcpyAsync(c->tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (kUseCompressedTable) {
+        CKC(dmalloc(c, &c->c16_rec, ct.rec.size()));
+        CKC(dmalloc(c, &c->c16_esc, ct.esc.size() * 4));
+        CKC(dmalloc(c, &c->c16_off, ct.off.size() * 4));
+        CKC(dmalloc(c, &c->c16_cnt, ct.cnt.size() * 4));
+        if (!ct.rec.empty())
+            CKC(cudaMemcpyAsync(c->c16_rec, ct.rec.data(), ct.rec.size(), cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaMemcpyAsync(c->c16_esc, ct.esc.data(), ct.esc.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        if (!ct.off.empty()) {
+            CKC(cudaMemcpyAsync(c->c16_off, ct.off.data(), ct.off.size() * 4, cudaMemcpyHostToDevice, c->stream));
+            CKC(cudaMemcpyAsync(c->c16_cnt, ct.cnt.data(), ct.cnt.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        }
+    }
     if (n) CKC(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
     DevLattice &L = c->L;
     L.q = q;
@@ -487,6 +594,10 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.tab = c->tab;
     L.perm = c->perm;
     L.err = c->err_flag;
+    L.c16_rec = c->c16_rec;
+    L.c16_esc = c->c16_esc;
+    L.c16_off = c->c16_off;
+    L.c16_cnt = c->c16_cnt;
     CKC(launch_zero(L, c->f_cur, c->stream));
     if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return

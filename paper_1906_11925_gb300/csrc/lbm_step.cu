@@ -259,19 +259,43 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+
+// bytes of one stage buffer: the larger of the int32 rows and the compressed
+// record plus a full escape list
+template <int Q>
+__host__ __device__ constexpr int stage_bytes() {
+    return (Q - 1) * kTile * 4 > tile_record_bytes(Q) + kEscapeCap * 4 ? (Q - 1) * kTile * 4
+                                                                        : tile_record_bytes(Q) + kEscapeCap * 4;
+}
+
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
 k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
               typename Raw<HALF>::T *__restrict__ fout, int *__restrict__ err) {
     using R = Raw<HALF>;
     constexpr int NE = Q - 1;
-    extern __shared__ __align__(128) int32_t stab[];  // [kStages][NE][kBlock]
+    constexpr int SB = stage_bytes<Q>();
+    constexpr int RB = tile_record_bytes(Q);
+    static_assert(kBlock == kTile, "one site per thread per tile");
+    extern __shared__ __align__(128) unsigned char sbuf[];  // [kStages][SB]
     __shared__ __align__(8) uint64_t bar[kStages];
+    __shared__ int fmt[kStages];  // 1: compressed record + escapes, 0: int32 rows
     __shared__ int ok;
     const int tid = threadIdx.x;
     const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
     const unsigned np = (unsigned)L.npad;
+    const bool c16 = kUseCompressedTable && L.c16_rec != nullptr;
     auto issue = [&](int stage, int tile) {
+        unsigned char *dst = sbuf + stage * SB;
+        const uint32_t cnt = c16 ? L.c16_cnt[tile] : kTileFallback;
+        if (cnt != kTileFallback) {
+            fmt[stage] = 1;
+            mbar_expect_tx(&bar[stage], (unsigned)RB + cnt * 4u);
+            bulk_g2s(dst, L.c16_rec + (size_t)tile * RB, (unsigned)RB, &bar[stage]);
+            if (cnt) bulk_g2s(dst + RB, L.c16_esc + L.c16_off[tile], cnt * 4u, &bar[stage]);
+            return;
+        }
+        fmt[stage] = 0;
         // ragged last tile: round the row up to 16 bytes (stays inside the
         // plane: npad is a multiple of 128 and >= n_bulk)
         const int count = min(kBlock, L.n_bulk - tile * kBlock);
@@ -279,8 +303,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         mbar_expect_tx(&bar[stage], bytes * NE);
 #pragma unroll 1
         for (int i = 0; i < NE; ++i)
-            bulk_g2s(stab + (stage * NE + i) * kBlock, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes,
-                     &bar[stage]);
+            bulk_g2s(dst + i * kBlock * 4, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
     };
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
@@ -291,6 +314,8 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         }
     }
     __syncthreads();
+    const int warp = tid >> 5;
+    const unsigned lt = (1u << (tid & 31)) - 1u;
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int stage = k % kStages;
@@ -307,10 +332,27 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
             return;
         }
         const int x = tile * kBlock + tid;
-        if (x < L.n_bulk) {
-            int s[Q];
+        const unsigned char *buf = sbuf + stage * SB;
+        int s[Q];
+        if (fmt[stage]) {
+            // every thread decodes (the ballots need the whole warp)
+            const int16_t *r16 = reinterpret_cast<const int16_t *>(buf);
+            const uint16_t *pre = reinterpret_cast<const uint16_t *>(buf + NE * kTile * 2);
+            const int32_t *escs = reinterpret_cast<const int32_t *>(buf + RB);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) s[i] = stab[(stage * NE + i - 1) * kBlock + tid];
+            for (int i = 1; i < Q; ++i) {
+                const int code = r16[(i - 1) * kTile + tid];
+                const bool esc = code == kCodeEscape;
+                const unsigned m = __ballot_sync(0xffffffffu, esc);
+                s[i] = esc ? escs[pre[(i - 1) * 8 + warp] + __popc(m & lt)]
+                           : (code == kCodeWall ? -1 : x + code);
+            }
+        } else {
+            const int32_t *r32 = reinterpret_cast<const int32_t *>(buf);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) s[i] = r32[(i - 1) * kTile + tid];
+        }
+        if (x < L.n_bulk) {
             float d[Q];
             d[0] = R::ld(fin + x);
 #pragma unroll
@@ -324,7 +366,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #pragma unroll
             for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
         }
-        __syncthreads();  // every thread is done with this stage's rows
+        __syncthreads();  // every thread is done with this stage's buffer
         if (tid == 0) {
             const int nt = tile + kStages * gridDim.x;
             if (nt < ntiles) {
@@ -414,7 +456,7 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
     if (nb) {
         if (HGB_STEP_STAGED && L.err) {
             static int grid_cache[2] = {0, 0};
-            const size_t smem = (size_t)kStages * (Q - 1) * kBlock * 4;
+            const size_t smem = (size_t)kStages * stage_bytes<Q>();
             int &g = grid_cache[HALF ? 1 : 0];
             if (g == 0) {
                 int dev = 0, sms = 0, per = 0;
