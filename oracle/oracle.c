@@ -241,12 +241,23 @@ int orc_links_build(int q, int64_t n, const int32_t *xyz, int64_t n_io,
  *   2. post-collision f*_i = f_i - (f_i - feq_i) / tau;
  *   3. for each i: fluid link -> fout_i(nbr) = f*_i;
  *                  wall link  -> fout_opp(i)(x) = f*_i   (halfway bounce-back);
- *                  iolet k    -> fout_opp(i)(x) = feq_opp(i)(rho_k(t), u).
+ *                  iolet k    -> fout_opp(i)(x) = feq_opp(i)(rho_k(t), u)
+ *                                (density iolet), or
+ *                  iolet k    -> fout_opp(i)(x) = f*_i - 6 w_i rho (c_i . u_b)
+ *                                (velocity iolet: bounce-back from a boundary
+ *                                moving with u_b = weight[x] U_k(t) n_k, Ladd's
+ *                                moving-wall rule with c_s^2 = 1/3; the paper
+ *                                drives its inlet this way, Sections 2 and 3.2,
+ *                                Table I).
+ * The schedule mean/amp/period/phase gives rho_k(t) for a density iolet and
+ * the velocity magnitude U_k(t) for a velocity iolet (io_kind[k] = 1, unit
+ * inward normal io_normal[3k..3k+2]); weight may be NULL (all 1).
  */
-int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
-             int n_io, const double *rho_mean, const double *amp,
-             const double *period, const double *phase, int64_t t,
-             const double *f, double *fout) {
+int orc_step_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                int n_io, const double *rho_mean, const double *amp,
+                const double *period, const double *phase, const int32_t *io_kind,
+                const double *io_normal, const double *weight, int64_t t,
+                const double *f, double *fout) {
     lattice_t L;
     if (get_lattice(q, &L)) return -1;
 #pragma omp parallel for schedule(static)
@@ -262,6 +273,13 @@ int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double t
                 fout[(int64_t)i * n + nbr[(int64_t)i * n + x]] = fs;
             } else if (lk == 1) {
                 fout[(int64_t)L.opp[i] * n + x] = fs;
+            } else if (io_kind && io_kind[lk - 2] == 1) {
+                int k = lk - 2;
+                double U = iolet_rho(k, t, rho_mean, amp, period, phase);
+                double wx = weight ? weight[x] : 1.0;
+                double cub = 0.0;
+                for (int a = 0; a < 3; ++a) cub += L.e[i][a] * wx * U * io_normal[3 * k + a];
+                fout[(int64_t)L.opp[i] * n + x] = fs - 6.0 * L.w[i] * rho * cub;
             } else {
                 int k = lk - 2;
                 double feq_k[19];
@@ -275,19 +293,36 @@ int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double t
     return 0;
 }
 
+int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+             int n_io, const double *rho_mean, const double *amp,
+             const double *period, const double *phase, int64_t t,
+             const double *f, double *fout) {
+    return orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
+                       t, f, fout);
+}
+
 /* nsteps steps from time t0; f holds the state on entry and on exit;
  * work is scratch of the same size. */
-int orc_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
-            int n_io, const double *rho_mean, const double *amp, const double *period,
-            const double *phase, int64_t t0, int64_t nsteps, double *f, double *work) {
+int orc_run_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+               int n_io, const double *rho_mean, const double *amp, const double *period,
+               const double *phase, const int32_t *io_kind, const double *io_normal,
+               const double *weight, int64_t t0, int64_t nsteps, double *f, double *work) {
     double *a = f, *b = work;
     for (int64_t s = 0; s < nsteps; ++s) {
-        int r = orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t0 + s, a, b);
+        int r = orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, io_kind,
+                            io_normal, weight, t0 + s, a, b);
         if (r) return r;
         double *tmp = a; a = b; b = tmp;
     }
     if (a != f) memcpy(f, a, sizeof(double) * (size_t)q * (size_t)n);
     return 0;
+}
+
+int orc_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+            int n_io, const double *rho_mean, const double *amp, const double *period,
+            const double *phase, int64_t t0, int64_t nsteps, double *f, double *work) {
+    return orc_run_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
+                      t0, nsteps, f, work);
 }
 
 /* --------------------------------------------------------------- macros */

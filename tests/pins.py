@@ -372,3 +372,49 @@ ALL_FAST += [
     ("adjoint_wss15", lambda o: pin_adjoint_gradient(o, 15, 0)),
     ("adjoint_density19", lambda o: pin_adjoint_gradient(o, 19, 1)),
 ]
+
+
+# ---------------------------------------------------------------- velocity iolets
+
+def _ladd_slab(o, q, ny, weight_fn, steps):
+    """Channel along x, periodic in y and z, no walls: iolet 0 (x = -1) is a
+    density outlet, iolet 1 (x = 12) a velocity inlet pushing in -x (using the
+    second iolet also checks that the iolet's own normal is used)."""
+    g = G.slab(12, ny, 1, rho_in=1.0, rho_out=1.0)
+    g.periodic[:] = (0, ny, 1)
+    nbr, link = o.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    U = 0.01
+    x, y, z = g.xyz.T
+    w = weight_fn(x, y, z)
+    f = o.run_bc(q, nbr, link, 1.5, o.rest_state(q, g.n), steps, io_kind=[0, 1],
+                 io_normal=[[0, 0, 0], [-1, 0, 0]], weight=w, rho_mean=[1.0, U])
+    rho, u, _ = o.macros(q, link, 1.5, f)
+    return g, x, y, w, U, rho, u
+
+
+def pin_ladd_plug(o, q):
+    """Velocity (Ladd) inlet with uniform weight w, density outlet, no walls
+    (periodic cross-section): the steady flow is the plug u = -w U (the inlet
+    pushes along its normal -x), and rho u is constant along the channel."""
+    g, x, y, w, U, rho, u = _ladd_slab(o, q, 1, lambda x, y, z: np.full(x.shape, 0.5), 6000)
+    assert np.abs(-u[:, 0] / (0.5 * U) - 1.0).max() < 1e-9, u[:, 0]
+    assert np.abs(u[:, 1:]).max() == 0.0
+
+
+def pin_ladd_flux(o, q):
+    """Non-uniform weights across the channel: at steady state the mass flux
+    through every cross-section equals the inflow, the sum over the inlet
+    sites of rho(x) w(x) U (each inlet site has all its +x links on the
+    iolet)."""
+    g, x, y, w, U, rho, u = _ladd_slab(o, q, 4, lambda x, y, z: 0.5 + 0.5 * y, 8000)
+    inlet = x == 11
+    inflow = float(np.sum(rho[inlet] * w[inlet] * U))
+    for k in range(12):
+        flux = -float(np.sum(rho[x == k] * u[x == k, 0]))
+        assert abs(flux / inflow - 1.0) < 1e-9, (k, flux, inflow)
+
+
+ALL_FAST += [
+    ("ladd_plug19", lambda o: pin_ladd_plug(o, 19)),
+    ("ladd_flux15", lambda o: pin_ladd_flux(o, 15)),
+]

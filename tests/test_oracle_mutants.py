@@ -34,6 +34,10 @@ MUTANTS = {
     "adj_tau_power": ("(g[i] - feq[i]) / (tau * tau);", "(g[i] - feq[i]) / tau;"),
     "adj_wall_lambda": ("ls[i] = lam_next[(int64_t)L.opp[i] * n + x];", "ls[i] = lam_next[(int64_t)i * n + x];"),
     "adj_velocity_term": ("double dj = (L.e[j][c] - u[c]) / rho;", "double dj = L.e[j][c] / rho;"),
+    "ladd_factor": ("fs - 6.0 * L.w[i] * rho * cub;", "fs - 3.0 * L.w[i] * rho * cub;"),
+    "ladd_sign": ("fs - 6.0 * L.w[i] * rho * cub;", "fs + 6.0 * L.w[i] * rho * cub;"),
+    "ladd_weight_ignored": ("double wx = weight ? weight[x] : 1.0;", "double wx = 1.0;"),
+    "ladd_normal_index": ("wx * U * io_normal[3 * k + a];", "wx * U * io_normal[a];"),
     "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
                   "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }

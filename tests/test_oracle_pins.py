@@ -85,3 +85,13 @@ def test_adjoint_dot_product(o, q):
 @pytest.mark.parametrize("kind", [0, 1])
 def test_adjoint_gradient_vs_central_differences(o, q, kind):
     pins.pin_adjoint_gradient(o, q, kind)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_velocity_iolet_plug_flow(o, q):
+    pins.pin_ladd_plug(o, q)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_velocity_iolet_flux_balance(o, q):
+    pins.pin_ladd_flux(o, q)
