@@ -66,6 +66,7 @@ typedef enum {
 
 enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1 };
 enum { LBM_STREAM_PULL = 0, LBM_STREAM_AA = 1 };
+enum { LBM_IOLET_DENSITY = 0, LBM_IOLET_VELOCITY = 1 };
 enum { LBM_MAX_IOLETS = 64 };
 
 typedef struct lbm_ctx lbm_ctx; /* opaque */
@@ -82,6 +83,19 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *   fp16_scale_log2  S in [0, 24]; ignored for LBM_STORE_FP32.
  *   n_iolets   K in [0, LBM_MAX_IOLETS]; the four arrays hold K doubles each
  *              (host memory, may be NULL when K = 0).
+ *   iolet_kind K int32 or NULL (all density iolets): LBM_IOLET_DENSITY, or
+ *              LBM_IOLET_VELOCITY: a link into the iolet bounces back from a
+ *              boundary moving with u_b = velocity_weight[x] U_k(t) n_k (Ladd's
+ *              moving-wall rule, f_opp(i) = f*_i - 6 w_i rho c_i.u_b); the paper
+ *              drives its inlet this way (Sections 2 and 3.2, Table I).  For a
+ *              velocity iolet the schedule (rho_mean, amp, period, phase) gives
+ *              the speed U_k(t), and the driven densities of lbm_step_driven
+ *              are speeds too.
+ *   iolet_normal  K x 3 doubles (unit inward normals of the velocity iolets);
+ *              may be NULL when there is none.
+ *   velocity_weight  n doubles, caller order, or NULL (all 1): the per-site
+ *              profile of the velocity iolets (the paper's velocity weights
+ *              file, Section 3.2).
  *   streaming  LBM_STREAM_PULL: two population buffers, every step gathers
  *              through the neighbour table.  LBM_STREAM_AA: one buffer updated
  *              in place by the AA pattern (even steps touch only a site's own
@@ -100,6 +114,9 @@ typedef struct {
     const double *period;
     const double *phase;
     int32_t streaming;
+    const int32_t *iolet_kind;
+    const double *iolet_normal;
+    const double *velocity_weight;
 } lbm_params;
 
 /* Neighbour-link table of a sparse site list (Section 2: every fluid site
@@ -212,7 +229,8 @@ lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link);
  * Gradients of a time-windowed objective by the discrete adjoint of the step
  * (reverse mode), with binomial checkpointing of raw state snapshots.  Not in
  * the paper, whose method is the forward solver only (Section 2); this is
- * the differentiation of that solver. */
+ * the differentiation of that solver.  Contexts with velocity iolets are not
+ * differentiated (LBM_ERR_STATE). */
 enum { LBM_OBJ_WSS = 0, LBM_OBJ_DENSITY = 1 };
 
 /* J = scale * sum over the states f(t) with t_begin <= t < t_end (t counted

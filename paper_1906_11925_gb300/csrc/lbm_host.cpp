@@ -41,6 +41,10 @@ struct lbm_ctx {
     uint32_t *c16_off = nullptr, *c16_cnt = nullptr;
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
+    int io_kind[LBM_MAX_IOLETS] = {};
+    double io_normal[LBM_MAX_IOLETS][3] = {};
+    bool has_velocity_iolet = false;
+    float *vel_weight = nullptr;
     double *partials = nullptr, *mass_dev = nullptr;
     int *err_flag = nullptr;
     double *rho_io = nullptr;  // driven iolet densities, grown on demand
@@ -240,6 +244,7 @@ bool compress_table(int q, int64_t npad, int64_t n_bulk, const std::vector<int32
 
 // Iolet densities of step t: rho_k(t) = mean + amp sin(2 pi t / period + phase),
 // in float64 on the host; the kernel receives rho_k and rho_k - rho0 as float.
+// A velocity iolet carries its speed U_k(t) in rho[k] and its normal in nrm[k].
 IoletStep iolet_step(const lbm_ctx *c, int64_t t) {
     IoletStep s{};
     for (int k = 0; k < c->n_iolets; ++k) {
@@ -248,6 +253,10 @@ IoletStep iolet_step(const lbm_ctx *c, int64_t t) {
             r += c->io_amp[k] * std::sin(2.0 * M_PI * (double)t / c->io_period[k] + c->io_phase[k]);
         s.drho[k] = (float)(r - c->rho0);
         s.rho[k] = (float)r;
+        if (c->io_kind[k] == LBM_IOLET_VELOCITY) {
+            s.vel_mask |= 1ull << k;
+            for (int a = 0; a < 3; ++a) s.nrm[k][a] = (float)c->io_normal[k][a];
+        }
     }
     return s;
 }
@@ -355,9 +364,21 @@ lbm_status validate_params(const lbm_params *p) {
     if (p->n_iolets > 0 && (!p->rho_mean || !p->amp || !p->period || !p->phase))
         return fail(nullptr, LBM_ERR_ARG, "iolet arrays are NULL");
     for (int k = 0; k < p->n_iolets; ++k) {
-        if (!std::isfinite(p->rho_mean[k]) || !(p->rho_mean[k] > 0) || !std::isfinite(p->amp[k]) ||
-            !std::isfinite(p->period[k]) || p->period[k] < 0 || !std::isfinite(p->phase[k]))
+        const int kind = p->iolet_kind ? p->iolet_kind[k] : LBM_IOLET_DENSITY;
+        if (kind != LBM_IOLET_DENSITY && kind != LBM_IOLET_VELOCITY)
+            return fail(nullptr, LBM_ERR_ARG, "iolet kind must be LBM_IOLET_DENSITY or LBM_IOLET_VELOCITY");
+        if (!std::isfinite(p->rho_mean[k]) || !std::isfinite(p->amp[k]) || !std::isfinite(p->period[k]) ||
+            p->period[k] < 0 || !std::isfinite(p->phase[k]))
             return fail(nullptr, LBM_ERR_ARG, "bad iolet schedule");
+        if (kind == LBM_IOLET_DENSITY && !(p->rho_mean[k] > 0))
+            return fail(nullptr, LBM_ERR_ARG, "bad iolet schedule");
+        if (kind == LBM_IOLET_VELOCITY) {
+            if (!p->iolet_normal) return fail(nullptr, LBM_ERR_ARG, "velocity iolet without a normal");
+            const double *nv = p->iolet_normal + 3 * k;
+            const double nn = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+            if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6)
+                return fail(nullptr, LBM_ERR_ARG, "velocity iolet normal must be a unit vector");
+        }
     }
     return LBM_OK;
 }
@@ -427,6 +448,7 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->f_cur);
     cudaFree(c->f_nxt);
     cudaFree(c->tab);
+    cudaFree(c->vel_weight);
     cudaFree(c->c16_rec);
     cudaFree(c->c16_esc);
     cudaFree(c->c16_off);
@@ -545,6 +567,11 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         c->io_amp[k] = p->amp[k];
         c->io_period[k] = p->period[k];
         c->io_phase[k] = p->phase[k];
+        c->io_kind[k] = p->iolet_kind ? p->iolet_kind[k] : LBM_IOLET_DENSITY;
+        if (c->io_kind[k] == LBM_IOLET_VELOCITY) {
+            c->has_velocity_iolet = true;
+            for (int a = 0; a < 3; ++a) c->io_normal[k][a] = p->iolet_normal[3 * k + a];
+        }
     }
 #define CKC(call)                                   \
     do {                                            \
@@ -560,6 +587,16 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     if (c->streaming == LBM_STREAM_PULL) CKC(dmalloc(c, &c->f_nxt, fbytes));
     CKC(dmalloc(c, &c->tab, tab.size() * 4));
     CKC(dmalloc(c, &c->perm, (size_t)n * 4));
+    {
+        // velocity-iolet weights of the iolet sites, internal order
+        std::vector<float> wt((size_t)std::max<int64_t>(n - n_bulk, 1), 1.0f);
+        if (p->velocity_weight)
+            for (int64_t xi = n_bulk; xi < n; ++xi)
+                wt[(size_t)(xi - n_bulk)] = (float)p->velocity_weight[perm[(size_t)xi]];
+        CKC(dmalloc(c, &c->vel_weight, wt.size() * 4));
+        CKC(cudaMemcpyAsync(c->vel_weight, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaStreamSynchronize(c->stream));  // wt dies at the end of this block
+    }
     CKC(dmalloc(c, &c->partials, (size_t)mass_blocks() * 8));
     CKC(dmalloc(c, &c->mass_dev, 8));
     CKC(dmalloc(c, &c->err_flag, 16));
@@ -594,6 +631,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.tab = c->tab;
     L.perm = c->perm;
     L.err = c->err_flag;
+    L.vel_weight = c->vel_weight;
     L.c16_rec = c->c16_rec;
     L.c16_esc = c->c16_esc;
     L.c16_off = c->c16_off;
@@ -990,6 +1028,8 @@ HGB_API lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *
     p.amp = amp;
     p.period = period;
     p.phase = phase;
+    p.iolet_kind = ctx->io_kind;
+    p.iolet_normal = &ctx->io_normal[0][0];
     lbm_status st = validate_params(&p);
     if (st != LBM_OK) return fail(ctx, st, g_err);
     for (int k = 0; k < n_iolets; ++k) {
@@ -1009,6 +1049,8 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
         return fail(ctx, LBM_ERR_ARG, "objective kind must be LBM_OBJ_WSS or LBM_OBJ_DENSITY");
     if (ctx->n > 0 && !obj->weight) return fail(ctx, LBM_ERR_ARG, "objective weight is NULL");
     if (!std::isfinite(obj->scale)) return fail(ctx, LBM_ERR_ARG, "objective scale is not finite");
+    if (ctx->has_velocity_iolet)
+        return fail(ctx, LBM_ERR_STATE, "contexts with velocity iolets are not differentiated");
     if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
     if (!J) return fail(ctx, LBM_ERR_ARG, "J is NULL");
     const int q = ctx->q, K = ctx->n_iolets;

@@ -41,9 +41,13 @@ enum Layout { LAYOUT_PULL = 0, LAYOUT_NATURAL = 1, LAYOUT_AA_SWAPPED = 2 };
 // Iolet densities of one step, evaluated on the host in float64 and passed
 // by value: drho[k] = rho_k(t) - rho0 (rounded once to float, so that the
 // small pressure differences keep their relative precision), rho[k] = rho_k(t).
+// For a velocity iolet (bit k of vel_mask) rho[k] carries the speed U_k(t)
+// instead, and nrm[k] its unit inward normal.
 struct IoletStep {
     float drho[kMaxIolets];
     float rho[kMaxIolets];
+    float nrm[kMaxIolets][3];
+    unsigned long long vel_mask;
 };
 
 // Device-side description of one simulation, passed by value to launchers.
@@ -76,6 +80,7 @@ struct DevLattice {
     const int32_t *c16_esc;       // escape lists (16-byte aligned per tile)
     const uint32_t *c16_off;      // [tiles] first escape-list index of the tile
     const uint32_t *c16_cnt;      // [tiles] escape count (padded to x4), or kTileFallback
+    const float *vel_weight;      // [n - n_bulk] velocity-iolet weight of the iolet sites
 };
 
 // One fused pull collide-and-stream step from fin into fout.  The iolet

@@ -89,7 +89,7 @@ struct Raw<true> {
 
 // Velocity moments of one site after its collision (for the iolet values).
 struct Velocity {
-    float ux, uy, uz, usq15;
+    float ux, uy, uz, usq15, rs;  // rs: density in stored units
 };
 
 // LBGK collision of one site in stored units (deviations, times 2^S for
@@ -117,6 +117,7 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
     v.uz = jz * ir;
     v.usq15 = 1.5f * (v.ux * v.ux + v.uy * v.uy + v.uz * v.uz);
     const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
+    v.rs = rs;
     const float om = L.omega, omc = 1.0f - L.omega;
     {
         const float w0 = (float)wdir<Q>(0);
@@ -136,14 +137,17 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
 }
 
 // Iolet links of a site with an iolet link (x >= n_bulk): for every i whose
-// table entry s[i] = -2 - k marks link opp(i) as iolet k, the population
-// that re-enters the site as population i at the next step is the
-// equilibrium at the iolet density and the site's current velocity; it
-// replaces the outgoing f*_opp(i), which leaves the domain.
+// table entry s[i] = -2 - k marks link opp(i) as iolet k, the slot read back
+// as population i at the next step holds
+//   density iolet:  the equilibrium at the iolet density and the site's
+//                   current velocity (replacing the outgoing f*_opp(i), which
+//                   leaves the domain);
+//   velocity iolet: the bounced f*_opp(i) plus Ladd's moving-boundary term
+//                   6 w_i rho (c_i . u_b), u_b = weight(x) U_k(t) n_k.
 template <int Q, bool HALF>
-__device__ __forceinline__ void iolet_override(const DevLattice &L, const int (&s)[Q], const Velocity &v,
-                                               const IoletStep &io, const double *__restrict__ rho_io,
-                                               float (&out)[Q]) {
+__device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const int (&s)[Q],
+                                               const Velocity &v, const IoletStep &io,
+                                               const double *__restrict__ rho_io, float (&out)[Q]) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (s[i] <= -2) {
@@ -156,6 +160,14 @@ __device__ __forceinline__ void iolet_override(const DevLattice &L, const int (&
             } else {
                 drk = io.drho[k];
                 rk = io.rho[k];
+            }
+            if ((io.vel_mask >> k) & 1ull) {
+                // rk is the speed U_k(t)
+                const float wu = L.vel_weight[x - L.n_bulk] * rk;
+                const float cn = cdir<Q>(i, 0) * io.nrm[k][0] + cdir<Q>(i, 1) * io.nrm[k][1] +
+                                 cdir<Q>(i, 2) * io.nrm[k][2];
+                out[opp(i)] += 6.0f * (float)wdir<Q>(i) * v.rs * wu * cn;
+                continue;
             }
             if (HALF) {
                 drk *= L.scale;
@@ -200,7 +212,7 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
     }
     float out[Q];
     const Velocity v = collide<Q, HALF>(L, d, out);
-    if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+    if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
 }
@@ -415,7 +427,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
         const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
     } else {
@@ -427,7 +439,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
         const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, s, v, io, rho_io, out);
+        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
     }

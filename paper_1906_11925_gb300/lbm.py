@@ -19,6 +19,8 @@ STORE_FP32 = 0
 STORE_FP16 = 1
 STREAM_PULL = 0
 STREAM_AA = 1
+IOLET_DENSITY = 0
+IOLET_VELOCITY = 1
 MAX_IOLETS = 64
 
 _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM",
@@ -54,7 +56,8 @@ class _Params(C.Structure):
     _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("tau", C.c_double),
                 ("rho0", C.c_double), ("fp16_scale_log2", C.c_int32), ("n_iolets", C.c_int32),
                 ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
-                ("phase", C.c_void_p), ("streaming", C.c_int32)]
+                ("phase", C.c_void_p), ("streaming", C.c_int32), ("iolet_kind", C.c_void_p),
+                ("iolet_normal", C.c_void_p), ("velocity_weight", C.c_void_p)]
 
 
 _lib = None
@@ -163,7 +166,8 @@ class Lattice:
                  rho0: float = 1.0, fp16_scale_log2: int = 14,
                  rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
                  period: Sequence[float] = None, phase: Sequence[float] = None,
-                 stream=None, streaming: int = STREAM_PULL):
+                 stream=None, streaming: int = STREAM_PULL, iolet_kind=None, iolet_normal=None,
+                 velocity_weight=None):
         self._lib = load_library()
         self._ctx = C.c_void_p()
         k = len(rho_mean)
@@ -177,8 +181,14 @@ class Lattice:
         n = xyz.shape[0]
         if nbr.shape != (q, n) or link.shape != (q, n):
             raise ValueError("nbr and link must be [q, n]")
+        self._kind = None if iolet_kind is None else np.ascontiguousarray(iolet_kind, dtype=np.int32)
+        self._nrm = None if iolet_normal is None else np.ascontiguousarray(iolet_normal, dtype=np.float64)
+        self._vw = None if velocity_weight is None else np.ascontiguousarray(velocity_weight, dtype=np.float64)
         prm = _Params(int(q), int(storage), float(tau), float(rho0), int(fp16_scale_log2), k,
-                      *[(a.ctypes.data if k else None) for a in self._io], int(streaming))
+                      *[(a.ctypes.data if k else None) for a in self._io], int(streaming),
+                      None if self._kind is None else self._kind.ctypes.data,
+                      None if self._nrm is None else self._nrm.ctypes.data,
+                      None if self._vw is None else self._vw.ctypes.data)
         self.streaming = int(streaming)
         self.q, self.n, self.tau, self.storage, self.rho0 = int(q), n, float(tau), int(storage), float(rho0)
         self.n_iolets = k

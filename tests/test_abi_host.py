@@ -141,3 +141,17 @@ def test_revolve_schedule_is_optimal():
     assert lbm.revolve_steps(4000, 64) == 9789 + 1
     assert lbm.revolve_steps(3000, 40) == 3 * 3000 - comb(43, 41) + 1
     assert lbm.revolve_steps(5, 6) == 5
+
+
+@pytest.mark.parametrize("case", ["kind", "no_normal", "not_unit"])
+def test_create_rejects_bad_velocity_iolet(case):
+    g = G.tube(radius=2, length=4, nx=5, ny=5)
+    kind = np.array([lbm.IOLET_VELOCITY, 0], np.int32)
+    normal = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 0.0]])
+    if case == "kind":
+        kind[1] = 7
+    if case == "not_unit":
+        normal[0] = [0.0, 0.0, 2.0]
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(15, g, iolet_kind=kind, iolet_normal=None if case == "no_normal" else normal)
+    assert ei.value.name == "LBM_ERR_ARG"
