@@ -4,7 +4,8 @@ Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
 package.  It wraps ``oracle.c`` (plain C, float64, optional OpenMP over sites)
 through ctypes and shares no code with the CUDA library.  Each function
 follows the stated reading of the paper's method (Section 2: collision and
-propagation over sparse fluid sites; Section 4: simple bounce-back walls);
+propagation over sparse fluid sites; Section 4: simple bounce-back walls;
+Section 3.3.2: ray-marched volume rendering);
 see ``oracle.c`` for the definitions.
 
 All arrays use caller site order; populations are float64 [q, n].
@@ -67,6 +68,7 @@ def _bind(path: str):
     lib.orc_objective_run.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, i32, P,
                                       i64, i64, f64]
     lib.orc_objective_run.restype = f64
+    lib.orc_render.argtypes = [P, i32, i32, i32, i32, i32, P, P, P, f64, f64, f64, f64, f64, P, P]
     lib.orc_num_threads.restype = i32
     lib.orc_set_threads.argtypes = [i32]
     return lib
@@ -278,6 +280,24 @@ class Oracle:
                                                 _p(I.mean), _p(I.amp), _p(I.period), _p(I.phase),
                                                 int(t0), int(nsteps), _p(f0), int(kind), _p(m),
                                                 int(t_begin), int(t_end), float(scale)))
+
+    def render(self, vol, width, height, eye, center, up, fov_y, dt, tf_scale, tf_offset, lut,
+               a_stop=0.99):
+        """Ray-marched RGBA image float32 [height, width, 4] of vol [nz, ny, nx]
+        (Section 3.3.2; definitions in orc_render)."""
+        vol = _c(vol, np.float32)
+        nz, ny, nx = vol.shape
+        lut = _c(lut, np.float32).reshape(256, 4)
+        out = np.zeros((height, width, 4), np.float32)
+        v3 = lambda a: _c(a, np.float64)
+        e, c, u = v3(eye), v3(center), v3(up)
+        r = self.lib.orc_render(_p(vol), nx, ny, nz, int(width), int(height), _p(e), _p(c), _p(u),
+                                float(fov_y), float(dt), float(tf_scale), float(tf_offset),
+                                float(a_stop), _p(lut),
+                                _p(out))
+        if r != 0:
+            raise ValueError("orc_render failed")
+        return out
 
     def rest_state(self, q: int, n: int, rho0: float = 1.0) -> np.ndarray:
         """f_i = w_i rho0 at every site (fluid at rest)."""

@@ -25,6 +25,8 @@
  *       sigma = -(1 - 1/(2 tau)) sum_i (f_i - feq_i) c_i c_i,
  *     traction t = sigma n, WSS = |t - (n.t) n|, with the wall normal
  *     n = -normalize(sum of c_i over the site's wall links).
+ *   Section 3.3.2: the visualisation renders a volume by ray marching with a
+ *     transfer-function look-up table; orc_render states its readings.
  *
  * Direction order: 0 is the rest vector; after it, opposite vectors are
  * adjacent (opp(i) = i + 1 for odd i, i - 1 for even i > 0).
@@ -631,4 +633,121 @@ double orc_objective_run(int q, int64_t n, const int32_t *nbr, const uint8_t *li
     free(a);
     free(b);
     return scale * J;
+}
+
+/* ------------------------------------------------------------- rendering
+ *
+ * Direct volume rendering by ray marching (Section 3.3.2: the renderer marches
+ * rays through a volume held in a 3D texture, with the view parameters and the
+ * transfer-function look-up table in constant memory; zoom, rotation and the
+ * scale and offset of the transfer function are steerable).  Readings, taken
+ * identically by the CUDA renderer:
+ *   - volume: float vol[nz][ny][nx], voxel (i, j, k) centred at (i, j, k) in
+ *     volume coordinates; samples are trilinear between voxel centres, clamped
+ *     to the edge voxels; the box is [-0.5, n - 0.5] per axis;
+ *   - camera: pinhole at eye looking at center, up vector up, vertical field of
+ *     view fov_y (radians); pixel (px, py) of a W x H image looks through
+ *     ((px + 0.5) / W * 2 - 1) * tan(fov_y/2) * W/H along the right axis and
+ *     (1 - (py + 0.5) / H * 2) * tan(fov_y/2) along the up axis;
+ *   - the ray's intersection [t_near, t_far] with the box (slab method; t_near
+ *     is raised to 0 when the eye is inside) is cut into segments of length dt
+ *     from t_near, the last one shorter; each segment takes one sample at its
+ *     midpoint, and its length l enters the opacity (so the image is continuous
+ *     in the view: a segment that appears at the far end starts with l = 0);
+ *   - transfer function: s = clamp((v - offset) * scale, 0, 1), LUT index
+ *     s * (L - 1) linearly interpolated between entries (L = 256 RGBA entries,
+ *     alpha = opacity per unit length); opacity of a sample a = min(1, alpha l);
+ *   - front to back: C += (1 - A) a c, A += (1 - A) a, before each sample the
+ *     ray stops once A >= a_stop (early ray termination; a_stop = 1 never
+ *     stops before A reaches 1).
+ * Output rgba[H][W][4] = (C_r, C_g, C_b, A).
+ */
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static double trilinear(const float *vol, int nx, int ny, int nz, double x, double y, double z) {
+    x = clampd(x, 0.0, nx - 1.0);
+    y = clampd(y, 0.0, ny - 1.0);
+    z = clampd(z, 0.0, nz - 1.0);
+    int i0 = (int)floor(x), j0 = (int)floor(y), k0 = (int)floor(z);
+    int i1 = i0 + 1 < nx ? i0 + 1 : i0, j1 = j0 + 1 < ny ? j0 + 1 : j0, k1 = k0 + 1 < nz ? k0 + 1 : k0;
+    double fx = x - i0, fy = y - j0, fz = z - k0;
+#define V(i, j, k) ((double)vol[((int64_t)(k) * ny + (j)) * nx + (i)])
+    double c00 = V(i0, j0, k0) * (1 - fx) + V(i1, j0, k0) * fx;
+    double c10 = V(i0, j1, k0) * (1 - fx) + V(i1, j1, k0) * fx;
+    double c01 = V(i0, j0, k1) * (1 - fx) + V(i1, j0, k1) * fx;
+    double c11 = V(i0, j1, k1) * (1 - fx) + V(i1, j1, k1) * fx;
+#undef V
+    double c0 = c00 * (1 - fy) + c10 * fy, c1 = c01 * (1 - fy) + c11 * fy;
+    return c0 * (1 - fz) + c1 * fz;
+}
+
+int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const double *eye,
+               const double *center, const double *up, double fov_y, double dt, double tf_scale,
+               double tf_offset, double a_stop, const float *lut /*[256][4]*/,
+               float *rgba /*[H][W][4]*/) {
+    if (W <= 0 || H <= 0 || nx <= 0 || ny <= 0 || nz <= 0 || !(dt > 0)) return -1;
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = center[a] - eye[a];
+    double fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] /= fn;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] /= rn;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double th = tan(0.5 * fov_y), aspect = (double)W / (double)H;
+    const double lo[3] = {-0.5, -0.5, -0.5}, hi[3] = {nx - 0.5, ny - 0.5, nz - 0.5};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int py = 0; py < H; ++py) {
+        for (int px = 0; px < W; ++px) {
+            double sx = ((px + 0.5) / W * 2.0 - 1.0) * th * aspect;
+            double sy = (1.0 - (py + 0.5) / H * 2.0) * th;
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = f[a] + sx * r[a] + sy * u[a];
+            double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int a = 0; a < 3; ++a) d[a] /= dn;
+            double tn = -1e300, tf = 1e300;
+            int hit = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.0) {
+                    if (eye[a] < lo[a] || eye[a] > hi[a]) hit = 0;
+                    continue;
+                }
+                double t0 = (lo[a] - eye[a]) / d[a], t1 = (hi[a] - eye[a]) / d[a];
+                if (t0 > t1) { double tmp = t0; t0 = t1; t1 = tmp; }
+                if (t0 > tn) tn = t0;
+                if (t1 < tf) tf = t1;
+            }
+            if (tn < 0.0) tn = 0.0;
+            double C[3] = {0.0, 0.0, 0.0}, A = 0.0;
+            if (hit && tn < tf) {
+                for (int64_t m = 0;; ++m) {
+                    double t0 = tn + m * dt;
+                    if (t0 >= tf || A >= a_stop) break;
+                    double l = tf - t0 < dt ? tf - t0 : dt;
+                    double t = t0 + 0.5 * l;
+                    double v = trilinear(vol, nx, ny, nz, eye[0] + t * d[0], eye[1] + t * d[1],
+                                         eye[2] + t * d[2]);
+                    double s = clampd((v - tf_offset) * tf_scale, 0.0, 1.0) * 255.0;
+                    int l0 = (int)floor(s);
+                    int l1 = l0 < 255 ? l0 + 1 : 255;
+                    double fl = s - l0, e[4];
+                    for (int c = 0; c < 4; ++c) e[c] = lut[4 * l0 + c] * (1 - fl) + lut[4 * l1 + c] * fl;
+                    double a = e[3] * l;
+                    if (a > 1.0) a = 1.0;
+                    for (int c = 0; c < 3; ++c) C[c] += (1.0 - A) * a * e[c];
+                    A += (1.0 - A) * a;
+                }
+            }
+            float *o = rgba + 4 * ((int64_t)py * W + px);
+            o[0] = (float)C[0];
+            o[1] = (float)C[1];
+            o[2] = (float)C[2];
+            o[3] = (float)A;
+        }
+    }
+    return 0;
 }

@@ -418,3 +418,183 @@ ALL_FAST += [
     ("ladd_plug19", lambda o: pin_ladd_plug(o, 19)),
     ("ladd_flux15", lambda o: pin_ladd_flux(o, 15)),
 ]
+
+
+# ---------------------------------------------------------------- volume rendering
+
+def _lut(rgb, alpha):
+    lut = np.zeros((256, 4), np.float32)
+    lut[:, :3] = rgb
+    lut[:, 3] = alpha
+    return lut
+
+
+def _axis_ray(o, vol, eye, center, lut, dt, a_stop=1.0, tf_scale=1.0, tf_offset=0.0, up=(0, 1, 0)):
+    """One pixel whose ray is exactly the view axis (a 1 x 1 image)."""
+    return o.render(vol, 1, 1, eye, center, up, 0.5, dt, tf_scale, tf_offset, lut, a_stop)[0, 0]
+
+
+def pin_render_homogeneous(o):
+    """A constant volume along the view axis: every segment has the same
+    colour, so A = 1 - prod(1 - alpha l_m) over the segment lengths l_m and
+    C = colour * A; small steps approach Beer-Lambert, 1 - exp(-alpha L);
+    early termination and the opacity clamp follow from the same closed form."""
+    nx = ny = nz = 8
+    vol = np.full((nz, ny, nx), 0.5, np.float32)
+    rgb = np.array([1.0, 0.5, 0.25])
+    eye, ctr = [3.5, 3.5, -20.0], [3.5, 3.5, 3.5]
+    L = 8.0  # the axis crosses z in [-0.5, 7.5]
+    alpha, dt = 0.2, 0.3  # 26 segments of 0.3, then one of 0.2
+    px = _axis_ray(o, vol, eye, ctr, _lut(rgb, alpha), dt)
+    A = 1.0 - (1.0 - alpha * dt) ** 26 * (1.0 - alpha * 0.2)
+    assert abs(px[3] - A) < 1e-6, (px, A)
+    assert np.abs(px[:3] - rgb * A).max() < 1e-6, px
+    px = _axis_ray(o, vol, eye, ctr, _lut(rgb, alpha), 1e-3)
+    assert abs(px[3] - (1.0 - math.exp(-alpha * L))) < 1e-3, px
+    # opacity 0.6 per sample: A_k = 1 - 0.4^k crosses 0.99 after six samples
+    px = _axis_ray(o, vol, eye, ctr, _lut(rgb, 2.0), 0.3, a_stop=0.99)
+    assert abs(px[3] - (1.0 - 0.4 ** 6)) < 1e-6, px
+    px = _axis_ray(o, vol, eye, ctr, _lut(rgb, 2.0), 0.3, a_stop=0.98)
+    assert abs(px[3] - (1.0 - 0.4 ** 5)) < 1e-6, px
+    # alpha l > 1 is clamped to an opaque sample
+    px = _axis_ray(o, vol, eye, ctr, _lut(rgb, 10.0), 0.3)
+    assert np.abs(px - np.r_[rgb, 1.0]).max() < 1e-6, px
+    # a volume whose transfer gives alpha 0 leaves the pixel empty
+    assert np.abs(_axis_ray(o, vol, eye, ctr, _lut(rgb, 0.0), 0.3)).max() == 0.0
+
+
+def pin_render_trilinear(o, seed=3):
+    """Trilinear interpolation reproduces a + b x + c y + d x y exactly (also
+    in the clamped half-voxel rim, at the clamped coordinate); with a constant
+    opacity the pixel colour is the LUT, linearly interpolated at
+    s = clamp((v - offset) scale, 0, 1) * 255, times the closed-form A.
+    Rays along z test the x and y weights, rays along x the z weight."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 9, 7, 6
+    a, b, c, d = 0.1, 0.07, 0.05, 0.01
+    lut = _lut(0.0, 0.3)
+    lut[:, :3] = rng.random((256, 3))
+    off, scale = 0.05, 1.3
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    A_z = 1.0 - (1.0 - 0.3 * 0.5) ** (2 * nz)  # L = nz, dt = 0.5
+
+    def expect(v, A):
+        s = min(max((v - off) * scale, 0.0), 1.0) * 255.0
+        return np.array([np.interp(s, np.arange(256), lut[:, ch]) for ch in range(3)]) * A
+
+    vol = (a + b * i + c * j + d * i * j).astype(np.float32)
+    for x0, y0 in [(2.3, 4.6), (0.5, 0.25), (7.9, 5.99), (-0.3, 3.2), (8.3, 6.4), (4.0, 3.0)]:
+        px = _axis_ray(o, vol, [x0, y0, -10.0], [x0, y0, 0.0], lut, 0.5, tf_scale=scale,
+                       tf_offset=off)
+        xc, yc = min(max(x0, 0.0), nx - 1.0), min(max(y0, 0.0), ny - 1.0)
+        v = a + b * xc + c * yc + d * xc * yc
+        # the volume holds float32 values: 1e-4 covers their rounding through the LUT slope
+        assert abs(px[3] - A_z) < 1e-6
+        assert np.abs(px[:3] - expect(v, A_z)).max() < 1e-4, (x0, y0, px, expect(v, A_z))
+    vol = (a + c * j + 0.12 * k).astype(np.float32)
+    A_x = 1.0 - (1.0 - 0.3 * 0.5) ** (2 * nx)
+    for y0, z0 in [(1.7, 2.45), (5.2, 4.9), (3.0, -0.2)]:
+        px = _axis_ray(o, vol, [-10.0, y0, z0], [0.0, y0, z0], lut, 0.5, tf_scale=scale,
+                       tf_offset=off)
+        v = a + c * y0 + 0.12 * min(max(z0, 0.0), nz - 1.0)
+        assert np.abs(px[:3] - expect(v, A_x)).max() < 1e-4, (y0, z0, px)
+
+
+def pin_render_midpoint(o):
+    """With a vanishing opacity C / A is the length-weighted mean colour along
+    the ray; the midpoint samples integrate the piecewise-linear colour of a
+    z ramp exactly when the segments start at its kinks.  The eye sits inside
+    the volume (z = 2.25), so the path is [2.25, 7.5]."""
+    nx, ny, nz = 5, 5, 8
+    k = np.arange(nz, dtype=np.float64)[:, None, None] * np.ones((1, ny, nx))
+    vol = (k / (nz - 1)).astype(np.float32)
+    lut = _lut(0.0, 1e-6)
+    lut[:, 0] = np.arange(256) / 255.0
+    px = _axis_ray(o, vol, [2.0, 2.0, 2.25], [2.0, 2.0, 5.0], lut, 0.25)
+    z0, z1 = 2.25, nz - 0.5
+    integral = (49.0 - z0 * z0) / (2.0 * 7.0) + (z1 - 7.0) * 1.0
+    mean = integral / (z1 - z0)
+    assert abs(px[0] / px[3] - mean) < 1e-5, (px, mean)
+    assert abs(px[3] - 1e-6 * (z1 - z0)) < 1e-10, px
+
+
+def pin_render_over_operator(o, seed=4):
+    """Front-to-back compositing is the 'over' operator: for a ray along z
+    through a volume that is zero on a slab between two random layers (and a
+    transfer function with zero opacity at 0), the full image equals
+    front + (1 - A_front) back, where front and back render each layer alone."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 6, 6, 14
+    vol = rng.random((nz, ny, nx)).astype(np.float32) + 0.05
+    vol[5:9] = 0.0  # the gap
+    front, back = vol.copy(), vol.copy()
+    front[9:] = 0.0
+    back[:5] = 0.0
+    lut = rng.random((256, 4)).astype(np.float32)
+    lut[:, 3] *= 0.6
+    lut[0, 3] = 0.0
+    args = dict(eye=[2.2, 3.1, -30.0], center=[2.6, 2.4, 7.0], up=[0, 1, 0], fov_y=0.15, dt=0.37,
+                tf_scale=1.0, tf_offset=0.0, lut=lut, a_stop=1.0)
+    full = o.render(vol, 7, 5, **args)
+    f = o.render(front, 7, 5, **args)
+    bk = o.render(back, 7, 5, **args)
+    comp = f + (1.0 - f[..., 3:4]) * bk
+    assert ((f[..., 3] > 0.05) & (bk[..., 3] > 0.05)).mean() > 0.5
+    assert np.abs(full - comp).max() < 1e-6, np.abs(full - comp).max()
+
+
+def pin_render_camera(o):
+    """Pinhole camera: looking down -z from the axis with up = +y, a pixel's
+    ray hits the box exactly when it passes through the front face, i.e. when
+    |s_x| D < n_x / 2 and |s_y| D < n_y / 2 for s_x = ((p_x + 1/2) / W * 2 - 1)
+    tan(fov/2) W / H and s_y = (1 - (p_y + 1/2) / H * 2) tan(fov/2), D the
+    distance to the front face.  +x is on the right of the image and +y at
+    the top (right = forward x up)."""
+    nx, ny, nz = 10, 6, 4
+    ctr = np.array([(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
+    eye = ctr + [0.0, 0.0, 30.0]
+    W, H, fov = 41, 23, 0.5
+    lut = _lut(1.0, 0.5)
+    img = o.render(np.ones((nz, ny, nx), np.float32), W, H, eye, ctr, [0, 1, 0], fov, 0.3, 1.0,
+                   0.0, lut)
+    D = eye[2] - (nz - 0.5)
+    th = math.tan(fov / 2)
+    sx = ((np.arange(W) + 0.5) / W * 2 - 1) * th * W / H
+    sy = (1 - (np.arange(H) + 0.5) / H * 2) * th
+    inx, iny = np.abs(sx) * D < nx / 2, np.abs(sy) * D < ny / 2
+    margin_x = np.abs(np.abs(sx) * D - nx / 2) > 1e-3
+    margin_y = np.abs(np.abs(sy) * D - ny / 2) > 1e-3
+    hit = img[..., 3] > 0
+    want = iny[:, None] & inx[None, :]
+    sure = margin_y[:, None] & margin_x[None, :]
+    assert want.sum() > 20 and (~want).sum() > 20
+    assert np.array_equal(hit[sure], want[sure]), (hit.sum(), want.sum())
+    # orientation: only the +x half (resp. the +y half) of the volume is visible
+    lut = _lut(1.0, 0.0)
+    lut[:, 3] = np.arange(256) / 255.0
+    half = np.zeros((nz, ny, nx), np.float32)
+    half[:, :, nx // 2 + 1:] = 1.0
+    a = o.render(half, W, H, eye, ctr, [0, 1, 0], fov, 0.3, 1.0, 0.0, lut)[..., 3]
+    assert a[:, : W // 2].max() == 0.0 and a[H // 2, W // 2 + 2: W // 2 + 7].min() > 0.0
+    half = np.zeros((nz, ny, nx), np.float32)
+    half[:, ny // 2 + 1:, :] = 1.0
+    a = o.render(half, W, H, eye, ctr, [0, 1, 0], fov, 0.3, 1.0, 0.0, lut)[..., 3]
+    assert a[H // 2:, :].max() == 0.0 and a[H // 2 - 3, W // 2] > 0.0
+
+
+def pin_render_miss(o):
+    """Rays that never meet the box leave the pixel empty."""
+    vol = np.ones((4, 4, 4), np.float32)
+    img = o.render(vol, 9, 7, [1.5, 1.5, -10.0], [1.5, 1.5, -20.0], [0, 1, 0], 0.5, 0.3, 1.0, 0.0,
+                   _lut(1.0, 1.0))
+    assert np.abs(img).max() == 0.0
+
+
+ALL_FAST += [
+    ("render_homogeneous", pin_render_homogeneous),
+    ("render_trilinear", pin_render_trilinear),
+    ("render_midpoint", pin_render_midpoint),
+    ("render_over", pin_render_over_operator),
+    ("render_camera", pin_render_camera),
+    ("render_miss", pin_render_miss),
+]

@@ -38,6 +38,23 @@ MUTANTS = {
     "ladd_sign": ("fs - 6.0 * L.w[i] * rho * cub;", "fs + 6.0 * L.w[i] * rho * cub;"),
     "ladd_weight_ignored": ("double wx = weight ? weight[x] : 1.0;", "double wx = 1.0;"),
     "ladd_normal_index": ("wx * U * io_normal[3 * k + a];", "wx * U * io_normal[a];"),
+    "render_dt_dropped": ("double a = e[3] * l;", "double a = e[3];"),
+    "render_no_transmittance": ("C[c] += (1.0 - A) * a * e[c];", "C[c] += a * e[c];"),
+    "render_lut_index_scale": ("0.0, 1.0) * 255.0;", "0.0, 1.0) * 254.0;"),
+    "render_tf_offset_sign": ("clampd((v - tf_offset) * tf_scale", "clampd((v + tf_offset) * tf_scale"),
+    "render_trilinear_x": ("double c00 = V(i0, j0, k0) * (1 - fx) + V(i1, j0, k0) * fx;",
+                           "double c00 = V(i0, j0, k0) * fx + V(i1, j0, k0) * (1 - fx);"),
+    "render_trilinear_z": ("return c0 * (1 - fz) + c1 * fz;", "return c0 * fz + c1 * (1 - fz);"),
+    "render_right_flipped": ("for (int a = 0; a < 3; ++a) r[a] /= rn;", "for (int a = 0; a < 3; ++a) r[a] /= -rn;"),
+    "render_up_flipped": ("u[1] = r[2] * f[0] - r[0] * f[2];", "u[1] = r[0] * f[2] - r[2] * f[0];"),
+    "render_full_fov": ("tan(0.5 * fov_y)", "tan(fov_y)"),
+    "render_pixel_corner": ("((px + 0.5) / W * 2.0 - 1.0)", "((px + 0.0) / W * 2.0 - 1.0)"),
+    "render_aspect_inverted": ("* th * aspect;", "* th / aspect;"),
+    "render_sample_at_start": ("double t = t0 + 0.5 * l;", "double t = t0;"),
+    "render_last_segment_full": ("double l = tf - t0 < dt ? tf - t0 : dt;", "double l = dt;"),
+    "render_behind_eye": ("if (tn < 0.0) tn = 0.0;", "if (tn < -1e300) tn = 0.0;"),
+    "render_no_early_stop": ("if (t0 >= tf || A >= a_stop) break;", "if (t0 >= tf || A >= 1.0) break;"),
+    "render_no_alpha_clamp": ("if (a > 1.0) a = 1.0;", "if (a > 9.0) a = 1.0;"),
     "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
                   "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }

@@ -95,3 +95,8 @@ def test_velocity_iolet_plug_flow(o, q):
 @pytest.mark.parametrize("q", [15, 19])
 def test_velocity_iolet_flux_balance(o, q):
     pins.pin_ladd_flux(o, q)
+
+
+@pytest.mark.parametrize("name", ["homogeneous", "trilinear", "midpoint", "over", "camera", "miss"])
+def test_render(o, name):
+    dict(pins.ALL_FAST)["render_" + name](o)
