@@ -51,6 +51,19 @@ WORKLOADS = {
 }
 
 
+RENDER_SPINUP = 2000
+
+
+def render_view(V, tf_scale: float):
+    """The benchmark's view of a volume: 1920 x 1080, orbiting eye at 1.6x the
+    largest extent, texture filter, default transfer function."""
+    from paper_1906_11925_gb300 import lbm
+
+    dims = np.array(V.shape[::-1], np.float64)
+    return lbm.View.orbit((dims - 1) / 2.0, 1.6 * dims.max(), 0.6, 0.25, 1920, 1080, fov_y=0.75,
+                          dt=0.5, tf_scale=tf_scale, lut=lbm.default_lut(0.3), a_stop=0.99)
+
+
 def make_geometry(name: str):
     cache = os.path.join(tempfile.gettempdir(), "hemelb_gb300_geom_%s.npz" % name)
     if os.path.exists(cache):
@@ -290,6 +303,46 @@ def run_ours(args):
                 "J": r["J"], "dJ_dtau": r["dtau"], "n_gradients": 1 + len(r["dmean"]),
                 "finite": bool(np.isfinite(r["dtau"]) and np.all(np.isfinite(r["dmean"])))}
 
+    def render_leg():
+        # visualisation (Section 3.3.2): after RENDER_SPINUP LB steps, every
+        # frame writes the speed |u| of all sites into the 3D texture and
+        # ray-marches a 1920 x 1080 image of it
+        L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP32, rho_mean=g.rho_mean,
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+        L.step(RENDER_SPINUP)
+        _, u, _ = L.macros(want=("u",))
+        umax = float(torch.linalg.vector_norm(u, dim=1).max())
+        V = lbm.Volume.for_lattice(L)
+        view = render_view(V, 1.0 / umax)  # noqa: F821 (module level)
+        img = torch.empty(view.height, view.width, 4, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            V.from_lattice(L, lbm.QTY_SPEED)
+            V.render(view, img, stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fill_ms = render_ms = 0.0
+        for _ in range(args.steps):
+            ev[0].record(stream)
+            V.from_lattice(L, lbm.QTY_SPEED)
+            ev[1].record(stream)
+            V.render(view, img, stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            fill_ms += ev[0].elapsed_time(ev[1])
+            render_ms += ev[1].elapsed_time(ev[2])
+        alpha = img[..., 3]
+        out = {"quantity": "speed |u|", "spinup_lb_steps": RENDER_SPINUP,
+               "volume_voxels": list(V.shape[::-1]), "image": [view.width, view.height],
+               "filter": "texture trilinear", "dt": view.dt, "a_stop": view.a_stop,
+               "empty_skipping": "8^3 bricks",
+               "fill_ms": round(fill_ms / args.steps, 4), "render_ms": round(render_ms / args.steps, 4),
+               "frames_per_s": round(1e3 * args.steps / (fill_ms + render_ms), 1),
+               "mrays_per_s": round(view.width * view.height * args.steps / render_ms / 1e3, 1),
+               "covered_pixels": round(float((alpha > 0.01).float().mean()), 4),
+               "fill_gbs": round(metrics.volume_fill_bytes(q, g.n) * args.steps / fill_ms / 1e6, 1)}
+        V.close()
+        L.close()
+        return out
+
     sampler = ClockSampler(local_rank) if rank == 0 else None
     r32 = device_leg(lbm.STORE_FP32, sampler)
     r16 = device_leg(lbm.STORE_FP16) if "fp16" in legs else None
@@ -297,6 +350,7 @@ def run_ours(args):
     raa16 = device_leg(lbm.STORE_FP16, streaming=lbm.STREAM_AA) if "aa" in legs else None
     e2e = e2e_leg() if "e2e" in legs else None
     adj = adjoint_leg() if "adjoint" in legs else None
+    rnd = render_leg() if "render" in legs else None
 
     n_lb = args.steps * inner
     value = world * metrics.msups(g.n, n_lb, r32["total_ms"] / 1e3)
@@ -355,7 +409,10 @@ def run_ours(args):
                      "unit": "MSUPS", "ms_per_step": round(raa16["total_ms"] / args.steps, 4),
                      "roofline": roofline(raa16, "fp16", "aa")}},
         "adjoint": adj,
-        "gpu_launches": args.steps * (inner + 1 + 2),
+        "render": rnd,
+        # per benchmark step: inner x (bulk-site launch + iolet-site launch),
+        # the fields, and the two mass kernels
+        "gpu_launches": args.steps * (inner * (2 if g.n_iolets else 1) + 1 + 2),
         "clocks": r32["clocks"],
         "finite": all(r is None or r["finite"] for r in (r32, r16, raa32, raa16)),
     }
@@ -434,8 +491,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
-    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint",
-                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint")
+    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint,render",
+                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint, render")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--adjoint-snapshots", type=int, default=0,
                     help="snapshot count (default: as many as fit in 150 GB)")

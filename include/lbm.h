@@ -292,6 +292,88 @@ lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *rho_mean
 /* Sizes: number of sites, padded plane length, and device bytes held. */
 lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_t *device_bytes);
 
+/* ------------------------------------------------------------------------
+ * Volume rendering (Section 3.3.2).  The paper's visualisation renders the
+ * flow on the GPU by ray marching (direct volume rendering), with the volume
+ * in a 3D texture, the viewing parameters and the transfer-function look-up
+ * table in constant memory, and zoom, rotation and the scale and offset of
+ * the transfer function as the steerable parameters.  Here the image goes to
+ * a caller-owned device buffer (there is no display path).  Definitions:
+ *   volume   float v[nz][ny][nx]; voxel (i, j, k) is centred at (i, j, k) and
+ *            the box is [-1/2, n - 1/2] on each axis; a sample is the
+ *            trilinear interpolation between voxel centres, its coordinates
+ *            clamped to [0, n - 1].
+ *   camera   pinhole at eye looking at center; forward f = normalize(center -
+ *            eye), right r = normalize(f x up), up' = r x f.  Pixel (px, py)
+ *            (py = 0 is the top row) looks along f + s_x r + s_y up', with
+ *            s_x = ((px + 1/2) / W * 2 - 1) tan(fov_y / 2) W / H and
+ *            s_y = (1 - (py + 1/2) / H * 2) tan(fov_y / 2).
+ *   march    the ray's piece inside the box (from the eye when the eye is
+ *            inside) is cut into segments of length dt, the last one
+ *            shorter, with one sample at each segment's midpoint.
+ *   transfer s = clamp((v - tf_offset) tf_scale, 0, 1); (r, g, b, alpha) is
+ *            the LUT linearly interpolated at s * 255 (alpha = opacity per
+ *            unit length); a segment of length l has opacity min(1, alpha l).
+ *   compose  front to back, C += (1 - A) a (r, g, b), A += (1 - A) a; the
+ *            ray stops before a sample once A >= a_stop.
+ * The pixel is (C_r, C_g, C_b, A), float32.  Arithmetic is float32. */
+typedef struct lbm_volume lbm_volume;
+
+enum { LBM_QTY_DENSITY = 0, LBM_QTY_SPEED = 1, LBM_QTY_WSS = 2 };
+enum { LBM_FILTER_TEXTURE = 0, LBM_FILTER_EXACT = 1 };
+
+/* One view.  filter: LBM_FILTER_TEXTURE samples with the texture unit's
+ * trilinear filter (one fetch; its weights are quantised to 1/256), and
+ * LBM_FILTER_EXACT with eight texel fetches and float32 weights.
+ * skip_empty = 1 lets rays jump over 8^3 bricks whose samples are all
+ * exactly 0 whenever the LUT gives value 0 zero opacity; the image is then
+ * bitwise the one of the full march (0 marches every segment).  Limits:
+ * 1 <= width, height <= 16384; 0 < fov_y < 3.1; dt >= 1e-3 with at most 2^24
+ * segments along the box diagonal; 0 < a_stop <= 1 (1: no early stop);
+ * every value finite; up not parallel to center - eye. */
+typedef struct {
+    int32_t width, height;
+    double eye[3], center[3], up[3];
+    double fov_y;
+    double dt;
+    double tf_scale, tf_offset;
+    double a_stop;
+    int32_t filter;
+    int32_t skip_empty;
+    float lut[256][4];
+} lbm_view;
+
+/* A volume of nx x ny x nz float voxels (1..16384 each) held as a 3D CUDA
+ * array with a trilinear and a point-sampling texture and a surface, plus
+ * its 8^3 brick occupancy.  Created holding zeros.  Synchronous.  Errors of
+ * the volume calls are read with lbm_last_error(NULL). */
+lbm_status lbm_volume_create(int32_t nx, int32_t ny, int32_t nz, lbm_volume **out);
+void lbm_volume_destroy(lbm_volume *vol);
+
+/* Copy v_d (device, float [nz][ny][nx], dense) into the volume and rebuild
+ * the brick occupancy from its non-zero voxels; lbm_volume_download copies
+ * the volume out to v_d.  Asynchronous on cuda_stream. */
+lbm_status lbm_volume_upload(lbm_volume *vol, const float *v_d, void *cuda_stream);
+lbm_status lbm_volume_download(const lbm_volume *vol, float *v_d, void *cuda_stream);
+
+/* Bounding box of the context's sites: lo[3] (smallest coordinates) and
+ * dims[3] (extent, 0 for no sites). */
+lbm_status lbm_lattice_box(const lbm_ctx *ctx, int32_t *lo, int32_t *dims);
+
+/* Write a quantity of the current state f(t) into the volume: the site at
+ * coordinates xyz goes to voxel xyz - origin[3] (sites outside the volume
+ * are left out); voxels without a site hold 0.  quantity: LBM_QTY_DENSITY
+ * (rho), LBM_QTY_SPEED (|u|) or LBM_QTY_WSS (as lbm_macros).  Refilling from
+ * the same context and origin rewrites only the sites' voxels.  Asynchronous
+ * on the context's stream. */
+lbm_status lbm_volume_from_lattice(lbm_volume *vol, lbm_ctx *ctx, int32_t quantity,
+                                   const int32_t *origin);
+
+/* Ray-march the volume into rgba_d (device, float [height][width][4],
+ * 16-byte aligned).  Asynchronous on cuda_stream; the caller orders it
+ * after the fill or upload when those run on another stream. */
+lbm_status lbm_render(const lbm_volume *vol, const lbm_view *view, float *rgba_d, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,8 @@ def _bind(path: str):
                                       i64, i64, f64]
     lib.orc_objective_run.restype = f64
     lib.orc_render.argtypes = [P, i32, i32, i32, i32, i32, P, P, P, f64, f64, f64, f64, f64, P, P]
+    lib.orc_render_pixels.argtypes = [P, i32, i32, i32, i32, i32, P, P, P, f64, f64, f64, f64,
+                                      f64, P, i64, P, P]
     lib.orc_num_threads.restype = i32
     lib.orc_set_threads.argtypes = [i32]
     return lib
@@ -297,6 +299,24 @@ class Oracle:
                                 _p(out))
         if r != 0:
             raise ValueError("orc_render failed")
+        return out
+
+    def render_pixels(self, vol, width, height, pixels, eye, center, up, fov_y, dt, tf_scale,
+                      tf_offset, lut, a_stop=0.99):
+        """The pixels [(px, py), ...] of the same image, float32 [len(pixels), 4]."""
+        vol = _c(vol, np.float32)
+        nz, ny, nx = vol.shape
+        lut = _c(lut, np.float32).reshape(256, 4)
+        pix = _c(pixels, np.int32).reshape(-1, 2)
+        out = np.zeros((pix.shape[0], 4), np.float32)
+        v3 = lambda a: _c(a, np.float64)
+        e, c, u = v3(eye), v3(center), v3(up)
+        r = self.lib.orc_render_pixels(_p(vol), nx, ny, nz, int(width), int(height), _p(e), _p(c),
+                                       _p(u), float(fov_y), float(dt), float(tf_scale),
+                                       float(tf_offset), float(a_stop), _p(lut), pix.shape[0],
+                                       _p(pix), _p(out))
+        if r != 0:
+            raise ValueError("orc_render_pixels failed")
         return out
 
     def rest_state(self, q: int, n: int, rho0: float = 1.0) -> np.ndarray:

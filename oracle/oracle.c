@@ -681,10 +681,13 @@ static double trilinear(const float *vol, int nx, int ny, int nz, double x, doub
     return c0 * (1 - fz) + c1 * fz;
 }
 
-int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const double *eye,
-               const double *center, const double *up, double fov_y, double dt, double tf_scale,
-               double tf_offset, double a_stop, const float *lut /*[256][4]*/,
-               float *rgba /*[H][W][4]*/) {
+/* Pixels (px, py) = pix[2k], pix[2k + 1] of a W x H image into out[k][4]
+ * (pix NULL: every pixel in row-major order, npix = W H). */
+int orc_render_pixels(const float *vol, int nx, int ny, int nz, int W, int H, const double *eye,
+                      const double *center, const double *up, double fov_y, double dt,
+                      double tf_scale, double tf_offset, double a_stop,
+                      const float *lut /*[256][4]*/, int64_t npix, const int32_t *pix,
+                      float *out) {
     if (W <= 0 || H <= 0 || nx <= 0 || ny <= 0 || nz <= 0 || !(dt > 0)) return -1;
     double f[3], r[3], u[3];
     for (int a = 0; a < 3; ++a) f[a] = center[a] - eye[a];
@@ -700,9 +703,10 @@ int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const dou
     u[2] = r[0] * f[1] - r[1] * f[0];
     const double th = tan(0.5 * fov_y), aspect = (double)W / (double)H;
     const double lo[3] = {-0.5, -0.5, -0.5}, hi[3] = {nx - 0.5, ny - 0.5, nz - 0.5};
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int py = 0; py < H; ++py) {
-        for (int px = 0; px < W; ++px) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < npix; ++k) {
+        {
+            const int px = pix ? pix[2 * k] : (int)(k % W), py = pix ? pix[2 * k + 1] : (int)(k / W);
             double sx = ((px + 0.5) / W * 2.0 - 1.0) * th * aspect;
             double sy = (1.0 - (py + 0.5) / H * 2.0) * th;
             double d[3];
@@ -742,7 +746,7 @@ int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const dou
                     A += (1.0 - A) * a;
                 }
             }
-            float *o = rgba + 4 * ((int64_t)py * W + px);
+            float *o = out + 4 * k;
             o[0] = (float)C[0];
             o[1] = (float)C[1];
             o[2] = (float)C[2];
@@ -750,4 +754,12 @@ int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const dou
         }
     }
     return 0;
+}
+
+int orc_render(const float *vol, int nx, int ny, int nz, int W, int H, const double *eye,
+               const double *center, const double *up, double fov_y, double dt, double tf_scale,
+               double tf_offset, double a_stop, const float *lut /*[256][4]*/,
+               float *rgba /*[H][W][4]*/) {
+    return orc_render_pixels(vol, nx, ny, nz, W, H, eye, center, up, fov_y, dt, tf_scale,
+                             tf_offset, a_stop, lut, (int64_t)W * H, NULL, rgba);
 }

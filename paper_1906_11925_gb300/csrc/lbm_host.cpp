@@ -4,6 +4,7 @@
 // link flags into the kernel table) runs here on the host in C++ with OpenMP;
 // every per-step operation is a kernel launch on the context's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -65,7 +66,26 @@ struct lbm_ctx {
     } ws;
     int64_t last_fwd_steps = 0, last_adj_steps = 0;
     double last_sweep_ms = 0.0;
+    // rendering: bounding box of the sites, their box coordinates packed 21
+    // bits per axis in internal order (device copy made on first use), and a
+    // serial number that tells volumes which lattice they hold
+    int32_t box_lo[3] = {0, 0, 0}, box_dims[3] = {0, 0, 0};
+    std::vector<uint64_t> vox_host;
+    uint64_t *vox = nullptr;
+    uint64_t serial = 0;
     std::string err;
+};
+
+struct lbm_volume {
+    int dims[3] = {0, 0, 0};
+    int bdims[3] = {0, 0, 0};
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex_lin = 0, tex_pt = 0;
+    cudaSurfaceObject_t surf = 0;
+    uint8_t *occ = nullptr;
+    size_t occ_bytes = 0;
+    uint64_t lattice_serial = 0;  // lattice whose sites the volume holds (0: other content)
+    int shift[3] = {0, 0, 0};
 };
 
 namespace {
@@ -459,6 +479,7 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->mass_dev);
     cudaFree(c->rho_io);
     cudaFree(c->mass_series);
+    cudaFree(c->vox);
     delete c;
 }
 
@@ -641,6 +662,30 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
 #undef CKC
     c->perm_host.swap(perm);
+    {
+        static std::atomic<uint64_t> next_serial{0};
+        c->serial = ++next_serial;
+        int64_t lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+        if (n > 0)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = hi[a] = xyz[a];
+                for (int64_t x = 0; x < n; ++x) {
+                    lo[a] = std::min<int64_t>(lo[a], xyz[3 * x + a]);
+                    hi[a] = std::max<int64_t>(hi[a], xyz[3 * x + a]);
+                }
+            }
+        for (int a = 0; a < 3; ++a) {
+            c->box_lo[a] = (int32_t)lo[a];
+            c->box_dims[a] = (int32_t)(hi[a] - lo[a] + 1);
+        }
+        c->vox_host.resize((size_t)n);
+        for (int64_t xi = 0; xi < n; ++xi) {
+            const int64_t x = c->perm_host[(size_t)xi];
+            c->vox_host[(size_t)xi] = (uint64_t)(xyz[3 * x] - lo[0]) |
+                                      ((uint64_t)(xyz[3 * x + 1] - lo[1]) << 21) |
+                                      ((uint64_t)(xyz[3 * x + 2] - lo[2]) << 42);
+        }
+    }
     *out = c;
     return LBM_OK;
 }
@@ -1206,5 +1251,230 @@ HGB_API lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_
     if (n) *n = ctx->n;
     if (npad) *npad = ctx->npad;
     if (device_bytes) *device_bytes = ctx->device_bytes;
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------------ rendering
+
+namespace {
+
+void free_volume(lbm_volume *v) {
+    if (!v) return;
+    if (v->tex_lin) cudaDestroyTextureObject(v->tex_lin);
+    if (v->tex_pt) cudaDestroyTextureObject(v->tex_pt);
+    if (v->surf) cudaDestroySurfaceObject(v->surf);
+    if (v->arr) cudaFreeArray(v->arr);
+    cudaFree(v->occ);
+    delete v;
+}
+
+cudaMemcpy3DParms linear_copy(lbm_volume *v, float *lin, bool to_array) {
+    cudaMemcpy3DParms cp{};
+    cudaPitchedPtr pp = make_cudaPitchedPtr(lin, (size_t)v->dims[0] * 4, (size_t)v->dims[0],
+                                            (size_t)v->dims[1]);
+    if (to_array) {
+        cp.srcPtr = pp;
+        cp.dstArray = v->arr;
+    } else {
+        cp.srcArray = v->arr;
+        cp.dstPtr = pp;
+    }
+    cp.extent = make_cudaExtent((size_t)v->dims[0], (size_t)v->dims[1], (size_t)v->dims[2]);
+    cp.kind = cudaMemcpyDeviceToDevice;
+    return cp;
+}
+
+bool finite3(const double *a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+}  // namespace
+
+HGB_API lbm_status lbm_volume_create(int32_t nx, int32_t ny, int32_t nz, lbm_volume **out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 16384 || ny > 16384 || nz > 16384)
+        return fail(nullptr, LBM_ERR_ARG, "volume dimensions must lie in [1, 16384]");
+    lbm_volume *v = new lbm_volume();
+    v->dims[0] = nx;
+    v->dims[1] = ny;
+    v->dims[2] = nz;
+    for (int a = 0; a < 3; ++a) v->bdims[a] = (v->dims[a] + 7) / 8;
+    v->occ_bytes = (size_t)v->bdims[0] * v->bdims[1] * v->bdims[2];
+    const size_t need = (size_t)nx * ny * nz * 4 + v->occ_bytes;
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e == cudaSuccess && need + (64u << 20) > free_b) {
+        free_volume(v);
+        return fail(nullptr, LBM_ERR_NOMEM, "the volume does not fit in device memory");
+    }
+    cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+    if (e == cudaSuccess)
+        e = cudaMalloc3DArray(&v->arr, &ch, make_cudaExtent((size_t)nx, (size_t)ny, (size_t)nz),
+                              cudaArraySurfaceLoadStore);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->occ, v->occ_bytes);
+    if (e == cudaSuccess) {
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = v->arr;
+        cudaTextureDesc td{};
+        for (int a = 0; a < 3; ++a) td.addressMode[a] = cudaAddressModeClamp;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        td.filterMode = cudaFilterModeLinear;
+        e = cudaCreateTextureObject(&v->tex_lin, &rd, &td, nullptr);
+        td.filterMode = cudaFilterModePoint;
+        if (e == cudaSuccess) e = cudaCreateTextureObject(&v->tex_pt, &rd, &td, nullptr);
+        if (e == cudaSuccess) e = cudaCreateSurfaceObject(&v->surf, &rd);
+    }
+    // a fresh volume holds zeros and no occupied brick
+    if (e == cudaSuccess) e = launch_volume_clear(v->surf, v->dims, nullptr);
+    if (e == cudaSuccess) e = cudaMemset(v->occ, 0, v->occ_bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_volume(v);
+        return cuda_fail(nullptr, e, "lbm_volume_create");
+    }
+    *out = v;
+    return LBM_OK;
+}
+
+HGB_API void lbm_volume_destroy(lbm_volume *vol) {
+    if (!vol) return;
+    cudaDeviceSynchronize();
+    free_volume(vol);
+}
+
+HGB_API lbm_status lbm_volume_upload(lbm_volume *vol, const float *v_d, void *cuda_stream) {
+    if (!vol || !v_d) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaMemcpy3DParms cp = linear_copy(vol, const_cast<float *>(v_d), true);
+    CK(nullptr, cudaMemcpy3DAsync(&cp, s));
+    CK(nullptr, cudaMemsetAsync(vol->occ, 0, vol->occ_bytes, s));
+    CK(nullptr, launch_occupancy(v_d, vol->dims, vol->occ, vol->bdims, s));
+    vol->lattice_serial = 0;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_volume_download(const lbm_volume *vol, float *v_d, void *cuda_stream) {
+    if (!vol || !v_d) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    cudaMemcpy3DParms cp = linear_copy(const_cast<lbm_volume *>(vol), v_d, false);
+    CK(nullptr, cudaMemcpy3DAsync(&cp, (cudaStream_t)cuda_stream));
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_lattice_box(const lbm_ctx *ctx, int32_t *lo, int32_t *dims) {
+    if (!ctx || !lo || !dims) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = ctx->box_lo[a];
+        dims[a] = ctx->box_dims[a];
+    }
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_volume_from_lattice(lbm_volume *vol, lbm_ctx *ctx, int32_t quantity,
+                                           const int32_t *origin) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!vol || !origin) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (quantity < LBM_QTY_DENSITY || quantity > LBM_QTY_WSS)
+        return fail(ctx, LBM_ERR_ARG, "unknown quantity");
+    if (ctx->n == 0) return LBM_OK;
+    if (!ctx->vox) {
+        CK(ctx, cudaMalloc((void **)&ctx->vox, (size_t)ctx->n * 8));
+        CK(ctx, cudaMemcpy(ctx->vox, ctx->vox_host.data(), (size_t)ctx->n * 8, cudaMemcpyHostToDevice));
+    }
+    VolumeTarget V{};
+    V.surf = vol->surf;
+    for (int a = 0; a < 3; ++a) {
+        V.dims[a] = vol->dims[a];
+        V.bdims[a] = vol->bdims[a];
+        const int64_t sh = (int64_t)ctx->box_lo[a] - origin[a];
+        if (sh < -(1LL << 30) || sh > (1LL << 30)) return fail(ctx, LBM_ERR_ARG, "origin out of range");
+        V.shift[a] = (int)sh;
+    }
+    V.quantity = quantity;
+    V.occ = vol->occ;
+    const bool same = vol->lattice_serial == ctx->serial && vol->shift[0] == V.shift[0] &&
+                      vol->shift[1] == V.shift[1] && vol->shift[2] == V.shift[2];
+    if (!same) {
+        // voxels without a site hold 0; bricks are flagged from the site positions
+        CK(ctx, launch_volume_clear(vol->surf, vol->dims, ctx->stream));
+        CK(ctx, cudaMemsetAsync(vol->occ, 0, vol->occ_bytes, ctx->stream));
+    }
+    V.mark = same ? 0 : 1;
+    CK(ctx, launch_volume_fill(ctx->L, ctx->f_cur, cur_layout(ctx), ctx->vox, V, ctx->stream));
+    vol->lattice_serial = ctx->serial;
+    for (int a = 0; a < 3; ++a) vol->shift[a] = V.shift[a];
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_render(const lbm_volume *vol, const lbm_view *view, float *rgba_d,
+                              void *cuda_stream) {
+    if (!vol || !view || !rgba_d) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    if (((uintptr_t)rgba_d & 15) != 0) return fail(nullptr, LBM_ERR_ARG, "rgba_d must be 16-byte aligned");
+    const lbm_view &w = *view;
+    if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
+        return fail(nullptr, LBM_ERR_ARG, "image size must lie in [1, 16384]");
+    if (!finite3(w.eye) || !finite3(w.center) || !finite3(w.up))
+        return fail(nullptr, LBM_ERR_ARG, "eye, center and up must be finite");
+    if (!(w.fov_y > 0.0 && w.fov_y < 3.1)) return fail(nullptr, LBM_ERR_ARG, "fov_y must lie in (0, 3.1)");
+    if (!std::isfinite(w.tf_scale) || !std::isfinite(w.tf_offset))
+        return fail(nullptr, LBM_ERR_ARG, "tf_scale and tf_offset must be finite");
+    if (!(w.a_stop > 0.0 && w.a_stop <= 1.0)) return fail(nullptr, LBM_ERR_ARG, "a_stop must lie in (0, 1]");
+    if (w.filter != LBM_FILTER_TEXTURE && w.filter != LBM_FILTER_EXACT)
+        return fail(nullptr, LBM_ERR_ARG, "unknown filter");
+    if (w.skip_empty != 0 && w.skip_empty != 1) return fail(nullptr, LBM_ERR_ARG, "skip_empty must be 0 or 1");
+    const double diag = std::sqrt((double)vol->dims[0] * vol->dims[0] + (double)vol->dims[1] * vol->dims[1] +
+                                  (double)vol->dims[2] * vol->dims[2]);
+    if (!(w.dt >= 1e-3) || !(diag / w.dt <= (double)(1 << 24)))
+        return fail(nullptr, LBM_ERR_ARG, "dt must be >= 1e-3 and leave at most 2^24 segments per ray");
+    for (int e = 0; e < 256; ++e)
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(w.lut[e][c])) return fail(nullptr, LBM_ERR_ARG, "LUT entries must be finite");
+    // camera basis in float64: forward, right = forward x up, up' = right x forward
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = w.center[a] - w.eye[a];
+    const double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fn > 0.0)) return fail(nullptr, LBM_ERR_ARG, "eye and center coincide");
+    for (double &x : f) x /= fn;
+    r[0] = f[1] * w.up[2] - f[2] * w.up[1];
+    r[1] = f[2] * w.up[0] - f[0] * w.up[2];
+    r[2] = f[0] * w.up[1] - f[1] * w.up[0];
+    const double un = std::sqrt(w.up[0] * w.up[0] + w.up[1] * w.up[1] + w.up[2] * w.up[2]);
+    const double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rn > 1e-9 * un)) return fail(nullptr, LBM_ERR_ARG, "up is parallel to the view direction");
+    for (double &x : r) x /= rn;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    RenderArgs a{};
+    for (int c = 0; c < 3; ++c) {
+        a.eye[c] = (float)w.eye[c];
+        a.fwd[c] = (float)f[c];
+        a.right[c] = (float)r[c];
+        a.up[c] = (float)u[c];
+        a.dims[c] = vol->dims[c];
+        a.bdims[c] = vol->bdims[c];
+    }
+    const double th = std::tan(0.5 * w.fov_y);
+    a.sx_mul = (float)(th * w.width / w.height);
+    a.sy_mul = (float)th;
+    a.dt = (float)w.dt;
+    a.tf_scale = (float)w.tf_scale;
+    a.tf_offset = (float)w.tf_offset;
+    a.a_stop = (float)w.a_stop;
+    a.width = w.width;
+    a.height = w.height;
+    a.filter = w.filter;
+    std::memcpy(a.lut, w.lut, sizeof a.lut);
+    // Skipping is exact when a sample of value 0 gets zero opacity: the LUT
+    // entries around s(0) (either side of any rounding) have alpha 0.
+    bool zero_alpha_at_zero = true;
+    {
+        const float s0 = std::min(std::max((0.0f - a.tf_offset) * a.tf_scale, 0.0f), 1.0f) * 255.0f;
+        const int l0 = (int)std::floor(s0);
+        for (int e = std::max(l0 - 1, 0); e <= std::min(l0 + 2, 255); ++e)
+            zero_alpha_at_zero &= w.lut[e][3] == 0.0f;
+    }
+    a.skip = (w.skip_empty && zero_alpha_at_zero) ? 1 : 0;
+    CK(nullptr, launch_render(a, vol->tex_lin, vol->tex_pt, vol->occ, rgba_d, (cudaStream_t)cuda_stream));
     return LBM_OK;
 }

@@ -153,6 +153,48 @@ cudaError_t launch_lam_to_caller(const DevLattice &L, const float *lam, double *
 size_t noalloc_max_values();
 cudaError_t noalloc_scratch(double **out);
 
+// ------------------------------------------------------------ rendering
+// Where k_volume_fill writes: a float 3D surface of dims[0] x dims[1] x
+// dims[2] voxels; a site at packed box coordinates p goes to voxel p + shift.
+// quantity: 0 density, 1 speed |u|, 2 wall shear stress.  When mark is set,
+// occ (bytes [bdims[2]][bdims[1]][bdims[0]], 8^3 bricks) is flagged where the
+// voxel can reach a sample.
+struct VolumeTarget {
+    cudaSurfaceObject_t surf;
+    int dims[3];
+    int shift[3];
+    int quantity;
+    int mark;
+    uint8_t *occ;
+    int bdims[3];
+};
+cudaError_t launch_volume_fill(const DevLattice &L, const void *f, int layout, const uint64_t *vox,
+                               const VolumeTarget &V, cudaStream_t s);
+
+// Render parameters, float32, passed by value (the kernel keeps the view in
+// the constant bank and copies the LUT into shared memory).
+struct RenderArgs {
+    float eye[3], fwd[3], right[3], up[3];
+    float sx_mul, sy_mul;  // tan(fov_y / 2) W / H, tan(fov_y / 2)
+    float dt, tf_scale, tf_offset, a_stop;
+    int width, height;
+    int dims[3];
+    int bdims[3];
+    int skip;    // skip bricks with occ == 0
+    int filter;  // 0 texture-unit trilinear, 1 eight point fetches
+    float lut[256][4];
+};
+// Ray-march the volume (tex_lin: linear filtering, tex_pt: point sampling,
+// both unnormalised, clamped) into rgba [height][width][4].
+cudaError_t launch_render(const RenderArgs &a, cudaTextureObject_t tex_lin, cudaTextureObject_t tex_pt,
+                          const uint8_t *occ, float *rgba, cudaStream_t s);
+// Zero every voxel of a surface of dims.
+cudaError_t launch_volume_clear(cudaSurfaceObject_t surf, const int (&dims)[3], cudaStream_t s);
+// Brick occupancy of a dense float volume v [dims[2]][dims[1]][dims[0]]: occ
+// must be zeroed; a brick is flagged when a non-zero voxel can reach it.
+cudaError_t launch_occupancy(const float *v, const int (&dims)[3], uint8_t *occ, const int (&bdims)[3],
+                             cudaStream_t s);
+
 // stored state of the rest fluid (all deviations zero).
 cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s);
 

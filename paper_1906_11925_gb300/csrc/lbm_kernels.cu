@@ -137,6 +137,37 @@ __device__ __forceinline__ float deq(int i, float drho, float rho, const Moments
     return (float)wdir<Q>(i) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - m.usq15));
 }
 
+// Wall shear stress of a site from its deviations, moments and the sum of
+// c_i over its wall links (0 when the site has no wall links or they sum to 0).
+template <int Q>
+__device__ __forceinline__ float wall_shear(const float (&d)[Q], const Moments &m, const int (&wn)[3],
+                                            float tau) {
+    // sum of c over wall links = -(sum of c_i over entries -1); n = -normalize()
+    const float nn2 = (float)(wn[0] * wn[0] + wn[1] * wn[1] + wn[2] * wn[2]);
+    if (nn2 == 0.f) return 0.f;
+    const float inn = 1.0f / sqrtf(nn2);
+    const float n0 = wn[0] * inn, n1 = wn[1] * inn, n2 = wn[2] * inn;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float ne = d[i] - deq<Q>(i, m.drho, m.rho, m);
+        const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
+        if (cx) pxx += ne;
+        if (cy) pyy += ne;
+        if (cz) pzz += ne;
+        if (cx * cy) pxy += (cx * cy) * ne;
+        if (cx * cz) pxz += (cx * cz) * ne;
+        if (cy * cz) pyz += (cy * cz) * ne;
+    }
+    const float coef = -(1.0f - 0.5f / tau);
+    const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
+    const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
+    const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
+    const float tn = t0 * n0 + t1 * n1 + t2 * n2;
+    const float s0 = t0 - tn * n0, s1 = t1 - tn * n1, s2 = t2 - tn * n2;
+    return sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
+}
+
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock)
 k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
@@ -154,34 +185,49 @@ k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int 
         u[3 * (int64_t)xc + 1] = m.uy;
         u[3 * (int64_t)xc + 2] = m.uz;
     }
-    if (!wss) return;
-    // sum of c over wall links = -(sum of c_i over entries -1); n = -normalize()
-    const float nn2 = (float)(wn[0] * wn[0] + wn[1] * wn[1] + wn[2] * wn[2]);
-    if (nn2 == 0.f) {
-        wss[xc] = 0.f;
-        return;
-    }
-    const float inn = 1.0f / sqrtf(nn2);
-    const float n0 = wn[0] * inn, n1 = wn[1] * inn, n2 = wn[2] * inn;
-    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+    if (wss) wss[xc] = wall_shear<Q>(d, m, wn, L.tau);
+}
+
+// Quantity of site x written into the render volume through a surface at
+// voxel coordinates (packed 21 bits per axis, relative to the lattice's box)
+// plus shift; sites outside the volume are skipped.  With mark set, every
+// 8^3 brick whose samples can depend on the voxel (voxel index within
+// [8b - 2, 8b + 9] on each axis) is flagged non-empty.
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_volume_fill(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
+              const uint64_t *__restrict__ vox, VolumeTarget V) {
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    if (x >= L.n) return;
+    const uint64_t pk = vox[x];
+    const int vx = (int)(pk & 0x1fffff) + V.shift[0];
+    const int vy = (int)((pk >> 21) & 0x1fffff) + V.shift[1];
+    const int vz = (int)((pk >> 42) & 0x1fffff) + V.shift[2];
+    if (vx < 0 || vy < 0 || vz < 0 || vx >= V.dims[0] || vy >= V.dims[1] || vz >= V.dims[2]) return;
+    float d[Q];
+    int wn[3];
+    gather<Q, HALF, false>(L, f, layout, x, d, wn);
+    const Moments m = moments<Q>(d, L.rho0);
+    float v;
+    if (V.quantity == 0)
+        v = m.rho;
+    else if (V.quantity == 1)
+        v = sqrtf(m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    else
+        v = wall_shear<Q>(d, m, wn, L.tau);
+    surf3Dwrite(v, V.surf, vx * (int)sizeof(float), vy, vz, cudaBoundaryModeZero);
+    if (!V.mark) return;
+    const int p[3] = {vx, vy, vz};
+    int b0[3], b1[3];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const float ne = d[i] - deq<Q>(i, m.drho, m.rho, m);
-        const int cx = cdir<Q>(i, 0), cy = cdir<Q>(i, 1), cz = cdir<Q>(i, 2);
-        if (cx) pxx += ne;
-        if (cy) pyy += ne;
-        if (cz) pzz += ne;
-        if (cx * cy) pxy += (cx * cy) * ne;
-        if (cx * cz) pxz += (cx * cz) * ne;
-        if (cy * cz) pyz += (cy * cz) * ne;
+    for (int a = 0; a < 3; ++a) {
+        b0[a] = max(0, (p[a] - 9 + 7) >> 3);  // ceil((p - 9) / 8), p - 9 + 7 >= -9: >> floors
+        b1[a] = min(V.bdims[a] - 1, (p[a] + 2) >> 3);
     }
-    const float coef = -(1.0f - 0.5f / L.tau);
-    const float t0 = coef * (pxx * n0 + pxy * n1 + pxz * n2);
-    const float t1 = coef * (pxy * n0 + pyy * n1 + pyz * n2);
-    const float t2 = coef * (pxz * n0 + pyz * n1 + pzz * n2);
-    const float tn = t0 * n0 + t1 * n1 + t2 * n2;
-    const float s0 = t0 - tn * n0, s1 = t1 - tn * n1, s2 = t2 - tn * n2;
-    wss[xc] = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
+    for (int bz = b0[2]; bz <= b1[2]; ++bz)
+        for (int by = b0[1]; by <= b1[1]; ++by)
+            for (int bx = b0[0]; bx <= b1[0]; ++bx)
+                V.occ[((int64_t)bz * V.bdims[1] + by) * V.bdims[0] + bx] = 1;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -331,7 +377,20 @@ cudaError_t scatter_impl(const DevLattice &L, const double *in, int layout, void
     k_scatter_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, in, layout, (T *)f);
     return cudaGetLastError();
 }
+template <int Q, bool HALF>
+cudaError_t volume_fill_impl(const DevLattice &L, const void *f, int layout, const uint64_t *vox,
+                             const VolumeTarget &V, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    k_volume_fill<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, vox, V);
+    return cudaGetLastError();
+}
 }  // namespace
+
+cudaError_t launch_volume_fill(const DevLattice &L, const void *f, int layout, const uint64_t *vox,
+                               const VolumeTarget &V, cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, volume_fill_impl, L, f, layout, vox, V, s);
+}
 
 cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float *rho, float *u,
                           float *wss, cudaStream_t s) {

@@ -8,6 +8,7 @@ CPU fallback: if the shared library is missing the calls raise.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from typing import Optional, Sequence, Tuple
 
@@ -34,7 +35,15 @@ EXPORTED = (
     "lbm_set_state", "lbm_get_links", "lbm_info",
     "lbm_objective_grad", "lbm_revolve_steps", "lbm_adjoint_counts", "lbm_release_workspace",
     "lbm_set_tau", "lbm_set_iolets",
+    "lbm_volume_create", "lbm_volume_destroy", "lbm_volume_upload", "lbm_volume_download",
+    "lbm_lattice_box", "lbm_volume_from_lattice", "lbm_render",
 )
+
+QTY_DENSITY = 0
+QTY_SPEED = 1
+QTY_WSS = 2
+FILTER_TEXTURE = 0
+FILTER_EXACT = 1
 
 OBJ_WSS = 0
 OBJ_DENSITY = 1
@@ -58,6 +67,14 @@ class _Params(C.Structure):
                 ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
                 ("phase", C.c_void_p), ("streaming", C.c_int32), ("iolet_kind", C.c_void_p),
                 ("iolet_normal", C.c_void_p), ("velocity_weight", C.c_void_p)]
+
+
+class _View(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("eye", C.c_double * 3),
+                ("center", C.c_double * 3), ("up", C.c_double * 3), ("fov_y", C.c_double),
+                ("dt", C.c_double), ("tf_scale", C.c_double), ("tf_offset", C.c_double),
+                ("a_stop", C.c_double), ("filter", C.c_int32), ("skip_empty", C.c_int32),
+                ("lut", (C.c_float * 4) * 256)]
 
 
 _lib = None
@@ -105,12 +122,20 @@ def load_library(build_if_missing: bool = True):
         "lbm_release_workspace": [P],
         "lbm_set_tau": [P, C.c_double],
         "lbm_set_iolets": [P, i32, P, P, P, P],
+        "lbm_volume_create": [i32, i32, i32, P],
+        "lbm_volume_destroy": [P],
+        "lbm_volume_upload": [P, P, P],
+        "lbm_volume_download": [P, P, P],
+        "lbm_lattice_box": [P, P, P],
+        "lbm_volume_from_lattice": [P, P, i32, P],
+        "lbm_render": [P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = C.c_int
     lib.lbm_destroy.restype = None
+    lib.lbm_volume_destroy.restype = None
     lib.lbm_last_error.restype = C.c_char_p
     _lib = lib
     return lib
@@ -369,6 +394,149 @@ class Lattice:
         n, npad, b = C.c_int64(), C.c_int64(), C.c_size_t()
         self._ck(self._lib.lbm_info(self._ctx, C.byref(n), C.byref(npad), C.byref(b)))
         return dict(n=n.value, npad=npad.value, device_bytes=b.value)
+
+    def box(self):
+        """Bounding box of the sites: (lo [3], dims [3]) as int tuples."""
+        lo, dims = (C.c_int32 * 3)(), (C.c_int32 * 3)()
+        self._ck(self._lib.lbm_lattice_box(self._ctx, lo, dims))
+        return tuple(lo), tuple(dims)
+
+
+# ---------------------------------------------------------------- rendering
+
+class View:
+    """Viewing and transfer-function parameters of ``lbm_render`` (steerable:
+    ``orbit`` rotates the eye about the centre, ``zoom`` scales the field of
+    view, ``tf_scale`` / ``tf_offset`` move the transfer function)."""
+
+    def __init__(self, width: int, height: int, eye, center, up=(0.0, 0.0, 1.0), fov_y: float = 0.6,
+                 dt: float = 0.5, tf_scale: float = 1.0, tf_offset: float = 0.0, lut=None,
+                 a_stop: float = 0.99, filter: int = FILTER_TEXTURE, skip_empty: bool = True):
+        self.width, self.height = int(width), int(height)
+        self.eye = np.asarray(eye, np.float64).copy()
+        self.center = np.asarray(center, np.float64).copy()
+        self.up = np.asarray(up, np.float64).copy()
+        self.fov_y, self.dt = float(fov_y), float(dt)
+        self.tf_scale, self.tf_offset, self.a_stop = float(tf_scale), float(tf_offset), float(a_stop)
+        self.lut = default_lut() if lut is None else np.asarray(lut, np.float32).reshape(256, 4)
+        self.filter, self.skip_empty = int(filter), bool(skip_empty)
+
+    @classmethod
+    def orbit(cls, center, distance: float, azimuth: float, elevation: float, width: int,
+              height: int, **kw):
+        """Eye on a sphere around center (angles in radians, z up)."""
+        c = np.asarray(center, np.float64)
+        d = np.array([math.cos(elevation) * math.cos(azimuth), math.cos(elevation) * math.sin(azimuth),
+                      math.sin(elevation)])
+        return cls(width, height, c + distance * d, c, up=(0.0, 0.0, 1.0), **kw)
+
+    def zoom(self, factor: float) -> "View":
+        """Narrow the field of view by factor (> 1 zooms in)."""
+        self.fov_y = 2.0 * math.atan(math.tan(self.fov_y / 2.0) / float(factor))
+        return self
+
+    def _struct(self) -> _View:
+        v = _View()
+        v.width, v.height = self.width, self.height
+        for name in ("eye", "center", "up"):
+            arr = getattr(v, name)
+            for a, x in enumerate(getattr(self, name)):
+                arr[a] = float(x)
+        v.fov_y, v.dt, v.tf_scale, v.tf_offset = self.fov_y, self.dt, self.tf_scale, self.tf_offset
+        v.a_stop, v.filter, v.skip_empty = self.a_stop, self.filter, int(self.skip_empty)
+        lut = np.ascontiguousarray(self.lut, dtype=np.float32)
+        if lut.shape != (256, 4):
+            raise ValueError("lut must be [256, 4]")
+        C.memmove(C.addressof(v.lut), lut.ctypes.data, lut.nbytes)
+        return v
+
+
+def default_lut(alpha_max: float = 0.5) -> np.ndarray:
+    """Blue-to-red RGBA table with opacity rising from 0 (value 0 is clear)."""
+    s = np.arange(256, dtype=np.float64) / 255.0
+    lut = np.zeros((256, 4), np.float32)
+    lut[:, 0] = np.clip(1.5 * s, 0, 1)
+    lut[:, 1] = np.clip(1.5 - np.abs(3.0 * s - 1.5), 0, 1)
+    lut[:, 2] = np.clip(1.5 * (1.0 - s), 0, 1)
+    lut[:, 3] = alpha_max * s * s
+    return lut
+
+
+class Volume:
+    """A float voxel volume in a 3D texture (``lbm_volume_create``)."""
+
+    def __init__(self, nx: int, ny: int, nz: int):
+        self._lib = load_library()
+        self._v = C.c_void_p()
+        _check(self._lib.lbm_volume_create(int(nx), int(ny), int(nz), C.byref(self._v)))
+        self.shape = (int(nz), int(ny), int(nx))
+
+    @classmethod
+    def for_lattice(cls, lattice: Lattice):
+        """A volume covering the lattice's bounding box (and its origin)."""
+        lo, dims = lattice.box()
+        v = cls(max(dims[0], 1), max(dims[1], 1), max(dims[2], 1))
+        v.origin = lo
+        return v
+
+    def close(self):
+        if getattr(self, "_v", None) and self._v.value:
+            self._lib.lbm_volume_destroy(self._v)
+            self._v = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_dense(self, t):
+        import torch
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != self.shape:
+            raise ValueError("volume data must be a contiguous float32 CUDA tensor of shape %s"
+                             % (self.shape,))
+
+    def upload(self, vol, stream=None):
+        """Copy a [nz, ny, nx] float32 CUDA tensor into the volume."""
+        self._check_dense(vol)
+        _check(self._lib.lbm_volume_upload(self._v, C.c_void_p(vol.data_ptr()), _stream_handle(stream)))
+
+    def download(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        self._check_dense(out)
+        _check(self._lib.lbm_volume_download(self._v, C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def from_lattice(self, lattice: Lattice, quantity: int = QTY_SPEED, origin=None):
+        """Write a quantity of the lattice's current state (on its stream)."""
+        org = getattr(self, "origin", (0, 0, 0)) if origin is None else origin
+        o = (C.c_int32 * 3)(*[int(x) for x in org])
+        lattice._ck(self._lib.lbm_volume_from_lattice(self._v, lattice._ctx, int(quantity), o))
+
+    def render(self, view: View, out=None, stream=None):
+        """RGBA image float32 [height, width, 4] (CUDA tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty(view.height, view.width, 4, dtype=torch.float32, device="cuda")
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() \
+                or tuple(out.shape) != (view.height, view.width, 4):
+            raise ValueError("out must be a contiguous float32 CUDA tensor [height, width, 4]")
+        v = view._struct()
+        _check(self._lib.lbm_render(self._v, C.byref(v), C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+
+def save_ppm(path: str, rgba, background=(0.0, 0.0, 0.0)):
+    """Write an RGBA float image (array or tensor [H, W, 4]) over a background
+    as a binary PPM file."""
+    img = rgba.detach().cpu().numpy() if hasattr(rgba, "detach") else np.asarray(rgba)
+    rgb = img[..., :3] + (1.0 - img[..., 3:4]) * np.asarray(background, np.float32)
+    b = (np.clip(rgb, 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8)
+    with open(path, "wb") as fh:
+        fh.write(b"P6\n%d %d\n255\n" % (b.shape[1], b.shape[0]))
+        fh.write(b.tobytes())
 
 
 class HemeObjective:

@@ -27,3 +27,11 @@ def bytes_per_site_update(q: int, storage: str, streaming: str = "pull") -> int:
     elem = {"fp32": 4, "fp16": 2}[storage]
     table = {"pull": 4 * (q - 1), "aa": 2 * (q - 1)}[streaming]
     return 2 * q * elem + table
+
+
+def volume_fill_bytes(q: int, n_sites: int, elem: int = 4) -> int:
+    """Algorithmic HBM bytes of writing one site quantity into the render
+    volume: per site the q populations and q - 1 table entries read (as in a
+    pull step), the packed 8-byte voxel coordinate read and one float
+    written."""
+    return n_sites * (q * elem + 4 * (q - 1) + 8 + 4)

@@ -2,6 +2,7 @@
 host-only parts (link building, argument and table validation) behave as
 specified -- no GPU needed."""
 import ctypes as C
+import math
 import os
 import re
 
@@ -155,3 +156,49 @@ def test_create_rejects_bad_velocity_iolet(case):
     with pytest.raises(lbm.LbmError) as ei:
         _create(15, g, iolet_kind=kind, iolet_normal=None if case == "no_normal" else normal)
     assert ei.value.name == "LBM_ERR_ARG"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of lbm_params, lbm_objective and lbm_view have the
+    sizes and field offsets the C compiler gives the header's structs."""
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lbm.h"\n'
+                   'int main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_params),\n'
+                   '         offsetof(lbm_params, velocity_weight), sizeof(lbm_objective),\n'
+                   '         sizeof(lbm_view), offsetof(lbm_view, fov_y), offsetof(lbm_view, filter),\n'
+                   '         offsetof(lbm_view, lut));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [C.sizeof(lbm._Params), lbm._Params.velocity_weight.offset, C.sizeof(lbm._Objective),
+            C.sizeof(lbm._View), lbm._View.fov_y.offset, lbm._View.filter.offset, lbm._View.lut.offset]
+    assert got == want
+
+
+def test_render_calls_reject_bad_arguments_before_any_gpu_call():
+    lib = lbm.load_library()
+    out = C.c_void_p()
+    for dims in [(0, 4, 4), (4, -1, 4), (4, 4, 16385)]:
+        assert lib.lbm_volume_create(*dims, C.byref(out)) == 1
+        assert out.value is None
+    assert "16384" in lib.lbm_last_error(None).decode()
+    assert lib.lbm_volume_create(4, 4, 4, None) == 1
+    v = lbm.View(8, 8, [10.0, 0, 0], [0, 0, 0])._struct()
+    assert lib.lbm_render(None, C.byref(v), None, None) == 1
+    assert lib.lbm_volume_upload(None, None, None) == 1
+    assert lib.lbm_volume_download(None, None, None) == 1
+    assert lib.lbm_lattice_box(None, None, None) == 1
+    assert lib.lbm_volume_from_lattice(None, None, 1, None) == 1
+    lib.lbm_volume_destroy(None)
+
+
+def test_default_lut_leaves_zero_clear():
+    lut = lbm.default_lut()
+    assert lut.shape == (256, 4) and lut[0, 3] == 0.0 and np.all(np.diff(lut[:, 3]) >= 0)
+    v = lbm.View.orbit([1.0, 2.0, 3.0], 10.0, 0.3, 0.2, 64, 32).zoom(2.0)
+    assert np.isclose(np.linalg.norm(v.eye - v.center), 10.0)
+    assert np.isclose(math.tan(v.fov_y / 2), math.tan(0.3) / 2.0)
