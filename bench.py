@@ -309,7 +309,7 @@ def run_ours(args):
         # ray-marches a 1920 x 1080 image of it
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP32, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream)
-        L.step(RENDER_SPINUP)
+        L.step(args.render_spinup)
         _, u, _ = L.macros(want=("u",))
         umax = float(torch.linalg.vector_norm(u, dim=1).max())
         V = lbm.Volume.for_lattice(L)
@@ -330,13 +330,21 @@ def run_ours(args):
             fill_ms += ev[0].elapsed_time(ev[1])
             render_ms += ev[1].elapsed_time(ev[2])
         alpha = img[..., 3]
-        out = {"quantity": "speed |u|", "spinup_lb_steps": RENDER_SPINUP,
+        # one more frame with the kernel's sample counters (not timed)
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        view.counters = cnt
+        V.render(view, img, stream)
+        torch.cuda.synchronize()
+        samples, jumps = [int(x) for x in cnt.cpu()]
+        out = {"quantity": "speed |u|", "spinup_lb_steps": args.render_spinup,
                "volume_voxels": list(V.shape[::-1]), "image": [view.width, view.height],
                "filter": "texture trilinear", "dt": view.dt, "a_stop": view.a_stop,
                "empty_skipping": "8^3 bricks",
                "fill_ms": round(fill_ms / args.steps, 4), "render_ms": round(render_ms / args.steps, 4),
                "frames_per_s": round(1e3 * args.steps / (fill_ms + render_ms), 1),
                "mrays_per_s": round(view.width * view.height * args.steps / render_ms / 1e3, 1),
+               "samples_per_frame": samples, "brick_jumps_per_frame": jumps,
+               "gsamples_per_s": round(samples * args.steps / render_ms / 1e6, 2),
                "covered_pixels": round(float((alpha > 0.01).float().mean()), 4),
                "fill_gbs": round(metrics.volume_fill_bytes(q, g.n) * args.steps / fill_ms / 1e6, 1)}
         V.close()
@@ -496,6 +504,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--adjoint-snapshots", type=int, default=0,
                     help="snapshot count (default: as many as fit in 150 GB)")
+    ap.add_argument("--render-spinup", type=int, default=RENDER_SPINUP,
+                    help="LB steps before the render leg's frames")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

@@ -330,7 +330,9 @@ enum { LBM_FILTER_TEXTURE = 0, LBM_FILTER_EXACT = 1 };
  * bitwise the one of the full march (0 marches every segment).  Limits:
  * 1 <= width, height <= 16384; 0 < fov_y < 3.1; dt >= 1e-3 with at most 2^24
  * segments along the box diagonal; 0 < a_stop <= 1 (1: no early stop);
- * every value finite; up not parallel to center - eye. */
+ * every value finite; up not parallel to center - eye.  counters_d, when
+ * not NULL (device, 2 x uint64, 8-byte aligned), receives += the number of
+ * samples composited and of brick jumps (a slightly slower kernel). */
 typedef struct {
     int32_t width, height;
     double eye[3], center[3], up[3];
@@ -340,6 +342,7 @@ typedef struct {
     double a_stop;
     int32_t filter;
     int32_t skip_empty;
+    unsigned long long *counters_d;
     float lut[256][4];
 } lbm_view;
 

@@ -82,7 +82,8 @@ struct lbm_volume {
     cudaArray_t arr = nullptr;
     cudaTextureObject_t tex_lin = 0, tex_pt = 0;
     cudaSurfaceObject_t surf = 0;
-    uint8_t *occ = nullptr;
+    uint8_t *occ = nullptr;   // brick flags (scratch of the distance transform)
+    uint8_t *dist = nullptr;  // brick distance map read by the render kernel
     size_t occ_bytes = 0;
     uint64_t lattice_serial = 0;  // lattice whose sites the volume holds (0: other content)
     int shift[3] = {0, 0, 0};
@@ -1265,6 +1266,7 @@ void free_volume(lbm_volume *v) {
     if (v->surf) cudaDestroySurfaceObject(v->surf);
     if (v->arr) cudaFreeArray(v->arr);
     cudaFree(v->occ);
+    cudaFree(v->dist);
     delete v;
 }
 
@@ -1299,7 +1301,7 @@ HGB_API lbm_status lbm_volume_create(int32_t nx, int32_t ny, int32_t nz, lbm_vol
     v->dims[2] = nz;
     for (int a = 0; a < 3; ++a) v->bdims[a] = (v->dims[a] + 7) / 8;
     v->occ_bytes = (size_t)v->bdims[0] * v->bdims[1] * v->bdims[2];
-    const size_t need = (size_t)nx * ny * nz * 4 + v->occ_bytes;
+    const size_t need = (size_t)nx * ny * nz * 4 + 2 * v->occ_bytes;
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e == cudaSuccess && need + (64u << 20) > free_b) {
@@ -1311,6 +1313,7 @@ HGB_API lbm_status lbm_volume_create(int32_t nx, int32_t ny, int32_t nz, lbm_vol
         e = cudaMalloc3DArray(&v->arr, &ch, make_cudaExtent((size_t)nx, (size_t)ny, (size_t)nz),
                               cudaArraySurfaceLoadStore);
     if (e == cudaSuccess) e = cudaMalloc((void **)&v->occ, v->occ_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->dist, v->occ_bytes);
     if (e == cudaSuccess) {
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
@@ -1328,6 +1331,7 @@ HGB_API lbm_status lbm_volume_create(int32_t nx, int32_t ny, int32_t nz, lbm_vol
     // a fresh volume holds zeros and no occupied brick
     if (e == cudaSuccess) e = launch_volume_clear(v->surf, v->dims, nullptr);
     if (e == cudaSuccess) e = cudaMemset(v->occ, 0, v->occ_bytes);
+    if (e == cudaSuccess) e = launch_brick_distance(v->occ, v->dist, v->bdims, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_volume(v);
@@ -1350,6 +1354,7 @@ HGB_API lbm_status lbm_volume_upload(lbm_volume *vol, const float *v_d, void *cu
     CK(nullptr, cudaMemcpy3DAsync(&cp, s));
     CK(nullptr, cudaMemsetAsync(vol->occ, 0, vol->occ_bytes, s));
     CK(nullptr, launch_occupancy(v_d, vol->dims, vol->occ, vol->bdims, s));
+    CK(nullptr, launch_brick_distance(vol->occ, vol->dist, vol->bdims, s));
     vol->lattice_serial = 0;
     return LBM_OK;
 }
@@ -1401,6 +1406,7 @@ HGB_API lbm_status lbm_volume_from_lattice(lbm_volume *vol, lbm_ctx *ctx, int32_
     }
     V.mark = same ? 0 : 1;
     CK(ctx, launch_volume_fill(ctx->L, ctx->f_cur, cur_layout(ctx), ctx->vox, V, ctx->stream));
+    if (!same) CK(ctx, launch_brick_distance(vol->occ, vol->dist, vol->bdims, ctx->stream));
     vol->lattice_serial = ctx->serial;
     for (int a = 0; a < 3; ++a) vol->shift[a] = V.shift[a];
     return LBM_OK;
@@ -1465,16 +1471,20 @@ HGB_API lbm_status lbm_render(const lbm_volume *vol, const lbm_view *view, float
     a.height = w.height;
     a.filter = w.filter;
     std::memcpy(a.lut, w.lut, sizeof a.lut);
-    // Skipping is exact when a sample of value 0 gets zero opacity: the LUT
-    // entries around s(0) (either side of any rounding) have alpha 0.
-    bool zero_alpha_at_zero = true;
+    // Skipping is exact when a sample of value 0 gets zero opacity: the
+    // kernel's float arithmetic for v = 0, repeated here, must select LUT
+    // entries whose alpha is 0 (both of them when it interpolates).
+    bool zero_alpha_at_zero;
     {
         const float s0 = std::min(std::max((0.0f - a.tf_offset) * a.tf_scale, 0.0f), 1.0f) * 255.0f;
-        const int l0 = (int)std::floor(s0);
-        for (int e = std::max(l0 - 1, 0); e <= std::min(l0 + 2, 255); ++e)
-            zero_alpha_at_zero &= w.lut[e][3] == 0.0f;
+        const int l0 = std::min((int)s0, 254);
+        const float fl = s0 - (float)l0;
+        zero_alpha_at_zero = w.lut[l0][3] == 0.0f && (fl == 0.0f || w.lut[l0 + 1][3] == 0.0f);
     }
     a.skip = (w.skip_empty && zero_alpha_at_zero) ? 1 : 0;
-    CK(nullptr, launch_render(a, vol->tex_lin, vol->tex_pt, vol->occ, rgba_d, (cudaStream_t)cuda_stream));
+    if (w.counters_d && ((uintptr_t)w.counters_d & 7) != 0)
+        return fail(nullptr, LBM_ERR_ARG, "counters_d must be 8-byte aligned");
+    a.counters = w.counters_d;
+    CK(nullptr, launch_render(a, vol->tex_lin, vol->tex_pt, vol->dist, rgba_d, (cudaStream_t)cuda_stream));
     return LBM_OK;
 }

@@ -182,12 +182,17 @@ struct RenderArgs {
     int bdims[3];
     int skip;    // skip bricks with occ == 0
     int filter;  // 0 texture-unit trilinear, 1 eight point fetches
+    unsigned long long *counters;  // null, or [2]: += samples composited, brick jumps
     float lut[256][4];
 };
 // Ray-march the volume (tex_lin: linear filtering, tex_pt: point sampling,
-// both unnormalised, clamped) into rgba [height][width][4].
+// both unnormalised, clamped) into rgba [height][width][4]; dist is the
+// brick distance map of launch_brick_distance.
 cudaError_t launch_render(const RenderArgs &a, cudaTextureObject_t tex_lin, cudaTextureObject_t tex_pt,
-                          const uint8_t *occ, float *rgba, cudaStream_t s);
+                          const uint8_t *dist, float *rgba, cudaStream_t s);
+// Chebyshev distance (in bricks, capped at 15) from every brick to the
+// nearest flagged one, from the flags in marks (overwritten) into dist.
+cudaError_t launch_brick_distance(uint8_t *marks, uint8_t *dist, const int (&bdims)[3], cudaStream_t s);
 // Zero every voxel of a surface of dims.
 cudaError_t launch_volume_clear(cudaSurfaceObject_t surf, const int (&dims)[3], cudaStream_t s);
 // Brick occupancy of a dense float volume v [dims[2]][dims[1]][dims[0]]: occ

@@ -168,8 +168,11 @@ __device__ __forceinline__ float wall_shear(const float (&d)[Q], const Moments &
     return sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
 }
 
+#ifndef HGB_MACROS_MINB
+#define HGB_MACROS_MINB 3
+#endif
 template <int Q, bool HALF>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, HGB_MACROS_MINB)
 k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
          float *__restrict__ rho, float *__restrict__ u, float *__restrict__ wss) {
     const int x = blockIdx.x * kBlock + threadIdx.x;
@@ -193,8 +196,11 @@ k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int 
 // plus shift; sites outside the volume are skipped.  With mark set, every
 // 8^3 brick whose samples can depend on the voxel (voxel index within
 // [8b - 2, 8b + 9] on each axis) is flagged non-empty.
-template <int Q, bool HALF>
-__global__ void __launch_bounds__(kBlock)
+#ifndef HGB_FILL_MINB
+#define HGB_FILL_MINB 3
+#endif
+template <int Q, bool HALF, int QTY>
+__global__ void __launch_bounds__(kBlock, QTY == 2 ? 1 : HGB_FILL_MINB)
 k_volume_fill(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
               const uint64_t *__restrict__ vox, VolumeTarget V) {
     const int x = blockIdx.x * kBlock + threadIdx.x;
@@ -209,9 +215,9 @@ k_volume_fill(const DevLattice L, const typename Store<HALF>::T *__restrict__ f,
     gather<Q, HALF, false>(L, f, layout, x, d, wn);
     const Moments m = moments<Q>(d, L.rho0);
     float v;
-    if (V.quantity == 0)
+    if (QTY == 0)
         v = m.rho;
-    else if (V.quantity == 1)
+    else if (QTY == 1)
         v = sqrtf(m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     else
         v = wall_shear<Q>(d, m, wn, L.tau);
@@ -381,7 +387,12 @@ template <int Q, bool HALF>
 cudaError_t volume_fill_impl(const DevLattice &L, const void *f, int layout, const uint64_t *vox,
                              const VolumeTarget &V, cudaStream_t s) {
     using T = typename Store<HALF>::T;
-    k_volume_fill<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, vox, V);
+    if (V.quantity == 0)
+        k_volume_fill<Q, HALF, 0><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, vox, V);
+    else if (V.quantity == 1)
+        k_volume_fill<Q, HALF, 1><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, vox, V);
+    else
+        k_volume_fill<Q, HALF, 2><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, vox, V);
     return cudaGetLastError();
 }
 }  // namespace

@@ -21,9 +21,11 @@
 //   - empty-space skipping over 8^3 bricks: a brick is empty when no non-zero
 //     voxel lies within two voxels of it, so every sample within one voxel of
 //     it reads exactly 0.  When the LUT gives such samples zero opacity (the
-//     host checks), a sample contributes exactly nothing, and the ray jumps
-//     to the segment where it leaves the brick; the image is bitwise the one
-//     of the full march.
+//     host checks), a sample contributes exactly nothing.  Each brick stores
+//     its Chebyshev distance k (in bricks, capped) to the nearest non-empty
+//     brick, so a ray in an empty brick jumps to the segment where it leaves
+//     the cube of 2k - 1 bricks around it; the image is bitwise the one of
+//     the full march.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,6 +36,7 @@ namespace hemelb_gb300 {
 namespace {
 
 constexpr int kTileX = 16, kTileY = 8;
+constexpr int kDistCap = 15;  // largest brick distance stored (means ">= 15")
 
 __device__ __forceinline__ float sample_exact(cudaTextureObject_t t, float x, float y, float z,
                                               const int (&n)[3]) {
@@ -55,10 +58,11 @@ __device__ __forceinline__ float sample_exact(cudaTextureObject_t t, float x, fl
     return c0 + (c1 - c0) * fz;
 }
 
-template <int FILTER>
+template <int FILTER, bool COUNT>
 __global__ void __launch_bounds__(kTileX * kTileY)
-k_render(const __grid_constant__ RenderArgs a, cudaTextureObject_t tex, const uint8_t *__restrict__ occ,
+k_render(const __grid_constant__ RenderArgs a, cudaTextureObject_t tex, const uint8_t *__restrict__ dist,
          float4 *__restrict__ out) {
+    unsigned taken = 0, jumps = 0;
     __shared__ float4 lut[256];
     const int tid = threadIdx.y * kTileX + threadIdx.x;
     for (int e = tid; e < 256; e += kTileX * kTileY)
@@ -99,31 +103,39 @@ k_render(const __grid_constant__ RenderArgs a, cudaTextureObject_t tex, const ui
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
     if (hit && tn < tf) {
         const float len = tf - tn, dt = a.dt;
+        float inv_d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) inv_d[c] = 1.0f / d[c];  // +-inf on an axis-parallel ray
+        float t_check = -1.f;  // the ray is in a non-empty brick up to here
         for (int m = 0;;) {
             const float s0 = m * dt;
             if (!(s0 < len) || A >= a.a_stop) break;
             const float l = fminf(dt, len - s0);
             const float t = tn + s0 + 0.5f * l;
             const float x = a.eye[0] + t * d[0], y = a.eye[1] + t * d[1], z = a.eye[2] + t * d[2];
-            if (a.skip) {
-                const int bx = min(max(__float2int_rd((x + 0.5f) * 0.125f), 0), a.bdims[0] - 1);
-                const int by = min(max(__float2int_rd((y + 0.5f) * 0.125f), 0), a.bdims[1] - 1);
-                const int bz = min(max(__float2int_rd((z + 0.5f) * 0.125f), 0), a.bdims[2] - 1);
-                if (!__ldg(occ + ((int64_t)bz * a.bdims[1] + by) * a.bdims[0] + bx)) {
-                    // leave the brick: smallest exit parameter over the axes
-                    const int b[3] = {bx, by, bz};
-                    float te = 3.0e38f;
+            if (a.skip && t >= t_check) {
+                const int b[3] = {min(max(__float2int_rd((x + 0.5f) * 0.125f), 0), a.bdims[0] - 1),
+                                  min(max(__float2int_rd((y + 0.5f) * 0.125f), 0), a.bdims[1] - 1),
+                                  min(max(__float2int_rd((z + 0.5f) * 0.125f), 0), a.bdims[2] - 1)};
+                const int k = __ldg(dist + ((int64_t)b[2] * a.bdims[1] + b[1]) * a.bdims[0] + b[0]);
+                // exit of the cube of bricks within r - 1 of this one (all
+                // empty when k = r > 0; the brick itself when k = 0)
+                const int r = k ? k : 1;
+                float te = 3.0e38f;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        if (d[c] != 0.f) {
-                            const float face = d[c] > 0.f ? 8.f * (b[c] + 1) - 0.5f : 8.f * b[c] - 0.5f;
-                            te = fminf(te, (face - a.eye[c]) / d[c]);
-                        }
-                    // segments that end before te sample inside the brick
+                for (int c = 0; c < 3; ++c) {
+                    const float face = d[c] > 0.f ? 8.f * (b[c] + r) - 0.5f : 8.f * (b[c] - r + 1) - 0.5f;
+                    const float tc = (face - a.eye[c]) * inv_d[c];
+                    if (d[c] != 0.f) te = fminf(te, tc);
+                }
+                if (k) {
+                    // segments that end before te sample inside the empty cube
                     const float mf = floorf((te - tn) / dt);
                     m = mf > (float)(m + 1) ? (mf < 3.0e7f ? (int)mf : 30000000) : m + 1;
+                    if (COUNT) ++jumps;
                     continue;
                 }
+                t_check = te;  // no look-up until the ray leaves this brick
             }
             float v;
             if (FILTER == 0)
@@ -142,9 +154,19 @@ k_render(const __grid_constant__ RenderArgs a, cudaTextureObject_t tex, const ui
             C2 += w * eb;
             A += w;
             ++m;
+            if (COUNT) ++taken;
         }
     }
     __stcs(out + (int64_t)py * a.width + px, make_float4(C0, C1, C2, A));
+    if (COUNT) {
+        // counters[0] += samples composited, counters[1] += brick jumps
+        const unsigned lane_mask = __activemask();
+        const unsigned ts = __reduce_add_sync(lane_mask, taken), js = __reduce_add_sync(lane_mask, jumps);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(lane_mask) - 1)) {
+            atomicAdd(a.counters, (unsigned long long)ts);
+            atomicAdd(a.counters + 1, (unsigned long long)js);
+        }
+    }
 }
 
 __global__ void k_volume_clear(cudaSurfaceObject_t surf, int nx, int ny, int nz) {
@@ -177,6 +199,31 @@ __global__ void k_occupancy(const float *__restrict__ v, int nx, int ny, int nz,
     }
 }
 
+// One axis of the separable Chebyshev distance transform on the brick grid:
+// out[p] = min over |j| <= kDistCap of max(|j|, in[p + j e_axis]) (cells
+// outside the grid count as kDistCap), capped at kDistCap.  With
+// first set, in holds marks (non-zero = occupied: distance 0, else kDistCap).
+template <int AXIS>
+__global__ void k_brick_distance(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int bx, int by,
+                                 int bz, bool first) {
+    const int64_t total = (int64_t)bx * by * bz;
+    const int n[3] = {bx, by, bz};
+    const int64_t stride[3] = {1, bx, (int64_t)bx * by};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int p[3] = {(int)(i % bx), (int)((i / bx) % by), (int)(i / ((int64_t)bx * by))};
+        int best = kDistCap;
+        for (int j = -kDistCap + 1; j < kDistCap; ++j) {
+            const int q = p[AXIS] + j;
+            if (q < 0 || q >= n[AXIS]) continue;
+            const int v = in[i + j * stride[AXIS]];
+            const int dv = first ? (v ? 0 : kDistCap) : v;
+            best = min(best, max(abs(j), dv));
+        }
+        out[i] = (uint8_t)best;
+    }
+}
+
 unsigned stride_grid(int64_t total) {
     const int64_t want = (total + 255) / 256;
     return (unsigned)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
@@ -185,19 +232,36 @@ unsigned stride_grid(int64_t total) {
 }  // namespace
 
 cudaError_t launch_render(const RenderArgs &a, cudaTextureObject_t tex_lin, cudaTextureObject_t tex_pt,
-                          const uint8_t *occ, float *rgba, cudaStream_t s) {
+                          const uint8_t *dist, float *rgba, cudaStream_t s) {
     const dim3 block(kTileX, kTileY);
     const dim3 grid((a.width + kTileX - 1) / kTileX, (a.height + kTileY - 1) / kTileY);
-    if (a.filter == 0)
-        k_render<0><<<grid, block, 0, s>>>(a, tex_lin, occ, reinterpret_cast<float4 *>(rgba));
-    else
-        k_render<1><<<grid, block, 0, s>>>(a, tex_pt, occ, reinterpret_cast<float4 *>(rgba));
+    float4 *o = reinterpret_cast<float4 *>(rgba);
+    if (a.counters) {
+        if (a.filter == 0)
+            k_render<0, true><<<grid, block, 0, s>>>(a, tex_lin, dist, o);
+        else
+            k_render<1, true><<<grid, block, 0, s>>>(a, tex_pt, dist, o);
+    } else {
+        if (a.filter == 0)
+            k_render<0, false><<<grid, block, 0, s>>>(a, tex_lin, dist, o);
+        else
+            k_render<1, false><<<grid, block, 0, s>>>(a, tex_pt, dist, o);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_volume_clear(cudaSurfaceObject_t surf, const int (&dims)[3], cudaStream_t s) {
     const int64_t total = (int64_t)dims[0] * dims[1] * dims[2];
     k_volume_clear<<<stride_grid(total), 256, 0, s>>>(surf, dims[0], dims[1], dims[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_distance(uint8_t *marks, uint8_t *dist, const int (&b)[3], cudaStream_t s) {
+    const int64_t total = (int64_t)b[0] * b[1] * b[2];
+    const unsigned g = stride_grid(total);
+    k_brick_distance<0><<<g, 256, 0, s>>>(marks, dist, b[0], b[1], b[2], true);
+    k_brick_distance<1><<<g, 256, 0, s>>>(dist, marks, b[0], b[1], b[2], false);
+    k_brick_distance<2><<<g, 256, 0, s>>>(marks, dist, b[0], b[1], b[2], false);
     return cudaGetLastError();
 }
 

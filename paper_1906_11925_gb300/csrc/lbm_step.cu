@@ -346,7 +346,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         const int x = tile * kBlock + tid;
         const unsigned char *buf = sbuf + stage * SB;
         int s[Q];
-        if (fmt[stage]) {
+        if (kUseCompressedTable && fmt[stage]) {
             // every thread decodes (the ballots need the whole warp)
             const int16_t *r16 = reinterpret_cast<const int16_t *>(buf);
             const uint16_t *pre = reinterpret_cast<const uint16_t *>(buf + NE * kTile * 2);

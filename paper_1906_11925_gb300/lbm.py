@@ -74,7 +74,7 @@ class _View(C.Structure):
                 ("center", C.c_double * 3), ("up", C.c_double * 3), ("fov_y", C.c_double),
                 ("dt", C.c_double), ("tf_scale", C.c_double), ("tf_offset", C.c_double),
                 ("a_stop", C.c_double), ("filter", C.c_int32), ("skip_empty", C.c_int32),
-                ("lut", (C.c_float * 4) * 256)]
+                ("counters_d", C.c_void_p), ("lut", (C.c_float * 4) * 256)]
 
 
 _lib = None
@@ -411,7 +411,8 @@ class View:
 
     def __init__(self, width: int, height: int, eye, center, up=(0.0, 0.0, 1.0), fov_y: float = 0.6,
                  dt: float = 0.5, tf_scale: float = 1.0, tf_offset: float = 0.0, lut=None,
-                 a_stop: float = 0.99, filter: int = FILTER_TEXTURE, skip_empty: bool = True):
+                 a_stop: float = 0.99, filter: int = FILTER_TEXTURE, skip_empty: bool = True,
+                 counters=None):
         self.width, self.height = int(width), int(height)
         self.eye = np.asarray(eye, np.float64).copy()
         self.center = np.asarray(center, np.float64).copy()
@@ -420,6 +421,8 @@ class View:
         self.tf_scale, self.tf_offset, self.a_stop = float(tf_scale), float(tf_offset), float(a_stop)
         self.lut = default_lut() if lut is None else np.asarray(lut, np.float32).reshape(256, 4)
         self.filter, self.skip_empty = int(filter), bool(skip_empty)
+        # optional int64 CUDA tensor [2]: += samples composited, brick jumps
+        self.counters = counters
 
     @classmethod
     def orbit(cls, center, distance: float, azimuth: float, elevation: float, width: int,
@@ -444,6 +447,11 @@ class View:
                 arr[a] = float(x)
         v.fov_y, v.dt, v.tf_scale, v.tf_offset = self.fov_y, self.dt, self.tf_scale, self.tf_offset
         v.a_stop, v.filter, v.skip_empty = self.a_stop, self.filter, int(self.skip_empty)
+        if self.counters is not None:
+            c = self.counters
+            if not c.is_cuda or c.numel() != 2 or c.element_size() != 8 or not c.is_contiguous():
+                raise ValueError("counters must be a contiguous 2-element 64-bit CUDA tensor")
+            v.counters_d = c.data_ptr()
         lut = np.ascontiguousarray(self.lut, dtype=np.float32)
         if lut.shape != (256, 4):
             raise ValueError("lut must be [256, 4]")

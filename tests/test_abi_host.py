@@ -167,7 +167,8 @@ def test_struct_layouts_match_the_header(tmp_path):
                    '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_params),\n'
                    '         offsetof(lbm_params, velocity_weight), sizeof(lbm_objective),\n'
                    '         sizeof(lbm_view), offsetof(lbm_view, fov_y), offsetof(lbm_view, filter),\n'
-                   '         offsetof(lbm_view, lut));\n  return 0;\n}\n')
+                   '         offsetof(lbm_view, lut));\n  printf("%zu\\n", offsetof(lbm_view, counters_d));\n'
+                   '  return 0;\n}\n')
     exe = tmp_path / "layout"
     import subprocess
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -175,7 +176,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
     want = [C.sizeof(lbm._Params), lbm._Params.velocity_weight.offset, C.sizeof(lbm._Objective),
-            C.sizeof(lbm._View), lbm._View.fov_y.offset, lbm._View.filter.offset, lbm._View.lut.offset]
+            C.sizeof(lbm._View), lbm._View.fov_y.offset, lbm._View.filter.offset, lbm._View.lut.offset,
+            lbm._View.counters_d.offset]
     assert got == want
 
 

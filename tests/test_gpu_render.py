@@ -146,6 +146,16 @@ def test_empty_skipping_is_bitwise_invisible(filt):
         view.skip_empty = False
         b = V.render(view)
         assert torch.equal(a, b), name
+    # the counting kernel draws the same image; skipping takes fewer samples
+    view = views(96, 64, filter=filt)["oblique"]
+    ref = V.render(view).clone()
+    n_skip, n_full = torch.zeros(2, dtype=torch.int64, device="cuda"), torch.zeros(2, dtype=torch.int64, device="cuda")
+    view.counters = n_skip
+    assert torch.equal(V.render(view), ref)
+    view.skip_empty, view.counters = False, n_full
+    assert torch.equal(V.render(view), ref)
+    (ts, js), (tf, jf) = n_skip.tolist(), n_full.tolist()
+    assert jf == 0 and js > 0 and 0 < ts < tf, (ts, js, tf, jf)
     # a LUT that gives value 0 some opacity turns skipping off by itself
     lut = lbm.default_lut(0.6)
     lut[:2, 3] = 0.05
