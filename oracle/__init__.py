@@ -56,7 +56,7 @@ def _bind(path: str):
     lib.orc_links_build.argtypes = [i32, i64, P, i64, P, P, P, P, P]
     lib.orc_step.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, P, P]
     lib.orc_run.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, P]
-    lib.orc_run_bc.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, P, P, P, i64, i64, P, P]
+    lib.orc_run_bc.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, P, P, P, P, i64, i64, P, P]
     lib.orc_macros.argtypes = [i32, i64, P, f64, P, P, P, P]
     lib.orc_mass.argtypes = [i32, i64, P]
     lib.orc_mass.restype = f64
@@ -169,23 +169,26 @@ class Oracle:
             raise ValueError("orc_run failed")
         return f
 
-    def run_bc(self, q, nbr, link, tau, f, nsteps, io_kind, io_normal, weight=None, t0=0,
-               geom=None, **io):
+    def run_bc(self, q, nbr, link, tau, f, nsteps, io_kind=None, io_normal=None, weight=None,
+               t0=0, geom=None, wall_q=None, **io):
         """As run(), with velocity (Ladd) iolets: io_kind[k] = 1 marks iolet k as
         a velocity iolet with unit inward normal io_normal[k] and speed given by
-        its schedule; weight [n] scales the speed per site (None = 1)."""
+        its schedule; weight [n] scales the speed per site (None = 1); and
+        interpolated (BFL) walls: wall_q [q, n] is the fluid fraction of each
+        wall link (None = every wall half-way)."""
         nbr = _c(nbr, np.int32)
         link = _c(link, np.uint8)
         f = np.array(f, dtype=np.float64, order="C", copy=True)
         n = f.shape[1]
         I = _Iolets(geom, **io)
-        kind = _c(io_kind, np.int32)
-        nrm = _c(io_normal, np.float64).reshape(-1, 3)
+        kind = None if io_kind is None else _c(io_kind, np.int32)
+        nrm = None if io_normal is None else _c(io_normal, np.float64).reshape(-1, 3)
         w = None if weight is None else _c(weight, np.float64)
+        wq = None if wall_q is None else _c(wall_q, np.float64).reshape(q, n)
         work = np.empty_like(f)
         r = self.lib.orc_run_bc(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
-                                _p(I.period), _p(I.phase), _p(kind), _p(nrm), _p(w), int(t0),
-                                int(nsteps), _p(f), _p(work))
+                                _p(I.period), _p(I.phase), _p(kind), _p(nrm), _p(w), _p(wq),
+                                int(t0), int(nsteps), _p(f), _p(work))
         if r != 0:
             raise ValueError("orc_run_bc failed")
         return f

@@ -254,12 +254,33 @@ int orc_links_build(int q, int64_t n, const int32_t *xyz, int64_t n_io,
  * The schedule mean/amp/period/phase gives rho_k(t) for a density iolet and
  * the velocity magnitude U_k(t) for a velocity iolet (io_kind[k] = 1, unit
  * inward normal io_normal[3k..3k+2]); weight may be NULL (all 1).
+ *
+ * Interpolated walls (the paper's BFL wall boundary, Section 3.2: Bouzidi,
+ * Firdaouss & Lallemand, Phys. Fluids 13, 3452 (2001)): wall_q[i][x] in
+ * (0, 1] is the fraction of the link from x along c_i that lies in the fluid
+ * (1/2: the wall half-way, the plain bounce-back above).  With xb = x - c_i:
+ *   q <  1/2, xb fluid: fout_opp(i)(x) = 2q f*_i(x) + (1 - 2q) f*_i(xb),
+ *   q >= 1/2:           fout_opp(i)(x) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_opp(i)(x),
+ *   q <  1/2, xb not fluid: the plain bounce-back (a reading: the
+ *   interpolation has no second fluid point).
+ * wall_q NULL: every wall is half-way.
  */
+/* Post-collision population i at site x (the collision written once more,
+ * for the BFL upstream point). */
+static double post_collision(const lattice_t *L, const double *f, int64_t n, int64_t x, int i,
+                             double tau) {
+    double h[19], he[19], r, v[3];
+    for (int j = 0; j < L->q; ++j) h[j] = f[(int64_t)j * n + x];
+    moments(L, h, &r, v);
+    equilibrium(L, r, v, he);
+    return h[i] - (h[i] - he[i]) / tau;
+}
+
 int orc_step_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
                 int n_io, const double *rho_mean, const double *amp,
                 const double *period, const double *phase, const int32_t *io_kind,
-                const double *io_normal, const double *weight, int64_t t,
-                const double *f, double *fout) {
+                const double *io_normal, const double *weight, const double *wall_q,
+                int64_t t, const double *f, double *fout) {
     lattice_t L;
     if (get_lattice(q, &L)) return -1;
 #pragma omp parallel for schedule(static)
@@ -268,13 +289,23 @@ int orc_step_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, doubl
         for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
         moments(&L, g, &rho, u);
         equilibrium(&L, rho, u, feq);
+        double fsa[19];
+        for (int i = 0; i < q; ++i) fsa[i] = g[i] - (g[i] - feq[i]) / tau;
         for (int i = 0; i < q; ++i) {
-            double fs = g[i] - (g[i] - feq[i]) / tau;
+            double fs = fsa[i];
             int lk = link[(int64_t)i * n + x];
+            double qw = (lk == 1 && wall_q) ? wall_q[(int64_t)i * n + x] : 0.5;
             if (lk == 0) {
                 fout[(int64_t)i * n + nbr[(int64_t)i * n + x]] = fs;
-            } else if (lk == 1) {
+            } else if (lk == 1 && qw == 0.5) {
                 fout[(int64_t)L.opp[i] * n + x] = fs;
+            } else if (lk == 1 && qw < 0.5) {
+                int64_t ob = (int64_t)L.opp[i] * n + x;  /* the link toward xb = x - c_i */
+                double val = fs;
+                if (link[ob] == 0) val = 2.0 * qw * fs + (1.0 - 2.0 * qw) * post_collision(&L, f, n, nbr[ob], i, tau);
+                fout[(int64_t)L.opp[i] * n + x] = val;
+            } else if (lk == 1) {
+                fout[(int64_t)L.opp[i] * n + x] = fs / (2.0 * qw) + (1.0 - 1.0 / (2.0 * qw)) * fsa[L.opp[i]];
             } else if (io_kind && io_kind[lk - 2] == 1) {
                 int k = lk - 2;
                 double U = iolet_rho(k, t, rho_mean, amp, period, phase);
@@ -300,7 +331,7 @@ int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double t
              const double *period, const double *phase, int64_t t,
              const double *f, double *fout) {
     return orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
-                       t, f, fout);
+                       NULL, t, f, fout);
 }
 
 /* nsteps steps from time t0; f holds the state on entry and on exit;
@@ -308,11 +339,12 @@ int orc_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double t
 int orc_run_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
                int n_io, const double *rho_mean, const double *amp, const double *period,
                const double *phase, const int32_t *io_kind, const double *io_normal,
-               const double *weight, int64_t t0, int64_t nsteps, double *f, double *work) {
+               const double *weight, const double *wall_q, int64_t t0, int64_t nsteps, double *f,
+               double *work) {
     double *a = f, *b = work;
     for (int64_t s = 0; s < nsteps; ++s) {
         int r = orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, io_kind,
-                            io_normal, weight, t0 + s, a, b);
+                            io_normal, weight, wall_q, t0 + s, a, b);
         if (r) return r;
         double *tmp = a; a = b; b = tmp;
     }
@@ -324,7 +356,7 @@ int orc_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double ta
             int n_io, const double *rho_mean, const double *amp, const double *period,
             const double *phase, int64_t t0, int64_t nsteps, double *f, double *work) {
     return orc_run_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
-                      t0, nsteps, f, work);
+                      NULL, t0, nsteps, f, work);
 }
 
 /* --------------------------------------------------------------- macros */

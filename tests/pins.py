@@ -598,3 +598,75 @@ ALL_FAST += [
     ("render_camera", pin_render_camera),
     ("render_miss", pin_render_miss),
 ]
+
+
+# ---------------------------------------------------------------- interpolated (BFL) walls
+
+def _slab_wall_q(o, q, g, link, q_lo, q_hi):
+    """Fluid fractions of the wall links of G.slab: q_lo for the links toward
+    the wall below (c_z = -1), q_hi toward the wall above (c_z = +1); the
+    walls sit at z = -q_lo and z = h - 1 + q_hi."""
+    e = np.asarray(o.lattice(q)[0]).reshape(q, 3)
+    wq = np.full(link.shape, 0.5)
+    for i in range(q):
+        w = link[i] == 1
+        wq[i, w & (e[i, 2] < 0)] = q_lo
+        wq[i, w & (e[i, 2] > 0)] = q_hi
+    return wq
+
+
+def bfl_slab_wall_error(o, q, h, q_lo, q_hi, tau=0.8, steps=None):
+    """Distance (lattice units) between the zeros of the steady BFL channel
+    profile and the true wall positions, below and above."""
+    nx = 64 if h < 20 else 128
+    g = G.slab(nx, 2, h)
+    nbr, link = _setup(o, q, g)
+    wq = _slab_wall_q(o, q, g, link, q_lo, q_hi)
+    steps = steps or int(4000 * (h / 12.0) ** 2)
+    f = o.run_bc(q, nbr, link, tau, o.rest_state(q, g.n), steps, wall_q=wq, geom=g)
+    _, u, _ = o.macros(q, link, tau, f)
+    x, y, z = g.xyz.T
+    sel = (x == nx // 2) & (y == 0)
+    roots = np.sort(np.roots(np.polyfit(z[sel], u[sel, 0], 2)).real)
+    return roots[0] + q_lo, roots[1] - (h - 1 + q_hi)
+
+
+def pin_bfl_halfway(o, q):
+    """BFL with q = 1/2 on every wall link is the plain half-way bounce-back."""
+    g = G.random_mask((7, 6, 5), p=0.6, seed=21, n_iolets=2)
+    nbr, link = _setup(o, q, g)
+    rng = np.random.default_rng(3)
+    f0 = o.rest_state(q, g.n) * (1.0 + 0.01 * (2 * rng.random((q, g.n)) - 1))
+    a = o.run(q, nbr, link, 0.7, f0, 15, geom=g)
+    b = o.run_bc(q, nbr, link, 0.7, f0, 15, wall_q=np.full((q, g.n), 0.5), geom=g)
+    assert np.array_equal(a, b)
+
+
+def pin_bfl_rest(o, q):
+    """Both BFL interpolations have weights summing to 1, so the rest state
+    stays at rest for any wall position."""
+    g = G.random_mask((7, 6, 5), p=0.6, seed=22, n_iolets=0)
+    nbr, link = _setup(o, q, g)
+    rng = np.random.default_rng(4)
+    wq = rng.uniform(0.02, 1.0, (q, g.n))
+    f0 = o.rest_state(q, g.n)
+    f = o.run_bc(q, nbr, link, 0.7, f0, 40, wall_q=wq, geom=g)
+    assert np.abs(f - f0).max() < 1e-14
+
+
+def pin_bfl_slab(o, q):
+    """Plane Poiseuille flow between walls off the half-way position: the zeros
+    of the BFL profile follow the walls to within 0.05 lattice units at
+    h = 12 (the linear interpolation leaves a tau- and q-dependent slip of
+    this size, halving with each doubling of h), where half-way bounce-back
+    would put them up to 0.4 away."""
+    for q_lo, q_hi in ((0.1, 0.7), (0.8, 0.35)):
+        lo, hi = bfl_slab_wall_error(o, q, 12, q_lo, q_hi)
+        assert abs(lo) < 0.05 and abs(hi) < 0.05, (q_lo, q_hi, lo, hi)
+
+
+ALL_FAST += [
+    ("bfl_halfway19", lambda o: pin_bfl_halfway(o, 19)),
+    ("bfl_rest15", lambda o: pin_bfl_rest(o, 15)),
+    ("bfl_slab19", lambda o: pin_bfl_slab(o, 19)),
+]

@@ -55,6 +55,13 @@ MUTANTS = {
     "render_behind_eye": ("if (tn < 0.0) tn = 0.0;", "if (tn < -1e300) tn = 0.0;"),
     "render_no_early_stop": ("if (t0 >= tf || A >= a_stop) break;", "if (t0 >= tf || A >= 1.0) break;"),
     "render_no_alpha_clamp": ("if (a > 1.0) a = 1.0;", "if (a > 9.0) a = 1.0;"),
+    "bfl_weights_swapped": ("val = 2.0 * qw * fs + (1.0 - 2.0 * qw) * post_collision(",
+                            "val = (1.0 - 2.0 * qw) * fs + 2.0 * qw * post_collision("),
+    "bfl_upstream_population": ("post_collision(&L, f, n, nbr[ob], i, tau)",
+                                "post_collision(&L, f, n, nbr[ob], L.opp[i], tau)"),
+    "bfl_high_own_population": ("(1.0 - 1.0 / (2.0 * qw)) * fsa[L.opp[i]]", "(1.0 - 1.0 / (2.0 * qw)) * fsa[i]"),
+    "bfl_high_factor": ("fs / (2.0 * qw) +", "fs / qw +"),
+    "bfl_collision_tau": ("return h[i] - (h[i] - he[i]) / tau;", "return h[i] - (h[i] - he[i]) * tau;"),
     "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
                   "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }

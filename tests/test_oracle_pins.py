@@ -100,3 +100,24 @@ def test_velocity_iolet_flux_balance(o, q):
 @pytest.mark.parametrize("name", ["homogeneous", "trilinear", "midpoint", "over", "camera", "miss"])
 def test_render(o, name):
     dict(pins.ALL_FAST)["render_" + name](o)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_bfl_halfway_and_rest(o, q):
+    pins.pin_bfl_halfway(o, q)
+    pins.pin_bfl_rest(o, q)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_bfl_slab(o, q):
+    pins.pin_bfl_slab(o, q)
+
+
+def test_bfl_second_order():
+    """Doubling the channel width (at fixed tau) halves the wall-position
+    error in lattice units: BFL is second-order accurate."""
+    o = oracle.default()
+    e12 = pins.bfl_slab_wall_error(o, 19, 12, 0.1, 0.7)
+    e24 = pins.bfl_slab_wall_error(o, 19, 24, 0.1, 0.7)
+    for a, b in zip(e12, e24):
+        assert 1.7 < a / b < 2.4, (e12, e24)
