@@ -68,18 +68,40 @@ def make_geometry(name: str):
     cache = os.path.join(tempfile.gettempdir(), "hemelb_gb300_geom_%s.npz" % name)
     if os.path.exists(cache):
         z = np.load(cache)
+        meta = json.loads(str(z["meta"])) if "meta" in z.files else {}
         return G.Geometry(name=str(z["name"]), xyz=z["xyz"], io_xyz=z["io_xyz"], io_id=z["io_id"],
                           periodic=z["periodic"], rho_mean=z["rho_mean"], amp=z["amp"],
-                          period=z["period"], phase=z["phase"])
+                          period=z["period"], phase=z["phase"], meta=meta)
     g = {"vessel_tree": G.vessel_tree, "aneurysm": G.aneurysm, "tube": G.tube}[name]()
     try:
         np.savez(cache + ".tmp.npz", name=g.name, xyz=g.xyz, io_xyz=g.io_xyz, io_id=g.io_id,
                  periodic=g.periodic, rho_mean=g.rho_mean, amp=g.amp, period=g.period,
-                 phase=g.phase)
+                 phase=g.phase, meta=json.dumps({"shape": g.meta.get("shape")}))
         os.replace(cache + ".tmp.npz", cache)
     except OSError:
         pass
     return g
+
+
+def wall_fractions_cached(g, q: int, link):
+    """Wall fractions of the geometry's analytic shape (G.wall_fractions),
+    cached beside the geometry (only the wall links are stored)."""
+    from paper_1906_11925_gb300 import lbm
+
+    cache = os.path.join(tempfile.gettempdir(), "hemelb_gb300_wallq_%s_q%d.npz" % (g.name, q))
+    if os.path.exists(cache):
+        z = np.load(cache)
+        wq = np.full((q, g.n), 0.5)
+        wq.reshape(-1)[z["idx"]] = z["val"]
+        return wq
+    wq = G.wall_fractions(g, lbm.lattice_vectors(q), link)
+    idx = np.flatnonzero((np.asarray(link) == 1).reshape(-1))
+    try:
+        np.savez(cache + ".tmp.npz", idx=idx, val=wq.reshape(-1)[idx])
+        os.replace(cache + ".tmp.npz", cache)
+    except OSError:
+        pass
+    return wq
 
 
 dist_env = replicas.rank_env
@@ -190,10 +212,10 @@ def run_ours(args):
     def max_over_ranks(v):
         return replicas.max_over_ranks(v, world, device="cuda")
 
-    def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL):
+    def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL, wall_q=None):
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
-                        streaming=streaming)
+                        streaming=streaming, wall_q=wall_q)
         rho = torch.empty(g.n, dtype=torch.float32, device="cuda")
         u = torch.empty(g.n, 3, dtype=torch.float32, device="cuda")
         wss = torch.empty(g.n, dtype=torch.float32, device="cuda")
@@ -359,6 +381,14 @@ def run_ours(args):
     e2e = e2e_leg() if "e2e" in legs else None
     adj = adjoint_leg() if "adjoint" in legs else None
     rnd = render_leg() if "render" in legs else None
+    if "bfl" in legs:
+        # interpolated walls at the analytic wall positions of the tree
+        wq = wall_fractions_cached(g, q, link)
+        rbfl32 = device_leg(lbm.STORE_FP32, wall_q=wq)
+        rbfl16 = device_leg(lbm.STORE_FP16, wall_q=wq)
+        n_bfl_sites = int(((np.asarray(link) == 1) & (wq != 0.5)).any(axis=0).sum())
+    else:
+        rbfl32 = rbfl16 = None
 
     n_lb = args.steps * inner
     value = world * metrics.msups(g.n, n_lb, r32["total_ms"] / 1e3)
@@ -418,11 +448,20 @@ def run_ours(args):
                      "roofline": roofline(raa16, "fp16", "aa")}},
         "adjoint": adj,
         "render": rnd,
+        "bfl": None if not rbfl32 else {
+            "walls": "Bouzidi-Firdaouss-Lallemand interpolation at the analytic wall positions",
+            "sites_with_interpolated_links": n_bfl_sites,
+            "fp32": {"value": round(world * metrics.msups(g.n, n_lb, rbfl32["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(rbfl32["total_ms"] / args.steps, 4),
+                     "roofline": roofline(rbfl32, "fp32")},
+            "fp16": {"value": round(world * metrics.msups(g.n, n_lb, rbfl16["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(rbfl16["total_ms"] / args.steps, 4),
+                     "roofline": roofline(rbfl16, "fp16")}},
         # per benchmark step: inner x (bulk-site launch + iolet-site launch),
         # the fields, and the two mass kernels
         "gpu_launches": args.steps * (inner * (2 if g.n_iolets else 1) + 1 + 2),
         "clocks": r32["clocks"],
-        "finite": all(r is None or r["finite"] for r in (r32, r16, raa32, raa16)),
+        "finite": all(r is None or r["finite"] for r in (r32, r16, raa32, raa16, rbfl32, rbfl16)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, g, nbr, link, q, tau,
@@ -499,8 +538,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
-    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint,render",
-                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint, render")
+    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint,render,bfl",
+                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint, render, bfl")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--adjoint-snapshots", type=int, default=0,
                     help="snapshot count (default: as many as fit in 150 GB)")

@@ -101,7 +101,17 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              in place by the AA pattern (even steps touch only a site's own
  *              slots, odd steps gather and scatter through the table): half
  *              the population memory and half the table traffic; identical
- *              results (the same collision arithmetic). */
+ *              results (the same collision arithmetic).
+ *   wall_q     q x n doubles, caller order, or NULL (every wall half-way):
+ *              for a wall link (link[i][x] == 1) the fraction of the link
+ *              from x along c_i that lies in the fluid, in (0, 1], rounded to
+ *              a multiple of 2^-24; ignored elsewhere.  A wall link with
+ *              q != 1/2 uses the Bouzidi-Firdaouss-Lallemand interpolation
+ *              (the paper's BFL wall boundary, Section 3.2), with x_b = x - c_i:
+ *              q < 1/2 and x_b fluid: f_opp(i)(x, t+1) = 2q f*_i(x) + (1 - 2q) f*_i(x_b);
+ *              q >= 1/2: f_opp(i)(x, t+1) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_opp(i)(x);
+ *              q < 1/2 without a fluid x_b: the half-way rule.  Requires
+ *              LBM_STREAM_PULL; not differentiated (lbm_objective_grad). */
 typedef struct {
     int32_t q;
     int32_t storage;
@@ -117,6 +127,7 @@ typedef struct {
     const int32_t *iolet_kind;
     const double *iolet_normal;
     const double *velocity_weight;
+    const double *wall_q;
 } lbm_params;
 
 /* Neighbour-link table of a sparse site list (Section 2: every fluid site

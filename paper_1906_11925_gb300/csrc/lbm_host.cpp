@@ -45,6 +45,7 @@ struct lbm_ctx {
     int io_kind[LBM_MAX_IOLETS] = {};
     double io_normal[LBM_MAX_IOLETS][3] = {};
     bool has_velocity_iolet = false;
+    bool has_bfl = false;  // interpolated wall links in the table
     float *vel_weight = nullptr;
     double *partials = nullptr, *mass_dev = nullptr;
     int *err_flag = nullptr;
@@ -505,6 +506,19 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     const int q = p->q;
     st = validate_tables(q, p->n_iolets, n, nbr, link);
     if (st != LBM_OK) return st;
+    // interpolated walls: q in (0, 1] on every wall link; pull streaming only
+    const double *wq = p->wall_q;
+    bool any_bfl = false;
+    if (wq) {
+        for (int64_t o = 0; o < (int64_t)q * n; ++o) {
+            if (link[o] != 1) continue;
+            if (!(wq[o] > 0.0 && wq[o] <= 1.0)) return fail(nullptr, LBM_ERR_ARG, "wall_q must lie in (0, 1]");
+            any_bfl |= wq[o] != 0.5;
+        }
+        if (any_bfl && p->streaming != LBM_STREAM_PULL)
+            return fail(nullptr, LBM_ERR_ARG, "interpolated walls need LBM_STREAM_PULL");
+    }
+    auto bfl_link = [&](int64_t o) { return any_bfl && link[o] == 1 && wq[o] != 0.5; };
     const int64_t lim = 1LL << 19;
     for (int64_t i = 0; i < 3 * n; ++i)
         if (xyz[i] < -lim || xyz[i] >= lim) return fail(nullptr, LBM_ERR_ARG, "coordinate out of range");
@@ -546,8 +560,9 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             uint64_t k = spread3((uint64_t)(xyz[3 * x] - lo[0])) |
                          (spread3((uint64_t)(xyz[3 * x + 1] - lo[1])) << 1) |
                          (spread3((uint64_t)(xyz[3 * x + 2] - lo[2])) << 2);
-            bool io_site = false;
-            for (int i = 1; i < q; ++i) io_site |= link[(int64_t)i * n + x] >= 2;
+            bool io_site = false;  // an iolet or an interpolated wall link
+            for (int i = 1; i < q; ++i)
+                io_site |= link[(int64_t)i * n + x] >= 2 || bfl_link((int64_t)i * n + x);
             if (!io_site) ++n_bulk;
             keys[(size_t)x] = {k | ((uint64_t)io_site << 63), (int32_t)x};
         }
@@ -565,7 +580,9 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         for (int i = 1; i < q; ++i) {
             const int j = opp(i);  // the link that population i arrives through
             const int lk = link[(int64_t)j * n + x];
-            tab[(size_t)(i - 1) * npad + xi] = lk == 0 ? inv[(size_t)nbr[(int64_t)j * n + x]] : -lk;
+            tab[(size_t)(i - 1) * npad + xi] = lk == 0 ? inv[(size_t)nbr[(int64_t)j * n + x]]
+                                               : bfl_link((int64_t)j * n + x) ? bfl_code(wq[(int64_t)j * n + x])
+                                                                              : -lk;
         }
     }
 
@@ -658,6 +675,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.c16_esc = c->c16_esc;
     L.c16_off = c->c16_off;
     L.c16_cnt = c->c16_cnt;
+    L.bfl = any_bfl ? 1 : 0;
+    c->has_bfl = any_bfl;
     CKC(launch_zero(L, c->f_cur, c->stream));
     if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
@@ -891,7 +910,7 @@ HGB_API lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link) {
         for (int j = 1; j < q; ++j) {
             const int32_t s = tab[(size_t)(opp(j) - 1) * npad + xi];
             nbr[(int64_t)j * n + x] = s >= 0 ? perm[(size_t)s] : -1;
-            link[(int64_t)j * n + x] = (uint8_t)(s >= 0 ? 0 : -s);
+            link[(int64_t)j * n + x] = (uint8_t)(s >= 0 ? 0 : is_bfl(s) ? 1 : -s);
         }
     }
     return LBM_OK;
@@ -1097,6 +1116,8 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (!std::isfinite(obj->scale)) return fail(ctx, LBM_ERR_ARG, "objective scale is not finite");
     if (ctx->has_velocity_iolet)
         return fail(ctx, LBM_ERR_STATE, "contexts with velocity iolets are not differentiated");
+    if (ctx->has_bfl)
+        return fail(ctx, LBM_ERR_STATE, "contexts with interpolated walls are not differentiated");
     if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
     if (!J) return fail(ctx, LBM_ERR_ARG, "J is NULL");
     const int q = ctx->q, K = ctx->n_iolets;

@@ -35,6 +35,28 @@ __host__ __device__
 #endif
 constexpr int tile_record_bytes(int q) { return (q - 1) * (kTile * 2 + 8 * 2); }
 
+// Interpolated (BFL) wall links in the pull table: the entry of population
+// p whose link opp(p) is a wall at fluid fraction q != 1/2 is
+// INT32_MIN + round(q 2^24) (q in (0, 1], a multiple of 2^-24).  Such sites
+// come after the bulk sites ([n_bulk, n)).  The slot the step reads back for
+// p (own slot opp(p)) holds, for q < 1/2 with a fluid upstream site, 2q f*
+// (the other part, (1 - 2q) times the population opp(p) pulled from the
+// upstream site, is added when the site gathers); otherwise the whole
+// interpolated value.
+#if defined(__CUDACC__)
+#define HGB_HD __host__ __device__
+#else
+#define HGB_HD
+#endif
+constexpr int32_t kBflMax = (int32_t)(0x80000000u + (1u << 24));
+HGB_HD inline bool is_bfl(int32_t e) { return e <= kBflMax; }
+HGB_HD inline float bfl_q(int32_t e) { return (float)((uint32_t)e ^ 0x80000000u) * (1.0f / 16777216.0f); }
+HGB_HD inline int32_t bfl_code(double q) {
+    const double k = q * 16777216.0 + 0.5;
+    uint32_t u = (uint32_t)(k < 1.0 ? 1.0 : (k > 16777216.0 ? 16777216.0 : k));
+    return (int32_t)(0x80000000u + u);
+}
+
 // Where population i of site x is stored (see src_slot in lbm_kernels.cu).
 enum Layout { LAYOUT_PULL = 0, LAYOUT_NATURAL = 1, LAYOUT_AA_SWAPPED = 2 };
 
@@ -81,6 +103,7 @@ struct DevLattice {
     const uint32_t *c16_off;      // [tiles] first escape-list index of the tile
     const uint32_t *c16_cnt;      // [tiles] escape count (padded to x4), or kTileFallback
     const float *vel_weight;      // [n - n_bulk] velocity-iolet weight of the iolet sites
+    int bfl;                      // the table holds interpolated wall links
 };
 
 // One fused pull collide-and-stream step from fin into fout.  The iolet

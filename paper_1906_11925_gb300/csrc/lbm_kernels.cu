@@ -76,8 +76,8 @@ __device__ __forceinline__ int64_t src_slot(int layout, int i, int s, int x, int
 }
 
 // Gather the q deviations of site x (pre-collision populations f(t) - w rho0).
-// Returns the smallest table entry seen (<= -2 means the site has iolet links)
-// and, through wall_n, the sum of c_i over entries == -1.
+// Returns the smallest table entry seen and, through wall_n, the sum of c_i
+// over wall entries (half-way or interpolated).
 template <int Q, bool HALF, bool STREAM_TAB>
 __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<HALF>::T *__restrict__ f,
                                       int layout, int x, float (&d)[Q], int (&wn)[3]) {
@@ -96,11 +96,21 @@ __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<
     for (int i = 1; i < Q; ++i) {
         d[i] = S::load(f + src_slot(layout, i, s[i], x, np), L.inv_scale);
         minc = min(minc, s[i]);
-        if (s[i] == -1) {
+        if (s[i] == -1 || is_bfl(s[i])) {
             wn[0] += cdir<Q>(i, 0);
             wn[1] += cdir<Q>(i, 1);
             wn[2] += cdir<Q>(i, 2);
         }
+    }
+    if (L.bfl && x >= L.n_bulk) {
+        // interpolated walls (pull layout only): q < 1/2 with a fluid
+        // upstream site adds (1 - 2q) times the population pulled from it
+#pragma unroll
+        for (int p = 1; p < Q; ++p)
+            if (is_bfl(s[p])) {
+                const float qv = bfl_q(s[p]);
+                if (qv < 0.5f && s[opp(p)] >= 0) d[p] = fmaf(1.0f - 2.0f * qv, d[opp(p)], d[p]);
+            }
     }
     return minc;
 }
@@ -269,6 +279,19 @@ k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
         float s = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) s += S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
+        if (L.bfl && x >= L.n_bulk) {
+            // interpolated walls: the slot of a q < 1/2 link holds only part of
+            // the population; the rest is (1 - 2q) times the upstream pull
+#pragma unroll
+            for (int p = 1; p < Q; ++p) {
+                const int e = L.tab[(int64_t)(p - 1) * L.npad + x];
+                if (!is_bfl(e)) continue;
+                const float qv = bfl_q(e);
+                const int u = L.tab[(int64_t)(opp(p) - 1) * L.npad + x];
+                if (qv < 0.5f && u >= 0)
+                    s += (1.0f - 2.0f * qv) * S::load(f + (int64_t)opp(p) * L.npad + u, L.inv_scale);
+            }
+        }
         acc += (double)s;
     }
     acc = block_sum(acc);
@@ -310,7 +333,13 @@ k_scatter_f64(const DevLattice L, const double *__restrict__ in, int layout,
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int s = L.tab[(int64_t)(i - 1) * np + x];
-        const double v = in[(int64_t)i * L.n + xc] - wdir<Q>(i) * (double)L.rho0;
+        double v = in[(int64_t)i * L.n + xc] - wdir<Q>(i) * (double)L.rho0;
+        if (is_bfl(s)) {
+            // the slot keeps f_i - (1 - 2q) f_opp(i) when the gather adds the rest
+            const double qv = bfl_q(s);
+            if (qv < 0.5 && L.tab[(int64_t)(opp(i) - 1) * np + x] >= 0)
+                v -= (1.0 - 2.0 * qv) * (in[(int64_t)opp(i) * L.n + xc] - wdir<Q>(i) * (double)L.rho0);
+        }
         S::store_plain(f + src_slot(layout, i, s, x, np), (float)v, L.scale);
     }
 }

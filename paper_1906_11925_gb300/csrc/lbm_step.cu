@@ -150,7 +150,7 @@ __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const
                                                const double *__restrict__ rho_io, float (&out)[Q]) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        if (s[i] <= -2) {
+        if (s[i] <= -2 && !is_bfl(s[i])) {
             const int k = -2 - s[i];
             float drk, rk;
             if (rho_io) {
@@ -175,6 +175,54 @@ __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const
             }
             const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
             out[opp(i)] = (float)wdir<Q>(i) * (drk + rk * (3.0f * cu + 4.5f * cu * cu - v.usq15));
+        }
+    }
+}
+
+// Interpolated (BFL) walls, pull form (entries is_bfl(s[p]): link opp(p) is
+// a wall at fluid fraction q; the population p of the next step is read back
+// from the site's own slot opp(p)).
+//   bfl_gather:  q < 1/2 with a fluid upstream site (s[opp(p)] >= 0): the
+//                slot holds 2q f*_opp(p)(x); add (1 - 2q) f*_opp(p)(x - c_opp(p)),
+//                the population opp(p) just pulled from the upstream site;
+//   bfl_scatter: after the collision, the slot opp(p) receives 2q f*_opp(p)
+//                (q < 1/2, fluid upstream), f*_opp(p) (q < 1/2, no fluid
+//                upstream: half-way rule), or f*_opp(p)/(2q) + (1 - 1/(2q)) f*_p
+//                (q >= 1/2), all from the collision's own values.
+template <int Q>
+__device__ __forceinline__ void bfl_gather(const int (&s)[Q], float (&d)[Q]) {
+#pragma unroll
+    for (int p = 1; p < Q; ++p) {
+        if (is_bfl(s[p])) {
+            const float qv = bfl_q(s[p]);
+            if (qv < 0.5f && s[opp(p)] >= 0) d[p] = fmaf(1.0f - 2.0f * qv, d[opp(p)], d[p]);
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void bfl_scatter(const int (&s)[Q], float (&out)[Q]) {
+#pragma unroll
+    for (int a = 1; a < Q; a += 2) {
+        const int b = a + 1;  // opp(a)
+        const float ra = out[a], rb = out[b];
+        if (is_bfl(s[b])) {  // wall along c_a: slot a feeds population b
+            const float qv = bfl_q(s[b]);
+            if (qv < 0.5f) {
+                if (s[a] >= 0) out[a] = 2.0f * qv * ra;
+            } else {
+                const float h = 0.5f / qv;
+                out[a] = fmaf(h, ra, (1.0f - h) * rb);
+            }
+        }
+        if (is_bfl(s[a])) {  // wall along c_b: slot b feeds population a
+            const float qv = bfl_q(s[a]);
+            if (qv < 0.5f) {
+                if (s[b] >= 0) out[b] = 2.0f * qv * rb;
+            } else {
+                const float h = 0.5f / qv;
+                out[b] = fmaf(h, rb, (1.0f - h) * ra);
+            }
         }
     }
 }
@@ -210,8 +258,10 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
                                      : (unsigned)opp(i) * np + (unsigned)x;
         d[i] = R::ld(fin + e);
     }
+    if (IO && L.bfl) bfl_gather<Q>(s, d);
     float out[Q];
     const Velocity v = collide<Q, HALF>(L, d, out);
+    if (IO && L.bfl) bfl_scatter<Q>(s, out);
     if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);

@@ -207,7 +207,8 @@ def tube(radius: float = 8.0, length: int = 64, nx: int = 17, ny: int = 17,
     outlet = _scan_box((0, 0, length), (nx, ny, length + 1), disk)
     return _finish("tube_r%g_L%d" % (radius, length), [fluid], [inlet, outlet],
                    rho_mean=(rho_in, rho_out),
-                   meta=dict(radius=radius, length=length, box=(nx, ny, length)))
+                   meta=dict(radius=radius, length=length, box=(nx, ny, length),
+                             shape=dict(kind="cylinder_z", center=(cx, cy), r=float(radius))))
 
 
 def aneurysm(tube_r: float = 20.0, arc_R: float = 150.0, sphere_r: float = 40.0,
@@ -225,7 +226,34 @@ def aneurysm(tube_r: float = 20.0, arc_R: float = 150.0, sphere_r: float = 40.0,
     Outlet (iolet 1): the end disk at x = -1, constant rho_out.
     Objective weights mark the sphere sites that are outside the tube.
     """
+    shape = dict(kind="aneurysm", tube_r=float(tube_r), arc_R=float(arc_R),
+                 sphere_r=float(sphere_r), arc_c=tuple(float(v) for v in arc_c))
+    fluid_pred, tube_d2, (sx, sy, sz), (e0, e1) = _aneurysm_parts(shape)
     ax, ay, az = arc_c
+    r2 = tube_r ** 2
+
+    fluid = _scan_box((0, 0, 0), (box, box, box), fluid_pred)
+    inlet = _scan_box((0, -1, 0), (box, 0, box),
+                      lambda X, Y, Z: (X - e0[0]) ** 2 + (Z - az) ** 2 <= r2)
+    outlet = _scan_box((-1, 0, 0), (0, box, box),
+                       lambda X, Y, Z: (Y - e1[1]) ** 2 + (Z - az) ** 2 <= r2)
+    g = _finish("aneurysm_r%g_R%g_s%g" % (tube_r, arc_R, sphere_r), [fluid],
+                [inlet, outlet], rho_mean=(rho_in, rho_out), amp=(amp_in, 0.0),
+                period=(period_in, 0.0), phase=(0.0, 0.0),
+                meta=dict(box=(box, box, box), sphere_c=(sx, sy, sz),
+                          sphere_r=sphere_r, shape=shape))
+    w = _sites_where(g, lambda X, Y, Z: (((X - sx) ** 2 + (Y - sy) ** 2 + (Z - sz) ** 2
+                                          <= sphere_r ** 2)
+                                         & (tube_d2(X, Y, Z) > r2)))
+    g.site_weight = w.astype(np.float64)
+    return g
+
+
+def _aneurysm_parts(shape):
+    """Inside predicate of the aneurysm shape, the squared distance to its
+    tube centreline, the sphere centre and the two arc ends."""
+    tube_r, arc_R, sphere_r = shape["tube_r"], shape["arc_R"], shape["sphere_r"]
+    ax, ay, az = shape["arc_c"]
     r2 = tube_r ** 2
     s_dist = arc_R + tube_r + sphere_r / 2.0
     sx = ax + s_dist * math.cos(math.pi / 4)
@@ -250,21 +278,7 @@ def aneurysm(tube_r: float = 20.0, arc_R: float = 150.0, sphere_r: float = 40.0,
         in_sph = (X - sx) ** 2 + (Y - sy) ** 2 + (Z - sz) ** 2 <= sphere_r ** 2
         return in_tube | in_sph
 
-    fluid = _scan_box((0, 0, 0), (box, box, box), fluid_pred)
-    inlet = _scan_box((0, -1, 0), (box, 0, box),
-                      lambda X, Y, Z: (X - e0[0]) ** 2 + (Z - az) ** 2 <= r2)
-    outlet = _scan_box((-1, 0, 0), (0, box, box),
-                       lambda X, Y, Z: (Y - e1[1]) ** 2 + (Z - az) ** 2 <= r2)
-    g = _finish("aneurysm_r%g_R%g_s%g" % (tube_r, arc_R, sphere_r), [fluid],
-                [inlet, outlet], rho_mean=(rho_in, rho_out), amp=(amp_in, 0.0),
-                period=(period_in, 0.0), phase=(0.0, 0.0),
-                meta=dict(box=(box, box, box), sphere_c=(sx, sy, sz),
-                          sphere_r=sphere_r))
-    w = _sites_where(g, lambda X, Y, Z: (((X - sx) ** 2 + (Y - sy) ** 2 + (Z - sz) ** 2
-                                          <= sphere_r ** 2)
-                                         & (tube_d2(X, Y, Z) > r2)))
-    g.site_weight = w.astype(np.float64)
-    return g
+    return fluid_pred, tube_d2, (sx, sy, sz), (e0, e1)
 
 
 def _perp_basis(d: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
@@ -307,6 +321,19 @@ def _tree_segments(seed: int, generations: int, root_r: float, length_factor: fl
     return segs
 
 
+def _tree_layout(shape):
+    """Segments of the tree shape, shifted so that the tree is centred in x
+    and y in its box: list of (start, dir, radius, length, gen, is_leaf)."""
+    segs = _tree_segments(shape["seed"], shape["generations"], shape["root_r"],
+                          shape["length_factor"], (0.0, 0.0, 0.0))
+    box = shape["box"]
+    lo = np.min([np.minimum(s[0], s[0] + s[3] * s[1]) - s[2] for s in segs], axis=0)
+    hi = np.max([np.maximum(s[0], s[0] + s[3] * s[1]) + s[2] for s in segs], axis=0)
+    shift = np.array([math.floor(box / 2.0 - (lo[0] + hi[0]) / 2.0),
+                      math.floor(box / 2.0 - (lo[1] + hi[1]) / 2.0), 0.0])
+    return [(s[0] + shift,) + tuple(s[1:]) for s in segs]
+
+
 def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
                 length_factor: float = 5.5, box: int = 1024,
                 rho_in: float = 1.001, rho_out: float = 1.0) -> Geometry:
@@ -324,12 +351,9 @@ def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
     (outlets, rho_out), numbered in breadth-first order.  With the defaults
     (length 5.5 r) the whole tree lies inside the 1024^3 box.
     """
-    segs = _tree_segments(seed, generations, root_r, length_factor, (0.0, 0.0, 0.0))
-    lo = np.min([np.minimum(s[0], s[0] + s[3] * s[1]) - s[2] for s in segs], axis=0)
-    hi = np.max([np.maximum(s[0], s[0] + s[3] * s[1]) + s[2] for s in segs], axis=0)
-    shift = np.array([math.floor(box / 2.0 - (lo[0] + hi[0]) / 2.0),
-                      math.floor(box / 2.0 - (lo[1] + hi[1]) / 2.0), 0.0])
-    segs = [(s[0] + shift,) + tuple(s[1:]) for s in segs]
+    shape = dict(kind="tree", seed=int(seed), generations=int(generations), root_r=float(root_r),
+                 length_factor=float(length_factor), box=int(box))
+    segs = _tree_layout(shape)
     fluid_keys = []
 
     def clip_lo_hi(lo, hi):
@@ -378,7 +402,7 @@ def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
     rho_mean = [rho_in] + [rho_out] * (K - 1)
     g = _finish("vessel_tree_s%d_g%d_r%g" % (seed, generations, root_r), fluid_keys,
                 io_sets, rho_mean=rho_mean,
-                meta=dict(box=(box, box, box), segments=len(segs), leaves=len(leaves)))
+                meta=dict(box=(box, box, box), segments=len(segs), leaves=len(leaves), shape=shape))
     return g
 
 
@@ -453,3 +477,154 @@ def random_populations(q: int, n: int, seed: int, amplitude: float = 1e-3,
     rng = np.random.default_rng(seed)
     base = rho0 / q
     return base * (1.0 + amplitude * (2.0 * rng.random((q, n)) - 1.0))
+
+
+# --------------------------------------------------------------------------
+# wall positions along the lattice links (for interpolated walls)
+# --------------------------------------------------------------------------
+
+Q_QUANTUM = 2.0 ** -24  # wall fractions are multiples of this
+
+
+def _quantise(qv: np.ndarray) -> np.ndarray:
+    k = np.clip(np.round(qv / Q_QUANTUM), 1, 1 / Q_QUANTUM)
+    return k * Q_QUANTUM
+
+
+def _quad_interval(alpha, beta, gamma):
+    """Interval [a, b] of s with alpha s^2 + beta s + gamma <= 0 (alpha >= 0);
+    empty intervals come back with a > b."""
+    a = np.full(alpha.shape, np.inf)
+    b = np.full(alpha.shape, -np.inf)
+    lin = alpha <= 0.0
+    a[lin & (gamma <= 0.0)] = -np.inf
+    b[lin & (gamma <= 0.0)] = np.inf
+    disc = beta * beta - 4.0 * alpha * gamma
+    ok = ~lin & (disc >= 0.0)
+    sq = np.sqrt(np.where(ok, disc, 0.0))
+    a[ok] = (-beta[ok] - sq[ok]) / (2.0 * alpha[ok])
+    b[ok] = (-beta[ok] + sq[ok]) / (2.0 * alpha[ok])
+    return a, b
+
+
+def _cylinder_interval(p, c, start, d, r, L):
+    """s-interval where p + s c lies in the capped cylinder (axis start + t d,
+    t in [0, L], radius r)."""
+    w = p - start
+    wd, cd = w @ d, c @ d
+    wp = w - wd[:, None] * d
+    cp = c - cd[:, None] * d
+    a, b = _quad_interval((cp * cp).sum(1), 2.0 * (wp * cp).sum(1), (wp * wp).sum(1) - r * r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t0, t1 = (0.0 - wd) / cd, (L - wd) / cd
+    par = cd == 0.0
+    lo = np.where(par, np.where((wd >= 0) & (wd <= L), -np.inf, np.inf), np.minimum(t0, t1))
+    hi = np.where(par, np.where((wd >= 0) & (wd <= L), np.inf, -np.inf), np.maximum(t0, t1))
+    return np.maximum(a, lo), np.minimum(b, hi)
+
+
+def _sphere_interval(p, c, centre, r):
+    w = p - centre
+    return _quad_interval((c * c).sum(1), 2.0 * (w * c).sum(1), (w * w).sum(1) - r * r)
+
+
+def _union_exit(link_id, a, b, n_links):
+    """First exit s >= 0 from the union of the intervals of each link,
+    starting inside at s = 0 (NaN where no interval contains 0)."""
+    order = np.argsort(link_id, kind="stable")
+    link_id, a, b = link_id[order], a[order], b[order]
+    out = np.full(n_links, np.nan)
+    if link_id.size == 0:
+        return out
+    starts = np.flatnonzero(np.r_[True, link_id[1:] != link_id[:-1]])
+    ids = link_id[starts]
+    cur = np.maximum.reduceat(np.where((a <= 0.0) & (b >= 0.0), b, -np.inf), starts)
+    for _ in range(8):
+        nxt = np.maximum.reduceat(np.where((a <= np.repeat(cur, np.diff(np.r_[starts, a.size])))
+                                           & (b >= 0.0), b, -np.inf), starts)
+        nxt = np.maximum(nxt, cur)
+        if np.array_equal(nxt, cur):
+            break
+        cur = nxt
+    out[ids] = np.where(np.isfinite(cur) & (cur >= 0.0), cur, np.nan)
+    return out
+
+
+def _bisect_exit(pred, p, c, samples=16, iters=30):
+    """First s in (0, 1] where pred turns false along p + s c (1 if never)."""
+    lo = np.zeros(p.shape[0])
+    hi = np.ones(p.shape[0])
+    found = np.zeros(p.shape[0], dtype=bool)
+    for j in range(1, samples + 1):
+        s = j / samples
+        q = p + s * c
+        out = ~pred(q[:, 0], q[:, 1], q[:, 2]) & ~found
+        hi[out] = s
+        lo[out] = (j - 1) / samples
+        found |= out
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        q = p + mid[:, None] * c
+        ins = pred(q[:, 0], q[:, 1], q[:, 2])
+        lo = np.where(ins & found, mid, lo)
+        hi = np.where(~ins & found, mid, hi)
+    return np.where(found, hi, 1.0)
+
+
+def wall_fractions(g: Geometry, vectors, link) -> np.ndarray:
+    """Fraction of each wall link that lies in the fluid, from the analytic
+    shape the geometry was voxelised from: for a fluid site p and a wall link
+    along the lattice vector c (link[i][x] == 1), the first s in (0, 1] where
+    p + s c leaves the shape, rounded to a multiple of 2^-24 (the wall crosses
+    the link at p + s c).  float64 [q, n]; 0.5 (the half-way wall) for links
+    that are not walls, for shapes without a description, and where the
+    shape does not contain p.  ``vectors`` [q, 3] are the lattice vectors in
+    the link table's direction order."""
+    e = np.asarray(vectors, dtype=np.float64).reshape(-1, 3)
+    link = np.asarray(link)
+    qn = e.shape[0]
+    out = np.full((qn, g.n), 0.5)
+    shape = g.meta.get("shape")
+    if shape is None or g.n == 0:
+        return out
+    ii, xx = np.nonzero(link == 1)
+    if ii.size == 0:
+        return out
+    p = g.xyz[xx].astype(np.float64)
+    c = e[ii]
+    kind = shape["kind"]
+    if kind == "cylinder_z":
+        cx, cy = shape["center"]
+        r = shape["r"]
+        a, b = _quad_interval(c[:, 0] ** 2 + c[:, 1] ** 2,
+                              2.0 * ((p[:, 0] - cx) * c[:, 0] + (p[:, 1] - cy) * c[:, 1]),
+                              (p[:, 0] - cx) ** 2 + (p[:, 1] - cy) ** 2 - r * r)
+        sv = np.where((a <= 0.0) & (b >= 0.0), b, np.nan)
+    elif kind == "aneurysm":
+        pred = _aneurysm_parts(shape)[0]
+        sv = _bisect_exit(pred, p, c)
+    elif kind == "tree":
+        segs = _tree_layout(shape)
+        ids, As, Bs = [], [], []
+        for start, d, r, L, gen, leaf in segs:
+            end = start + L * d
+            lo = np.minimum(start, end) - r - 2.0
+            hi = np.maximum(start, end) + r + 2.0
+            sel = np.flatnonzero(np.all((p >= lo) & (p <= hi), axis=1))
+            if sel.size:
+                a, b = _cylinder_interval(p[sel], c[sel], start, d, r, L)
+                ids.append(sel); As.append(a); Bs.append(b)
+            if not leaf:
+                sel = np.flatnonzero(np.all((p >= end - r - 2.0) & (p <= end + r + 2.0), axis=1))
+                if sel.size:
+                    a, b = _sphere_interval(p[sel], c[sel], end, r)
+                    ids.append(sel); As.append(a); Bs.append(b)
+        if ids:
+            sv = _union_exit(np.concatenate(ids), np.concatenate(As), np.concatenate(Bs), ii.size)
+        else:
+            sv = np.full(ii.size, np.nan)
+    else:
+        return out
+    sv = np.where(np.isnan(sv), 0.5, np.minimum(sv, 1.0))
+    out[ii, xx] = _quantise(sv)
+    return out

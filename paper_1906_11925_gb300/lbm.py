@@ -48,6 +48,19 @@ FILTER_EXACT = 1
 OBJ_WSS = 0
 OBJ_DENSITY = 1
 
+# Lattice vectors in the direction order of the C ABI (include/lbm.h): the
+# rest vector, then opposite pairs.
+_VEC15 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+          (1, 1, 1), (-1, -1, -1), (1, 1, -1), (-1, -1, 1), (1, -1, 1), (-1, 1, -1),
+          (-1, 1, 1), (1, -1, -1)]
+_VEC19 = _VEC15[:7] + [(1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
+                       (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+
+
+def lattice_vectors(q: int) -> np.ndarray:
+    """int32 [q, 3] lattice vectors c_i in the library's direction order."""
+    return np.array({15: _VEC15, 19: _VEC19}[int(q)], dtype=np.int32)
+
 
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
@@ -66,7 +79,8 @@ class _Params(C.Structure):
                 ("rho0", C.c_double), ("fp16_scale_log2", C.c_int32), ("n_iolets", C.c_int32),
                 ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
                 ("phase", C.c_void_p), ("streaming", C.c_int32), ("iolet_kind", C.c_void_p),
-                ("iolet_normal", C.c_void_p), ("velocity_weight", C.c_void_p)]
+                ("iolet_normal", C.c_void_p), ("velocity_weight", C.c_void_p),
+                ("wall_q", C.c_void_p)]
 
 
 class _View(C.Structure):
@@ -192,7 +206,7 @@ class Lattice:
                  rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
                  period: Sequence[float] = None, phase: Sequence[float] = None,
                  stream=None, streaming: int = STREAM_PULL, iolet_kind=None, iolet_normal=None,
-                 velocity_weight=None):
+                 velocity_weight=None, wall_q=None):
         self._lib = load_library()
         self._ctx = C.c_void_p()
         k = len(rho_mean)
@@ -209,11 +223,15 @@ class Lattice:
         self._kind = None if iolet_kind is None else np.ascontiguousarray(iolet_kind, dtype=np.int32)
         self._nrm = None if iolet_normal is None else np.ascontiguousarray(iolet_normal, dtype=np.float64)
         self._vw = None if velocity_weight is None else np.ascontiguousarray(velocity_weight, dtype=np.float64)
+        self._wq = None if wall_q is None else np.ascontiguousarray(wall_q, dtype=np.float64)
+        if self._wq is not None and self._wq.shape != (q, n):
+            raise ValueError("wall_q must be [q, n]")
         prm = _Params(int(q), int(storage), float(tau), float(rho0), int(fp16_scale_log2), k,
                       *[(a.ctypes.data if k else None) for a in self._io], int(streaming),
                       None if self._kind is None else self._kind.ctypes.data,
                       None if self._nrm is None else self._nrm.ctypes.data,
-                      None if self._vw is None else self._vw.ctypes.data)
+                      None if self._vw is None else self._vw.ctypes.data,
+                      None if self._wq is None else self._wq.ctypes.data)
         self.streaming = int(streaming)
         self.q, self.n, self.tau, self.storage, self.rho0 = int(q), n, float(tau), int(storage), float(rho0)
         self.n_iolets = k

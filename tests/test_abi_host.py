@@ -204,3 +204,51 @@ def test_default_lut_leaves_zero_clear():
     v = lbm.View.orbit([1.0, 2.0, 3.0], 10.0, 0.3, 0.2, 64, 32).zoom(2.0)
     assert np.isclose(np.linalg.norm(v.eye - v.center), 10.0)
     assert np.isclose(math.tan(v.fov_y / 2), math.tan(0.3) / 2.0)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_lattice_vectors_match_the_link_tables(q):
+    """The binding's direction table is the order the link builder uses."""
+    g = G.periodic_box(5, 4, 3)
+    nbr, _ = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    e = lbm.lattice_vectors(q)
+    for i in range(q):
+        d = (g.xyz[nbr[i]] - g.xyz) % g.periodic
+        assert np.all(d == e[i] % g.periodic), i
+    assert np.array_equal(e, np.asarray(oracle.lattice(q)[0]).reshape(q, 3))
+
+
+@pytest.mark.parametrize("case", ["zero", "above_one", "nan", "aa"])
+def test_create_rejects_bad_wall_fractions(case):
+    g = G.tube(radius=2, length=4, nx=5, ny=5)
+    q = 15
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    wq = np.full((q, g.n), 0.3)
+    kw = {}
+    if case == "zero":
+        wq[link == 1] = 0.0
+    elif case == "above_one":
+        wq[np.nonzero(link == 1)[0][0], np.nonzero(link == 1)[1][0]] = 1.5
+    elif case == "nan":
+        wq[link == 1] = np.nan
+    else:
+        kw["streaming"] = lbm.STREAM_AA
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Lattice(q, g.xyz, nbr, link, 0.7, rho_mean=g.rho_mean, wall_q=wq, stream=0, **kw)
+    assert ei.value.name == "LBM_ERR_ARG"
+
+
+def test_wall_fractions_of_the_tube_are_exact():
+    """Against the circle crossing computed independently here: for each wall
+    link of the tube, the wall point p + q c lies on the cylinder."""
+    g = G.tube(radius=5.3, length=6, nx=13, ny=13)
+    q = 19
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    e = lbm.lattice_vectors(q)
+    wq = G.wall_fractions(g, e, link)
+    ii, xx = np.nonzero(link == 1)
+    pts = g.xyz[xx] + wq[ii, xx][:, None] * e[ii]
+    r = np.hypot(pts[:, 0] - 6.0, pts[:, 1] - 6.0)
+    assert np.abs(r - 5.3).max() < 1e-5
+    assert np.all((wq[ii, xx] > 0) & (wq[ii, xx] <= 1)) and np.all(wq[link != 1] == 0.5)
+    assert np.all(np.round(wq * 2 ** 24) == wq * 2 ** 24)
