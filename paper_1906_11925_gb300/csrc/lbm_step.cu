@@ -238,8 +238,17 @@ __device__ __forceinline__ void bfl_scatter(const int (&s)[Q], float (&out)[Q]) 
 // IO = false: the bulk sites [0, n_bulk); IO = true: the sites with an
 // iolet link [n_bulk, n), launched separately so that the bulk kernel carries
 // no iolet code (and no register cost for it).
-template <int Q, bool HALF, bool IO>
-__global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
+// resident blocks per SM for the launch of the sites with iolet or
+// interpolated-wall links
+#ifndef HGB_TAIL_MINB_FP32
+#define HGB_TAIL_MINB_FP32 4
+#endif
+#ifndef HGB_TAIL_MINB_FP16
+#define HGB_TAIL_MINB_FP16 HGB_STEP_MINB_FP16
+#endif
+template <int Q, bool HALF, bool IO, bool BFL = false>
+__global__ void __launch_bounds__(kBlock, IO ? (HALF ? HGB_TAIL_MINB_FP16 : HGB_TAIL_MINB_FP32)
+                                             : (HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32))
 k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
        typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
        const double *__restrict__ rho_io) {
@@ -258,10 +267,10 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
                                      : (unsigned)opp(i) * np + (unsigned)x;
         d[i] = R::ld(fin + e);
     }
-    if (IO && L.bfl) bfl_gather<Q>(s, d);
+    if (BFL) bfl_gather<Q>(s, d);
     float out[Q];
     const Velocity v = collide<Q, HALF>(L, d, out);
-    if (IO && L.bfl) bfl_scatter<Q>(s, out);
+    if (BFL) bfl_scatter<Q>(s, out);
     if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
@@ -538,7 +547,10 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
             k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
         }
     }
-    if (ni) k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    if (ni && L.bfl)
+        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    else if (ni)
+        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
     return cudaGetLastError();
 }
 
