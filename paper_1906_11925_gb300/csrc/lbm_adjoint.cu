@@ -41,10 +41,16 @@ constexpr int kBlock = 256;
 // resident blocks per SM requested from the register allocator for the
 // adjoint kernel without and with the wall-shear-stress objective term
 #ifndef HGB_ADJ_MINB
-#define HGB_ADJ_MINB 4
+#define HGB_ADJ_MINB 3
 #endif
 #ifndef HGB_ADJ_MINB_WSS
 #define HGB_ADJ_MINB_WSS 2
+#endif
+// 1: the block's table rows go through shared memory instead of registers
+// (fewer registers, one barrier); measured on the tree it was not faster
+// (fp16 forward state: 0.97 against 0.93 ms per adjoint step), so it is off
+#ifndef HGB_ADJ_SMEM_TAB
+#define HGB_ADJ_SMEM_TAB 0
 #endif
 
 template <bool HALF>
@@ -112,8 +118,8 @@ __device__ __forceinline__ Stress stress(const float (&ne)[Q]) {
 template <int Q>
 __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q], const Stress &P,
                                            float rho, float ir, float ux, float uy, float uz,
-                                           float usq15, double mx, double scale, float (&lam)[Q],
-                                           double *dtau) {
+                                           float usq15, double mx, double scale, double wss_dlog,
+                                           float (&lam)[Q], double *dtau) {
     int wn0 = 0, wn1 = 0, wn2 = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
@@ -134,8 +140,7 @@ __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q
     const float v0 = t0 - tn * n0, v1 = t1 - tn * n1, v2 = t2 - tn * n2;
     const float wss = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
     if (wss > 0.f) {
-        const double ht = 0.5 / ((double)L.tau * (double)L.tau);
-        *dtau += scale * mx * (double)wss * ht / (1.0 - 0.5 / (double)L.tau);
+        *dtau += scale * mx * (double)wss * wss_dlog;
         const float iv = 1.0f / wss;
         const float h0 = v0 * iv, h1 = v1 * iv, h2 = v2 * iv;
         float M[Q];
@@ -173,20 +178,36 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           double *__restrict__ io_acc) {
     using R = AdjLoad<HALF>;
     __shared__ double part[kBlock / 32];
+#if HGB_ADJ_SMEM_TAB
+    // the block's table rows, read once (coalesced) and then from shared
+    // memory where needed, instead of being held in registers
+    __shared__ int32_t stab[Q - 1][kBlock];
+#endif
     const int x = x_begin + blockIdx.x * kBlock + threadIdx.x;
     const bool valid = x < x_end;
     const unsigned np = (unsigned)L.npad;
+#if HGB_ADJ_SMEM_TAB
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        stab[i - 1][threadIdx.x] = valid ? __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x) : 0;
+    __syncthreads();
+#define HGB_S(i) stab[(i) - 1][threadIdx.x]
+#else
+#define HGB_S(i) s[i]
+#endif
     double j_site = 0.0, dtau_site = 0.0;
     if (valid) {
+#if !HGB_ADJ_SMEM_TAB
         int s[Q];
-        float ne[Q];
 #pragma unroll
         for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+#endif
+        float ne[Q];
         ne[0] = R::ld(P + x, L.inv_scale);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
-                                         : (unsigned)opp(i) * np + (unsigned)x;
+            const int si = HGB_S(i);
+            const unsigned e = si >= 0 ? (unsigned)i * np + (unsigned)si : (unsigned)opp(i) * np + (unsigned)x;
             ne[i] = R::ld(P + e, L.inv_scale);
         }
         float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
@@ -227,7 +248,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         ls[0] = has_next ? lam_next[x] : 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-            const int sp = s[opp(i)];  // link i of x: >= 0 -> the site x + c_i
+            const int sp = HGB_S(opp(i));  // link i of x: >= 0 -> the site x + c_i
             ls[i] = 0.f;
             if (has_next) {
                 if (sp >= 0) {
@@ -278,7 +299,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         bx = rho * (bx - 3.0f * ux * sb);
         by = rho * (by - 3.0f * uy * sb);
         bz = rho * (bz - 3.0f * uz * sb);
-        dtau_site = (double)dt / ((double)L.tau * (double)L.tau);
+        dtau_site = (double)dt * obj.inv_tau2;
         const float om = L.omega, omc = 1.0f - L.omega;
         // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
         const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
@@ -296,8 +317,13 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
             const double mx = obj.weight[x];
             if (mx != 0.0) {
                 if (WSS) {
-                    j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale, lam,
-                                         &dtau_site);
+#if HGB_ADJ_SMEM_TAB
+                    int s[Q];
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) s[i] = HGB_S(i);
+#endif
+                    j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale,
+                                         obj.wss_dlog, lam, &dtau_site);
                 } else if (obj.kind == 1) {
                     j_site = mx * (double)rho;
                     const float sm = (float)(obj.scale * mx);
@@ -309,6 +335,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
 #pragma unroll
         for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
     }
+#undef HGB_S
     const double bj = block_sum(j_site, part);
     const double bt = block_sum(dtau_site, part);
     if (threadIdx.x == 0) {

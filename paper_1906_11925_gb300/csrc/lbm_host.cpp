@@ -986,6 +986,9 @@ struct AdjointRun {
         o.kind = kind;
         o.scale = scale;
         o.weight = weight;
+        const double tau = (double)c->L.tau;
+        o.inv_tau2 = 1.0 / (tau * tau);
+        o.wss_dlog = (0.5 / (tau * tau)) / (1.0 - 0.5 / tau);
         return o;
     }
     AdjStep adj_step(int64_t t) const {

@@ -154,6 +154,11 @@ struct AdjObjective {
     int kind;
     double scale;
     const double *weight;
+    // float64 constants of tau, formed on the host (a float64 division per
+    // site would load GB300's narrow FP64 pipe): 1/tau^2 and, for the wall
+    // shear stress, d(ln coef)/dtau = (1/(2 tau^2)) / (1 - 1/(2 tau))
+    double inv_tau2;
+    double wss_dlog;
 };
 
 int adjoint_blocks(const DevLattice &L);
