@@ -24,8 +24,11 @@
 // that the forward table lists as the source of population opp(i) (the site
 // x + c_i), or from x itself for wall and iolet links.  Arithmetic is float32;
 // the time accumulation of J and of every derivative is float64:
-//   - J and dJ/dtau: one float64 pair per thread block, added to by the same
-//     block at every step (a fixed grid, so the summation order is fixed);
+//   - J and dJ/dtau: the per-site terms (float) are summed over each thread
+//     block in float, and the block totals go into one float64 pair per
+//     block, added to by the same block at every step (a fixed grid, so the
+//     summation order is fixed; GB300's FP64 pipe is narrow, so nothing per
+//     site runs in float64);
 //   - iolet derivatives: one float64 slot per (iolet site, direction) and
 //     parameter, owned by one thread; reduced per iolet at the end.
 // Nothing uses atomics, so gradients are bitwise reproducible.
@@ -86,6 +89,30 @@ __device__ __forceinline__ double block_sum(double v, double *part) {
     return v;
 }
 
+// float block sum of two per-thread values (the per-site terms of J and
+// dJ/dtau), in a fixed order, valid in thread 0; the kernel converts the
+// block totals to float64 for the accumulation over blocks and steps
+__device__ __forceinline__ float2 block_sum_f2(float a, float b, float2 *part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) part[w] = make_float2(a, b);
+    __syncthreads();
+    float2 v = threadIdx.x < kBlock / 32 ? part[threadIdx.x] : make_float2(0.f, 0.f);
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    }
+    return v;
+}
+
 template <int Q>
 __device__ __forceinline__ float cdot(int i, float ux, float uy, float uz) {
     return cdir<Q>(i, 0) * ux + cdir<Q>(i, 1) * uy + cdir<Q>(i, 2) * uz;
@@ -116,10 +143,10 @@ __device__ __forceinline__ Stress stress(const float (&ne)[Q]) {
 }
 
 template <int Q>
-__device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q], const Stress &P,
-                                           float rho, float ir, float ux, float uy, float uz,
-                                           float usq15, double mx, double scale, double wss_dlog,
-                                           float (&lam)[Q], double *dtau) {
+__device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q], const Stress &P,
+                                          float rho, float ir, float ux, float uy, float uz,
+                                          float usq15, float mx, float scale, float wss_dlog,
+                                          float (&lam)[Q], float *dtau) {
     int wn0 = 0, wn1 = 0, wn2 = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
@@ -129,7 +156,7 @@ __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q
             wn2 += cdir<Q>(i, 2);
         }
     const float nn2 = (float)(wn0 * wn0 + wn1 * wn1 + wn2 * wn2);
-    if (nn2 == 0.f) return 0.0;
+    if (nn2 == 0.f) return 0.f;
     const float inn = 1.0f / sqrtf(nn2);
     const float n0 = wn0 * inn, n1 = wn1 * inn, n2 = wn2 * inn;
     const float coef = -(1.0f - 0.5f / L.tau);
@@ -140,7 +167,7 @@ __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q
     const float v0 = t0 - tn * n0, v1 = t1 - tn * n1, v2 = t2 - tn * n2;
     const float wss = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
     if (wss > 0.f) {
-        *dtau += scale * mx * (double)wss * wss_dlog;
+        *dtau += scale * mx * wss * wss_dlog;
         const float iv = 1.0f / wss;
         const float h0 = v0 * iv, h1 = v1 * iv, h2 = v2 * iv;
         float M[Q];
@@ -156,7 +183,7 @@ __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q
             By += br * (3.0f * cdir<Q>(i, 1) + 9.0f * cu * cdir<Q>(i, 1) - 3.0f * uy);
             Bz += br * (3.0f * cdir<Q>(i, 2) + 9.0f * cu * cdir<Q>(i, 2) - 3.0f * uz);
         }
-        const float sc = (float)(scale * mx) * coef;
+        const float sc = scale * mx * coef;
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const float vx = (cdir<Q>(j, 0) - ux) * ir, vy = (cdir<Q>(j, 1) - uy) * ir,
@@ -164,7 +191,7 @@ __device__ __forceinline__ double wss_term(const DevLattice &L, const int (&s)[Q
             lam[j] += sc * (M[j] - (A + Bx * vx + By * vy + Bz * vz));
         }
     }
-    return mx * (double)wss;
+    return mx * wss;
 }
 
 // One adjoint step over the sites [x_begin, x_end): the bulk sites (no
@@ -177,7 +204,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           const AdjObjective obj, int x_begin, int x_end, double *__restrict__ acc_block,
           double *__restrict__ io_acc) {
     using R = AdjLoad<HALF>;
-    __shared__ double part[kBlock / 32];
+    __shared__ float2 part[kBlock / 32];
 #if HGB_ADJ_SMEM_TAB
     // the block's table rows, read once (coalesced) and then from shared
     // memory where needed, instead of being held in registers
@@ -195,7 +222,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
 #else
 #define HGB_S(i) s[i]
 #endif
-    double j_site = 0.0, dtau_site = 0.0;
+    float j_site = 0.f, dtau_site = 0.f;
     if (valid) {
 #if !HGB_ADJ_SMEM_TAB
         int s[Q];
@@ -299,7 +326,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         bx = rho * (bx - 3.0f * ux * sb);
         by = rho * (by - 3.0f * uy * sb);
         bz = rho * (bz - 3.0f * uz * sb);
-        dtau_site = (double)dt * obj.inv_tau2;
+        dtau_site = dt * obj.inv_tau2_f;
         const float om = L.omega, omc = 1.0f - L.omega;
         // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
         const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
@@ -314,19 +341,23 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         }
         // explicit objective terms of the state f(t)
         if (obj.active) {
-            const double mx = obj.weight[x];
-            if (mx != 0.0) {
+            // a non-zero weight, tested on its bits (no float64 instruction)
+            const double mxd = obj.weight[x];
+            if ((__double_as_longlong(mxd) << 1) != 0) {
+                const float mx = (float)mxd;
                 if (WSS) {
 #if HGB_ADJ_SMEM_TAB
                     int s[Q];
 #pragma unroll
                     for (int i = 1; i < Q; ++i) s[i] = HGB_S(i);
 #endif
-                    j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale,
-                                         obj.wss_dlog, lam, &dtau_site);
+                    j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
+                                         obj.wss_dlog_f, lam, &dtau_site);
                 } else if (obj.kind == 1) {
-                    j_site = mx * (double)rho;
-                    const float sm = (float)(obj.scale * mx);
+                    // m (rho - rho0): the host adds rho0 sum(m) per state in
+                    // float64, so the float block sums carry only the small part
+                    j_site = mx * drho;
+                    const float sm = obj.scale_f * mx;
 #pragma unroll
                     for (int j = 0; j < Q; ++j) lam[j] += sm;
                 }
@@ -336,12 +367,11 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
     }
 #undef HGB_S
-    const double bj = block_sum(j_site, part);
-    const double bt = block_sum(dtau_site, part);
+    const float2 bsum = block_sum_f2(j_site, dtau_site, part);
     if (threadIdx.x == 0) {
         const int b = (x_begin == 0 ? 0 : (L.n_bulk + kBlock - 1) / kBlock) + blockIdx.x;
-        acc_block[2 * b] += bj;
-        acc_block[2 * b + 1] += bt;
+        acc_block[2 * b] += (double)bsum.x;
+        acc_block[2 * b + 1] += (double)bsum.y;
     }
 }
 

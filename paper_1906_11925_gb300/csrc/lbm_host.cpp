@@ -989,6 +989,9 @@ struct AdjointRun {
         const double tau = (double)c->L.tau;
         o.inv_tau2 = 1.0 / (tau * tau);
         o.wss_dlog = (0.5 / (tau * tau)) / (1.0 - 0.5 / tau);
+        o.inv_tau2_f = (float)o.inv_tau2;
+        o.wss_dlog_f = (float)o.wss_dlog;
+        o.scale_f = (float)scale;
         return o;
     }
     AdjStep adj_step(int64_t t) const {
@@ -1244,7 +1247,17 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (aa && nsteps > 0) ctx->aa_swapped = false;
     ctx->last_fwd_steps = R.fwd_steps;
     ctx->last_adj_steps = R.adj_steps;
-    *J = obj->scale * out[0];
+    double jsum = out[0];
+    if (obj->kind == LBM_OBJ_DENSITY) {
+        // the kernel sums m (rho - rho0); add rho0 sum(m) for every state of
+        // the window that the run visits (t0 .. t0 + nsteps)
+        double msum = 0.0;
+        for (int64_t x = 0; x < n; ++x) msum += obj->weight[x];
+        const int64_t lo = std::max<int64_t>(R.t0, obj->t_begin);
+        const int64_t hi = std::min<int64_t>(R.T, obj->t_end - 1);
+        if (hi >= lo) jsum += (double)(hi - lo + 1) * (double)ctx->L.rho0 * msum;
+    }
+    *J = obj->scale * jsum;
     if (dJ_dtau) *dJ_dtau = out[1];
     for (int k = 0; k < K; ++k) {
         if (dJ_dmean) dJ_dmean[k] = out[(size_t)(2 + k)];

@@ -159,6 +159,9 @@ struct AdjObjective {
     // shear stress, d(ln coef)/dtau = (1/(2 tau^2)) / (1 - 1/(2 tau))
     double inv_tau2;
     double wss_dlog;
+    // the same in float, for the per-site terms (summed per block in float,
+    // then in float64 over blocks and steps)
+    float inv_tau2_f, wss_dlog_f, scale_f;
 };
 
 int adjoint_blocks(const DevLattice &L);
