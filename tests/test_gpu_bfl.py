@@ -129,3 +129,22 @@ def test_bfl_vessel_tree_full_size():
     e = rel(f - rest, fo - rest)
     print("vessel tree BFL, 5 steps: deviation rel-L2 %.3e" % e)
     assert e < 1e-5
+
+
+@pytest.mark.parametrize("qv", [1.0, 2.0 ** -24, 0.5 - 2.0 ** -24, 0.5 + 2.0 ** -24])
+def test_bfl_extreme_fractions(qv):
+    """Every wall at the same fraction: at the far end of the link (q = 1),
+    at the site itself (q = 2^-24), and just either side of 1/2."""
+    q = 19
+    g = G.random_mask((8, 7, 6), p=0.65, seed=73, n_iolets=2)
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    wq = np.full((q, g.n), qv)
+    rng = np.random.default_rng(5)
+    f0 = oracle.rest_state(q, g.n) * (1.0 + 0.01 * (2 * rng.random((q, g.n)) - 1))
+    L = lbm.Lattice(q, g.xyz, nbr, link, 0.7, rho_mean=g.rho_mean, amp=g.amp, period=g.period,
+                    phase=g.phase, wall_q=wq)
+    L.set_populations(f0)
+    L.step(15)
+    fo = oracle.default().run_bc(q, nbr, link, 0.7, f0, 15, wall_q=wq, geom=g)
+    rest = oracle.rest_state(q, g.n)
+    assert rel(L.get_populations() - rest, fo - rest) < 1e-5

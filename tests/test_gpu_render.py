@@ -319,3 +319,28 @@ def test_vessel_tree_full_size_sampled():
     assert err_ex.max() <= 0.01 + 2e-4
     assert (err_ex > 2e-4).mean() < 0.02
     assert err_tex.max() <= 3e-2 and np.quantile(err_tex, 0.9) <= 1e-2
+
+
+def test_degenerate_volumes():
+    """A 1 x 1 x 1 volume, a one-voxel-thick slab, and the volume of a lattice
+    without sites (all zero) against the oracle."""
+    for shape in [(1, 1, 1), (1, 9, 13), (7, 1, 5)]:
+        vol = (0.3 + 0.5 * np.random.default_rng(sum(shape)).random(shape)).astype(np.float32)
+        V = upload(vol)
+        ctr = (np.array(shape[::-1], np.float64) - 1) / 2.0
+        for filt in (lbm.FILTER_EXACT, lbm.FILTER_TEXTURE):
+            view = lbm.View.orbit(ctr, 12.0, 0.4, 0.3, 24, 17, fov_y=0.9, dt=0.21, a_stop=1.0,
+                                  lut=lbm.default_lut(0.8), filter=filt)
+            got, want = gpu_image(V, view), oracle_image(vol, view)
+            assert (want[..., 3] > 0).any()
+            tol = (2e-4, 5e-5) if filt == lbm.FILTER_EXACT else (1e-2, 3e-3)
+            check(got, want, *tol)
+    g = G.random_mask((3, 3, 3), p=0.0, seed=1, n_iolets=0)
+    assert g.n == 0
+    nbr, link = lbm.links_build(19, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    L = lbm.Lattice(19, g.xyz, nbr, link, 0.7)
+    V = lbm.Volume.for_lattice(L)
+    V.from_lattice(L, lbm.QTY_SPEED)
+    assert V.shape == (1, 1, 1) and float(V.download().abs().max()) == 0.0
+    img = V.render(lbm.View(8, 8, [5.0, 5.0, 5.0], [0.0, 0.0, 0.0], up=[0, 0, 1]))
+    assert float(img.abs().max()) == 0.0
