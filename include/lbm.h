@@ -199,6 +199,14 @@ lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d);
  * LBM_ERR_UNSTABLE (and stores the value) when the sum is not finite. */
 lbm_status lbm_mass(lbm_ctx *ctx, double *out);
 
+/* Weighted sum over the sites of the current state f(t), accumulated in
+ * float64 in a fixed order (deterministic): sum_x weight[x] q(x), with q the
+ * wall shear stress of lbm_macros (kind LBM_OBJ_WSS) or the density
+ * (LBM_OBJ_DENSITY).  weight_d: device float64 [n], caller order, or NULL
+ * for all ones (e.g. the mean WSS over a site subset is a 0/1 weight divided
+ * by its count).  Synchronous. */
+lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, double *out);
+
 /* Populations f(t) as float64 [q][n], caller order (host memory).  Sync. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
 

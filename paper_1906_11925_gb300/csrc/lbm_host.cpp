@@ -804,6 +804,17 @@ HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     return LBM_OK;
 }
 
+HGB_API lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, double *out) {
+    if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    if (kind != LBM_OBJ_WSS && kind != LBM_OBJ_DENSITY) return fail(ctx, LBM_ERR_ARG, "unknown kind");
+    CK(ctx, launch_weighted_sum(ctx->L, ctx->f_cur, cur_layout(ctx), kind == LBM_OBJ_DENSITY ? 1 : 0,
+                                weight_d, ctx->partials, ctx->mass_dev, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!std::isfinite(*out)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite sum");
+    return LBM_OK;
+}
+
 HGB_API lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host) {
     if (!ctx || (!f_host && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     if (ctx->n == 0) return LBM_OK;

@@ -130,6 +130,12 @@ int mass_blocks();
 cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, double *out,
                         cudaStream_t s);
 
+// sum_x weight[x] q(x) of the state in f (q: 0 wall shear stress, 1
+// density; weight float64 caller order or null), deterministic float64,
+// through partials[mass_blocks()] into out.
+cudaError_t launch_weighted_sum(const DevLattice &L, const void *f, int layout, int kind,
+                                const double *weight, double *partials, double *out, cudaStream_t s);
+
 // f(t) as float64 [q][n] caller order (gather of the stored state).
 cudaError_t launch_gather_f64(const DevLattice &L, const void *f, int layout, double *out,
                               cudaStream_t s);

@@ -310,6 +310,31 @@ k_mass_final(const double *__restrict__ partials, int nparts, double base, doubl
     if (threadIdx.x == 0) out[0] = base + acc;
 }
 
+// Weighted sum over the sites of q(x) (KIND 0: wall shear stress, 1:
+// density), per-block float64 partial sums in a fixed grid (deterministic):
+// weight is float64 in caller order (null: all ones).  The density is formed
+// as rho0 + drho in float64 so that the deviation keeps its precision.
+template <int Q, bool HALF, int KIND, bool BFL>
+__global__ void __launch_bounds__(kBlock)
+k_wsum_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
+               const double *__restrict__ weight, double *__restrict__ partials) {
+    double acc = 0.0;
+    for (int x = blockIdx.x * kBlock + threadIdx.x; x < L.n; x += gridDim.x * kBlock) {
+        const double w = weight ? weight[L.perm[x]] : 1.0;
+        if (w == 0.0) continue;
+        float d[Q];
+        int wn[3];
+        gather<Q, HALF, false, BFL>(L, f, layout, x, d, wn);
+        const Moments m = moments<Q>(d, L.rho0);
+        if (KIND == 1)
+            acc += w * ((double)L.rho0 + (double)m.drho);
+        else
+            acc += w * (double)wall_shear<Q>(d, m, wn, L.tau);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 template <int Q, bool HALF, bool BFL>
 __global__ void __launch_bounds__(kBlock)
 k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
@@ -454,6 +479,33 @@ cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float 
                           float *wss, cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
     return HGB_DISPATCH(L, macros_impl, L, f, layout, rho, u, wss, s);
+}
+
+namespace {
+template <int Q, bool HALF>
+cudaError_t wsum_impl(const DevLattice &L, const void *f, int layout, int kind, const double *weight,
+                      double *partials, cudaStream_t s) {
+    using T = typename Store<HALF>::T;
+    const T *ft = (const T *)f;
+    if (L.bfl) {
+        if (kind == 1) k_wsum_partial<Q, HALF, 1, true><<<kMassBlocks, kBlock, 0, s>>>(L, ft, layout, weight, partials);
+        else k_wsum_partial<Q, HALF, 0, true><<<kMassBlocks, kBlock, 0, s>>>(L, ft, layout, weight, partials);
+    } else {
+        if (kind == 1) k_wsum_partial<Q, HALF, 1, false><<<kMassBlocks, kBlock, 0, s>>>(L, ft, layout, weight, partials);
+        else k_wsum_partial<Q, HALF, 0, false><<<kMassBlocks, kBlock, 0, s>>>(L, ft, layout, weight, partials);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_weighted_sum(const DevLattice &L, const void *f, int layout, int kind,
+                                const double *weight, double *partials, double *out, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (L.n > 0) e = HGB_DISPATCH(L, wsum_impl, L, f, layout, kind, weight, partials, s);
+    else e = cudaMemsetAsync(partials, 0, (size_t)kMassBlocks * 8, s);
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<1, kBlock, 0, s>>>(partials, kMassBlocks, 0.0, out);
+    return cudaGetLastError();
 }
 
 int mass_blocks() { return kMassBlocks; }

@@ -30,6 +30,7 @@ _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM"
 EXPORTED = (
     "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
     "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
+    "lbm_weighted_sum",
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
     "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
@@ -122,6 +123,7 @@ def load_library(build_if_missing: bool = True):
         "lbm_set_time": [P, i64],
         "lbm_macros": [P, P, P, P],
         "lbm_mass": [P, P],
+        "lbm_weighted_sum": [P, i32, P, P],
         "lbm_get_populations": [P, P],
         "lbm_get_populations_noalloc": [P, P],
         "lbm_set_populations": [P, P],
@@ -322,6 +324,23 @@ class Lattice:
         m = C.c_double()
         self._ck(self._lib.lbm_mass(self._ctx, C.byref(m)))
         return m.value
+
+    def weighted_sum(self, kind: int, weight=None) -> float:
+        """sum_x weight[x] q(x) in float64 (q: OBJ_WSS wall shear stress,
+        OBJ_DENSITY density); weight: [n] caller order (a CUDA float64 tensor,
+        or anything numpy-like, copied to the device), None = all ones."""
+        import torch
+        w = None
+        if weight is not None:
+            w = weight if (hasattr(weight, "is_cuda") and weight.is_cuda and weight.dtype == torch.float64
+                           and weight.is_contiguous()) else torch.as_tensor(
+                np.ascontiguousarray(weight, dtype=np.float64)).cuda()
+            if w.numel() != self.n:
+                raise ValueError("weight must have n entries")
+        out = C.c_double()
+        self._ck(self._lib.lbm_weighted_sum(self._ctx, int(kind), None if w is None else C.c_void_p(w.data_ptr()),
+                                            C.byref(out)))
+        return out.value
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((self.q, self.n), np.float64)

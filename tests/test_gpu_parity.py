@@ -269,3 +269,39 @@ def test_vessel_tree_full_size_one_step(tree, storage):
     err = rel_l2(deviations(q, gf), deviations(q, of))
     print("tree one step", storage, err)
     assert err <= TOL_POP[storage]
+    # the float64 reductions at full size: mean WSS over the wall sites and
+    # the density sum, against the oracle on the same populations
+    m = (link == 1).any(axis=0).astype(np.float64)
+    o = oracle.default()
+    got = L.weighted_sum(lbm.OBJ_WSS, m)
+    want = o.objective(q, link, tau, lbm.OBJ_WSS, m, gf)
+    assert abs(got / want - 1.0) < 1e-5, (got, want)
+    got = L.weighted_sum(lbm.OBJ_DENSITY)
+    want = o.objective(q, link, tau, lbm.OBJ_DENSITY, np.ones(g.n), gf)
+    assert abs(got - want) <= 1e-8 * g.n, (got, want)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_weighted_sums_match_oracle(q, storage):
+    """Float64 reductions of the current state (wall shear stress and density
+    over weighted site subsets) against the oracle's objective of the same
+    populations."""
+    g = G.tube(radius=4, length=16, nx=9, ny=9, rho_in=1.002, rho_out=0.999)
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    L = lbm.Lattice(q, g.xyz, nbr, link, 0.7, storage=storage, rho_mean=g.rho_mean)
+    L.step(200)
+    f = L.get_populations()
+    o = oracle.default()
+    rng = np.random.default_rng(q)
+    for w in (None, (rng.random(g.n) < 0.3) * 1.0, rng.normal(size=g.n)):
+        m = np.ones(g.n) if w is None else w
+        for kind in (lbm.OBJ_WSS, lbm.OBJ_DENSITY):
+            got = L.weighted_sum(kind, w)
+            want = o.objective(q, link, 0.7, kind, m, f)
+            # float32 site values: WSS to ~1e-6 of its magnitude, density to
+            # ~1e-7 of its deviation from rho0 (both sides see the same f)
+            mag = o.objective(q, link, 0.7, kind, np.abs(m), f)
+            tol = 1e-5 * mag if kind == lbm.OBJ_WSS else 1e-8 * np.abs(m).sum()
+            assert abs(got - want) <= tol, (kind, got, want, tol)
+    assert abs(L.weighted_sum(lbm.OBJ_DENSITY) - L.mass()) <= 1e-9 * L.mass()
