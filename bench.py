@@ -430,6 +430,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": rf32,
+        "paper_context": {"value": 15.17, "unit": "MSUPS",
+                          "hardware": "Exxact TWS: Intel i7-5960X + 4x GeForce GTX 1080 Ti",
+                          "workload": "patient aneurysm, 296,814 sites, D3Q19 (Table III)",
+                          "note": "another machine and workload: context, not the target"},
         "fp16": None if not r16 else {
             "value": round(world * metrics.msups(g.n, n_lb, r16["total_ms"] / 1e3), 2),
             "unit": "MSUPS", "ms_per_step": round(r16["total_ms"] / args.steps, 4),
