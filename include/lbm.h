@@ -207,6 +207,16 @@ lbm_status lbm_mass(lbm_ctx *ctx, double *out);
  * by its count).  Synchronous. */
 lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, double *out);
 
+/* Failure detection, checked on its own: the table-staged step waits for its
+ * bulk copies on mbarriers with a bounded number of polls (about 4M); a step
+ * kernel that gives up sets an error flag, returns without leaving anything
+ * in flight, and lbm_mass reports LBM_ERR_CUDA.  This call runs that bounded
+ * wait, with `limit` polls (1 .. 2^24), on a barrier that no copy completes,
+ * and stores 1 in *gave_up when the wait gave up (it always should).  The
+ * context and the device stay usable.  Synchronous on cuda_stream.  The
+ * paper has no counterpart. */
+lbm_status lbm_check_wait_timeout(uint32_t limit, void *cuda_stream, int32_t *gave_up);
+
 /* Populations f(t) as float64 [q][n], caller order (host memory).  Sync. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
 

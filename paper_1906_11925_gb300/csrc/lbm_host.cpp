@@ -804,6 +804,23 @@ HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     return LBM_OK;
 }
 
+HGB_API lbm_status lbm_check_wait_timeout(uint32_t limit, void *cuda_stream, int32_t *gave_up) {
+    if (!gave_up) return fail(nullptr, LBM_ERR_ARG, "gave_up is NULL");
+    if (limit < 1 || limit > (1u << 24)) return fail(nullptr, LBM_ERR_ARG, "limit must lie in [1, 2^24]");
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc((void **)&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_wait_probe(limit, flag, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbm_check_wait_timeout");
+    *gave_up = h;
+    return LBM_OK;
+}
+
 HGB_API lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, double *out) {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     if (kind != LBM_OBJ_WSS && kind != LBM_OBJ_DENSITY) return fail(ctx, LBM_ERR_ARG, "unknown kind");

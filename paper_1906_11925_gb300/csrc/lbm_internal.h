@@ -117,6 +117,10 @@ cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const 
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
                            const double *rho_io, cudaStream_t s);
 
+// The bounded mbarrier wait of the staged step on a barrier no copy
+// completes: sets *err when it gives up after limit polls.
+cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s);
+
 // Exact copy of a stored state between layouts.
 cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,
                             int dst_layout, cudaStream_t s);

@@ -316,10 +316,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
-    for (unsigned it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
+                                                  unsigned limit = kWaitLimit) {
+    for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// The failure path of the staged step, on its own: an mbarrier that expects
+// 16 bytes no copy will ever deliver, waited on with the same bounded wait;
+// on giving up the kernel sets *err and returns (no copy was issued, so
+// nothing is in flight; the barrier is left as the staged step leaves one).
+__global__ void k_wait_probe(int *err, unsigned limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16u);
+    if (!mbar_wait_bounded(&bar, 0u, limit)) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
@@ -564,6 +577,11 @@ cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const 
                         const double *rho_io, cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
     return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
+}
+
+cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(err, limit);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,

@@ -30,7 +30,7 @@ _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM"
 EXPORTED = (
     "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
     "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
-    "lbm_weighted_sum",
+    "lbm_weighted_sum", "lbm_check_wait_timeout",
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
     "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
@@ -124,6 +124,7 @@ def load_library(build_if_missing: bool = True):
         "lbm_macros": [P, P, P, P],
         "lbm_mass": [P, P],
         "lbm_weighted_sum": [P, i32, P, P],
+        "lbm_check_wait_timeout": [C.c_uint32, P, P],
         "lbm_get_populations": [P, P],
         "lbm_get_populations_noalloc": [P, P],
         "lbm_set_populations": [P, P],
@@ -182,6 +183,14 @@ def links_build(q: int, xyz, io_xyz=None, io_id=None, periodic=(0, 0, 0)):
     _check(lib.lbm_links_build(int(q), n, _p(xyz), io_xyz.shape[0], _p(io_xyz), _p(io_id),
                                _p(per), _p(nbr), _p(link)))
     return nbr, link
+
+
+def check_wait_timeout(limit: int = 4096, stream=None) -> bool:
+    """Run the step kernels' bounded mbarrier wait on a barrier that nothing
+    completes (``lbm_check_wait_timeout``); True when it gave up."""
+    out = C.c_int32()
+    _check(load_library().lbm_check_wait_timeout(int(limit), _stream_handle(stream), C.byref(out)))
+    return bool(out.value)
 
 
 def revolve_steps(nsteps: int, n_snap: int) -> int:
