@@ -488,10 +488,23 @@ def cpu_baseline(workload, g, nbr, link, q, tau, budget_s=15.0, lb_steps=None):
     t0 = time.perf_counter()
     oracle.run(q, nbr, link, tau, f, n, t0=1, geom=g)
     dt = time.perf_counter() - t0
-    return {"value": round(metrics.msups(g.n, n, dt), 3), "unit": "MSUPS",
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d LB steps of the full %s workload (%d sites), float64, push form"
-                      % (n, workload, g.n)}
+    out = {"value": round(metrics.msups(g.n, n, dt), 3), "unit": "MSUPS",
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "%d LB steps of the full %s workload (%d sites), float64, push form"
+                     % (n, workload, g.n)}
+    if lb_steps is None:
+        # the same on one core, one LB step
+        nt = oracle.num_threads()
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.step(q, nbr, link, tau, f, t=1, geom=g)
+            d1 = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(nt)
+        out["one_core"] = {"value": round(metrics.msups(g.n, 1, d1), 3), "unit": "MSUPS",
+                           "sample": "1 LB step of the same workload on 1 core"}
+    return out
 
 
 def run_reference(args):
