@@ -168,7 +168,7 @@ k_render(const __grid_constant__ RenderArgs a, cudaTextureObject_t tex, const ui
         // counters[0] += samples composited, counters[1] += brick jumps
         const unsigned lane_mask = __activemask();
         const unsigned ts = __reduce_add_sync(lane_mask, taken), js = __reduce_add_sync(lane_mask, jumps);
-        if ((threadIdx.x & 31) == (unsigned)(__ffs(lane_mask) - 1)) {
+        if ((tid & 31) == __ffs(lane_mask) - 1) {  // the lowest active lane of the warp
             atomicAdd(a.counters, (unsigned long long)ts);
             atomicAdd(a.counters + 1, (unsigned long long)js);
         }

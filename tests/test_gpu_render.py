@@ -344,3 +344,16 @@ def test_degenerate_volumes():
     assert V.shape == (1, 1, 1) and float(V.download().abs().max()) == 0.0
     img = V.render(lbm.View(8, 8, [5.0, 5.0, 5.0], [0.0, 0.0, 0.0], up=[0, 0, 1]))
     assert float(img.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("w,h", [(48, 20), (1, 1), (33, 9)])
+def test_sample_counters_count_every_ray_once(w, h):
+    """Nearly parallel rays (fov 1e-3 from 100 voxels away) cross the whole
+    box along z: every ray takes ceil(8 / 0.3) = 27 samples."""
+    vol = np.full((8, 9, 9), 0.5, np.float32)
+    V = upload(vol)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    view = lbm.View(w, h, [4.0, 4.0, -100.0], [4.0, 4.0, 4.0], up=[0, 1, 0], fov_y=1e-3, dt=0.3,
+                    a_stop=1.0, lut=lbm.default_lut(0.01), skip_empty=False, counters=cnt)
+    V.render(view)
+    assert cnt.tolist() == [27 * w * h, 0]
