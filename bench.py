@@ -5,11 +5,13 @@ LBGK collide-and-stream on one GB300, with its HBM roofline fraction.
 Workload (default): the seeded six-generation bifurcating vessel tree
 (root radius 48, Murray's law, 1024^3 box, ~10.8M fluid sites), D3Q19 LBGK,
 tau = 0.6, one inlet at rho 1.001 and 32 outlets at rho 1.0, synthetic data.
-One benchmark step = 100 lattice-Boltzmann time steps (one fused kernel
-launch each) + density/velocity/wall-shear-stress fields + the float64 mass
-reduction.  value = fluid sites x LB time steps / device time, fp32 storage;
-the fp16-deviation storage form is reported beside it.  The inputs (~2.4 GB
-touched per LB step) are larger than the 126 MB L2, so no flush is needed.
+One benchmark step = 100 lattice-Boltzmann time steps (fused collide-and-
+stream kernels, AA-pattern streaming in place by default, sites kept along a
+Morton curve of 32-site runs) + density/velocity/wall-shear-stress fields +
+the float64 mass reduction.  value = fluid sites x LB time steps / device
+time, fp32 storage; the fp16-deviation storage form and the pull streaming
+form are reported beside it.  The inputs (~2 GB touched per LB step) are
+larger than the 126 MB L2, so no flush is needed.
 
 ``--impl reference`` times the FP64 CPU oracle on this machine's host cores
 on the same workload and metric (a few LB steps per benchmark step).
@@ -37,7 +39,8 @@ from paper_1906_11925_gb300 import metrics  # noqa: E402
 from paper_1906_11925_gb300 import replicas  # noqa: E402
 
 LB_STEPS_PER_BENCH_STEP = 100
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md")
+PROFILE_SUMMARY = {"pull": os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md"),
+                   "aa": os.path.join(ROOT, "profiles", "k_step_aa_q19_vessel_tree.md")}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_step.cu")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -117,13 +120,14 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when it is missing or was taken on a different kernel source."""
+def recorded_traffic(summary=None):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (of the AA kernels by default), or None when it is missing or was taken
+    on a different kernel source."""
     try:
         src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
         fields = {}
-        for line in open(PROFILE_SUMMARY):
+        for line in open(summary or PROFILE_SUMMARY["aa"]):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
@@ -212,10 +216,15 @@ def run_ours(args):
     def max_over_ranks(v):
         return replicas.max_over_ranks(v, world, device="cuda")
 
-    def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL, wall_q=None):
+    main_form = args.streaming
+    alt_form = "pull" if main_form == "aa" else "aa"
+    stream_id = {"pull": lbm.STREAM_PULL, "aa": lbm.STREAM_AA}
+
+    def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL, wall_q=None,
+                   site_order=lbm.ORDER_MORTON_RUNS):
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
-                        streaming=streaming, wall_q=wall_q)
+                        streaming=streaming, wall_q=wall_q, site_order=site_order)
         rho = torch.empty(g.n, dtype=torch.float32, device="cuda")
         u = torch.empty(g.n, 3, dtype=torch.float32, device="cuda")
         wss = torch.empty(g.n, dtype=torch.float32, device="cuda")
@@ -257,7 +266,8 @@ def run_ours(args):
         # and outlet densities of its LB steps go host -> device from pinned
         # memory, and the resulting total mass comes back device -> host.
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP32, rho_mean=g.rho_mean,
-                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream,
+                        streaming=stream_id[main_form])
         K = g.n_iolets
         rows = []
         for s in range(args.warmup + args.steps):
@@ -374,18 +384,21 @@ def run_ours(args):
         return out
 
     sampler = ClockSampler(local_rank) if rank == 0 else None
-    r32 = device_leg(lbm.STORE_FP32, sampler)
-    r16 = device_leg(lbm.STORE_FP16) if "fp16" in legs else None
-    raa32 = device_leg(lbm.STORE_FP32, streaming=lbm.STREAM_AA) if "aa" in legs else None
-    raa16 = device_leg(lbm.STORE_FP16, streaming=lbm.STREAM_AA) if "aa" in legs else None
+    r32 = device_leg(lbm.STORE_FP32, sampler, streaming=stream_id[main_form])
+    r16 = device_leg(lbm.STORE_FP16, streaming=stream_id[main_form]) if "fp16" in legs else None
+    # the other streaming form, for comparison
+    alt = alt_form in legs
+    raa32 = device_leg(lbm.STORE_FP32, streaming=stream_id[alt_form]) if alt else None
+    raa16 = device_leg(lbm.STORE_FP16, streaming=stream_id[alt_form]) if alt else None
     e2e = e2e_leg() if "e2e" in legs else None
     adj = adjoint_leg() if "adjoint" in legs else None
     rnd = render_leg() if "render" in legs else None
     if "bfl" in legs:
         # interpolated walls at the analytic wall positions of the tree
         wq = wall_fractions_cached(g, q, link)
-        rbfl32 = device_leg(lbm.STORE_FP32, wall_q=wq)
-        rbfl16 = device_leg(lbm.STORE_FP16, wall_q=wq)
+        # (pull streaming; the plain Morton order measured faster with these walls)
+        rbfl32 = device_leg(lbm.STORE_FP32, wall_q=wq, site_order=lbm.ORDER_MORTON)
+        rbfl16 = device_leg(lbm.STORE_FP16, wall_q=wq, site_order=lbm.ORDER_MORTON)
         n_bfl_sites = int(((np.asarray(link) == 1) & (wq != 0.5)).any(axis=0).sum())
     else:
         rbfl32 = rbfl16 = None
@@ -402,12 +415,15 @@ def run_ours(args):
                     frac=round(achieved / peak, 4), peak_source=peak_kind,
                     bytes_per_site_update=bps, launch_us=round(per_launch_s * 1e6, 2))
 
-    traffic = recorded_traffic()
-    rf32 = roofline(r32, "fp32")
+    traffic = recorded_traffic(PROFILE_SUMMARY[main_form])
+    rf32 = roofline(r32, "fp32", main_form)
     rf32["traffic"] = traffic.get("traffic_bytes_per_launch_fp32") if traffic else None
     if r16:
-        rf16 = roofline(r16, "fp16")
+        rf16 = roofline(r16, "fp16", main_form)
         rf16["traffic"] = traffic.get("traffic_bytes_per_launch_fp16") if traffic else None
+    forms = {"pull": "pull: gather through the neighbour table from one buffer into another",
+             "aa": "AA pattern: one buffer updated in place, even steps on a site's own slots, "
+                   "odd steps through the neighbour table"}
 
     out = {
         "metric": "MSUPS (million fluid-site updates per second), fused LBGK collide-and-stream",
@@ -424,8 +440,10 @@ def run_ours(args):
         "data": "synthetic (seeded vessel geometry, fluid initialised at rest)",
         "config": {"workload": args.workload, "description": W["desc"], "lattice": "D3Q%d" % q,
                    "tau": tau, "fluid_sites": g.n, "iolets": g.n_iolets, "storage": "fp32",
+                   "streaming": forms[main_form],
+                   "site_order": "Morton curve of 32-site runs along x",
                    "lb_steps_per_bench_step": inner,
-                   "bench_step": "%d fused collide-stream launches + rho/u/WSS fields + fp64 mass"
+                   "bench_step": "%d fused collide-stream steps + rho/u/WSS fields + fp64 mass"
                                  % inner,
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -442,14 +460,14 @@ def run_ours(args):
             "value": round(world * metrics.msups(g.n, n_lb, e2e["seconds"]), 2),
             "unit": "MSUPS", "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
             "path": "lbm_step_driven (host iolet densities, pinned) + lbm_mass (host)"},
-        "aa": None if not raa32 else {
-            "streaming": "AA pattern, one population buffer updated in place",
+        alt_form: None if not raa32 else {
+            "streaming": forms[alt_form],
             "fp32": {"value": round(world * metrics.msups(g.n, n_lb, raa32["total_ms"] / 1e3), 2),
                      "unit": "MSUPS", "ms_per_step": round(raa32["total_ms"] / args.steps, 4),
-                     "roofline": roofline(raa32, "fp32", "aa")},
+                     "roofline": roofline(raa32, "fp32", alt_form)},
             "fp16": {"value": round(world * metrics.msups(g.n, n_lb, raa16["total_ms"] / 1e3), 2),
                      "unit": "MSUPS", "ms_per_step": round(raa16["total_ms"] / args.steps, 4),
-                     "roofline": roofline(raa16, "fp16", "aa")}},
+                     "roofline": roofline(raa16, "fp16", alt_form)}},
         "adjoint": adj,
         "render": rnd,
         "bfl": None if not rbfl32 else {
@@ -555,8 +573,11 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
-    ap.add_argument("--legs", default="fp32,fp16,aa,e2e,adjoint,render,bfl",
-                    help="comma list of fp32 (always run), fp16, aa, e2e, adjoint, render, bfl")
+    ap.add_argument("--streaming", choices=("aa", "pull"), default="aa",
+                    help="streaming form of the main legs (the other one is the comparison leg)")
+    ap.add_argument("--legs", default="fp32,fp16,pull,aa,e2e,adjoint,render,bfl",
+                    help="comma list of fp32 (always run), fp16, pull, aa (the comparison leg "
+                         "of the form not chosen by --streaming), e2e, adjoint, render, bfl")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--adjoint-snapshots", type=int, default=0,
                     help="snapshot count (default: as many as fit in 150 GB)")

@@ -68,6 +68,7 @@ enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1 };
 enum { LBM_STREAM_PULL = 0, LBM_STREAM_AA = 1 };
 enum { LBM_IOLET_DENSITY = 0, LBM_IOLET_VELOCITY = 1 };
 enum { LBM_MAX_IOLETS = 64 };
+enum { LBM_ORDER_MORTON_RUNS = 0, LBM_ORDER_MORTON = 1, LBM_ORDER_ROWS = 2 };
 
 typedef struct lbm_ctx lbm_ctx; /* opaque */
 
@@ -111,7 +112,19 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              q < 1/2 and x_b fluid: f_opp(i)(x, t+1) = 2q f*_i(x) + (1 - 2q) f*_i(x_b);
  *              q >= 1/2: f_opp(i)(x, t+1) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_opp(i)(x);
  *              q < 1/2 without a fluid x_b: the half-way rule.  Requires
- *              LBM_STREAM_PULL; not differentiated (lbm_objective_grad). */
+ *              LBM_STREAM_PULL; not differentiated (lbm_objective_grad).
+ *   site_order the order the device keeps the sites in (every result is the
+ *              same, outputs are in caller order; the sites with iolet or
+ *              interpolated-wall links come last in all of them):
+ *              LBM_ORDER_MORTON_RUNS (0, default): runs of 32 sites along x
+ *              (from x multiples of 32) kept contiguous, the runs ordered
+ *              along the Morton curve of (x / 32, y, z): a warp's 32 sites
+ *              then have neighbours in a few contiguous runs, which makes the
+ *              scattered stores of the AA odd step nearly coalesced (the
+ *              sites after the bulk, a shell on the walls and iolets, stay in
+ *              plain Morton order);
+ *              LBM_ORDER_MORTON (1): the Morton (Z-order) curve of (x, y, z);
+ *              LBM_ORDER_ROWS (2): (z, y, x) row order. */
 typedef struct {
     int32_t q;
     int32_t storage;
@@ -128,6 +141,7 @@ typedef struct {
     const double *iolet_normal;
     const double *velocity_weight;
     const double *wall_q;
+    int32_t site_order;
 } lbm_params;
 
 /* Neighbour-link table of a sparse site list (Section 2: every fluid site

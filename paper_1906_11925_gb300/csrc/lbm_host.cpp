@@ -381,6 +381,9 @@ lbm_status validate_params(const lbm_params *p) {
         return fail(nullptr, LBM_ERR_ARG, "fp16_scale_log2 must be in [0, 24]");
     if (p->streaming != LBM_STREAM_PULL && p->streaming != LBM_STREAM_AA)
         return fail(nullptr, LBM_ERR_ARG, "streaming must be LBM_STREAM_PULL or LBM_STREAM_AA");
+    if (p->site_order != LBM_ORDER_MORTON_RUNS && p->site_order != LBM_ORDER_MORTON &&
+        p->site_order != LBM_ORDER_ROWS)
+        return fail(nullptr, LBM_ERR_ARG, "unknown site_order");
     if (p->n_iolets < 0 || p->n_iolets > LBM_MAX_IOLETS)
         return fail(nullptr, LBM_ERR_ARG, "n_iolets out of range");
     if (p->n_iolets > 0 && (!p->rho_mean || !p->amp || !p->period || !p->phase))
@@ -542,8 +545,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         return fail(nullptr, LBM_ERR_NOMEM, msg);
     }
 
-    // Internal order: sites without iolet links in Morton order, then the
-    // sites with an iolet link in Morton order (the kernel tests x >= n_bulk
+    // Internal order: sites without iolet links along the chosen curve
+    // (site_order), then the sites with an iolet link along it (the kernel tests x >= n_bulk
     // instead of scanning the table for iolet entries).
     std::vector<int32_t> perm((size_t)n);
     int64_t n_bulk = 0;
@@ -557,12 +560,20 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         std::vector<std::pair<uint64_t, int32_t>> keys((size_t)n);
 #pragma omp parallel for schedule(static) reduction(+ : n_bulk)
         for (int64_t x = 0; x < n; ++x) {
-            uint64_t k = spread3((uint64_t)(xyz[3 * x] - lo[0])) |
-                         (spread3((uint64_t)(xyz[3 * x + 1] - lo[1])) << 1) |
-                         (spread3((uint64_t)(xyz[3 * x + 2] - lo[2])) << 2);
+            const uint64_t rx = (uint64_t)(xyz[3 * x] - lo[0]), ry = (uint64_t)(xyz[3 * x + 1] - lo[1]),
+                           rz = (uint64_t)(xyz[3 * x + 2] - lo[2]);
             bool io_site = false;  // an iolet or an interpolated wall link
             for (int i = 1; i < q; ++i)
                 io_site |= link[(int64_t)i * n + x] >= 2 || bfl_link((int64_t)i * n + x);
+            // the sites after the bulk lie on the walls and iolets (a shell,
+            // not runs along x): they keep the plain Morton order
+            uint64_t k;
+            if (p->site_order == LBM_ORDER_ROWS)
+                k = (rz << 42) | (ry << 21) | rx;
+            else if (p->site_order == LBM_ORDER_MORTON_RUNS && !io_site)
+                k = ((spread3(rx >> 5) | (spread3(ry) << 1) | (spread3(rz) << 2)) << 5) | (rx & 31);
+            else
+                k = spread3(rx) | (spread3(ry) << 1) | (spread3(rz) << 2);
             if (!io_site) ++n_bulk;
             keys[(size_t)x] = {k | ((uint64_t)io_site << 63), (int32_t)x};
         }

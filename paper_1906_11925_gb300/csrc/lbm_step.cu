@@ -472,10 +472,10 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 // After an even step A holds the populations of time t+1 in swapped slots;
 // after an odd step they are back in natural order, A[i][x] = f_i(x).
 #ifndef HGB_AA_MINB_FP32
-#define HGB_AA_MINB_FP32 3
+#define HGB_AA_MINB_FP32 4
 #endif
 #ifndef HGB_AA_MINB_FP16
-#define HGB_AA_MINB_FP16 3
+#define HGB_AA_MINB_FP16 4
 #endif
 template <int Q, bool HALF, bool ODD, bool IO>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)

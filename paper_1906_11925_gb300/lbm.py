@@ -23,6 +23,9 @@ STREAM_AA = 1
 IOLET_DENSITY = 0
 IOLET_VELOCITY = 1
 MAX_IOLETS = 64
+ORDER_MORTON_RUNS = 0
+ORDER_MORTON = 1
+ORDER_ROWS = 2
 
 _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM",
            4: "LBM_ERR_CUDA", 5: "LBM_ERR_UNSTABLE", 6: "LBM_ERR_STATE"}
@@ -81,7 +84,7 @@ class _Params(C.Structure):
                 ("rho_mean", C.c_void_p), ("amp", C.c_void_p), ("period", C.c_void_p),
                 ("phase", C.c_void_p), ("streaming", C.c_int32), ("iolet_kind", C.c_void_p),
                 ("iolet_normal", C.c_void_p), ("velocity_weight", C.c_void_p),
-                ("wall_q", C.c_void_p)]
+                ("wall_q", C.c_void_p), ("site_order", C.c_int32)]
 
 
 class _View(C.Structure):
@@ -217,7 +220,7 @@ class Lattice:
                  rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
                  period: Sequence[float] = None, phase: Sequence[float] = None,
                  stream=None, streaming: int = STREAM_PULL, iolet_kind=None, iolet_normal=None,
-                 velocity_weight=None, wall_q=None):
+                 velocity_weight=None, wall_q=None, site_order: int = ORDER_MORTON_RUNS):
         self._lib = load_library()
         self._ctx = C.c_void_p()
         k = len(rho_mean)
@@ -242,7 +245,7 @@ class Lattice:
                       None if self._kind is None else self._kind.ctypes.data,
                       None if self._nrm is None else self._nrm.ctypes.data,
                       None if self._vw is None else self._vw.ctypes.data,
-                      None if self._wq is None else self._wq.ctypes.data)
+                      None if self._wq is None else self._wq.ctypes.data, int(site_order))
         self.streaming = int(streaming)
         self.q, self.n, self.tau, self.storage, self.rho0 = int(q), n, float(tau), int(storage), float(rho0)
         self.n_iolets = k

@@ -168,6 +168,7 @@ def test_struct_layouts_match_the_header(tmp_path):
                    '         offsetof(lbm_params, velocity_weight), sizeof(lbm_objective),\n'
                    '         sizeof(lbm_view), offsetof(lbm_view, fov_y), offsetof(lbm_view, filter),\n'
                    '         offsetof(lbm_view, lut));\n  printf("%zu\\n", offsetof(lbm_view, counters_d));\n'
+                   '  printf("%zu\\n", offsetof(lbm_params, site_order));\n'
                    '  return 0;\n}\n')
     exe = tmp_path / "layout"
     import subprocess
@@ -177,7 +178,7 @@ def test_struct_layouts_match_the_header(tmp_path):
                                           text=True).stdout.split()]
     want = [C.sizeof(lbm._Params), lbm._Params.velocity_weight.offset, C.sizeof(lbm._Objective),
             C.sizeof(lbm._View), lbm._View.fov_y.offset, lbm._View.filter.offset, lbm._View.lut.offset,
-            lbm._View.counters_d.offset]
+            lbm._View.counters_d.offset, lbm._Params.site_order.offset]
     assert got == want
 
 
