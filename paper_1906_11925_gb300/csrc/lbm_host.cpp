@@ -46,6 +46,7 @@ struct lbm_ctx {
     double io_normal[LBM_MAX_IOLETS][3] = {};
     bool has_velocity_iolet = false;
     bool has_bfl = false;  // interpolated wall links in the table
+    SideStream side{nullptr, nullptr, nullptr};  // for the launch after the bulk
     float *vel_weight = nullptr;
     double *partials = nullptr, *mass_dev = nullptr;
     int *err_flag = nullptr;
@@ -292,11 +293,12 @@ int cur_layout(const lbm_ctx *c) {
 // One time step of the context's state (pull: two buffers; AA: in place).
 cudaError_t advance_one(lbm_ctx *c, const IoletStep &io, const double *rho_io) {
     cudaError_t e;
+    const SideStream *side = c->side.s ? &c->side : nullptr;
     if (c->streaming == LBM_STREAM_AA) {
-        e = launch_step_aa(c->L, c->f_cur, c->aa_swapped, io, rho_io, c->stream);
+        e = launch_step_aa(c->L, c->f_cur, c->aa_swapped, io, rho_io, c->stream, side);
         if (e == cudaSuccess) c->aa_swapped = !c->aa_swapped;
     } else {
-        e = launch_step(c->L, c->f_cur, c->f_nxt, io, rho_io, c->stream);
+        e = launch_step(c->L, c->f_cur, c->f_nxt, io, rho_io, c->stream, side);
         if (e == cudaSuccess) std::swap(c->f_cur, c->f_nxt);
     }
     return e;
@@ -485,6 +487,9 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->rho_io);
     cudaFree(c->mass_series);
     cudaFree(c->vox);
+    if (c->side.s) cudaStreamDestroy(c->side.s);
+    if (c->side.fork) cudaEventDestroy(c->side.fork);
+    if (c->side.join) cudaEventDestroy(c->side.join);
     delete c;
 }
 
@@ -688,6 +693,12 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.c16_cnt = c->c16_cnt;
     L.bfl = any_bfl ? 1 : 0;
     c->has_bfl = any_bfl;
+    if (n_bulk > 0 && n_bulk < n) {
+        // the launch of the sites after the bulk runs beside the bulk launch
+        CKC(cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking));
+        CKC(cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming));
+    }
     CKC(launch_zero(L, c->f_cur, c->stream));
     if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return

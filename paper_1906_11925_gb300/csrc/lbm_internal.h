@@ -109,13 +109,23 @@ struct DevLattice {
 // One fused pull collide-and-stream step from fin into fout.  The iolet
 // densities come from io, or, when rho_io (device, float64 [n_iolets]) is not
 // null, from rho_io.
+// A second stream on which the small launch of the sites after the bulk runs
+// alongside the bulk launch (the two touch disjoint slots): fork records on
+// the main stream and the side stream waits for it, join records on the side
+// stream and the main stream waits for it.  Null: both launches in order on
+// the main stream.
+struct SideStream {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                        const double *rho_io, cudaStream_t s);
+                        const double *rho_io, cudaStream_t s, const SideStream *side = nullptr);
 
 // One in-place AA-pattern step on the single buffer A: the even kernel
 // (A in natural layout -> swapped) or the odd kernel (swapped -> natural).
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                           const double *rho_io, cudaStream_t s);
+                           const double *rho_io, cudaStream_t s, const SideStream *side = nullptr);
 
 // The bounded mbarrier wait of the staged step on a barrier no copy
 // completes: sets *err when it gives up after limit polls.

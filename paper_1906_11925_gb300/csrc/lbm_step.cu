@@ -604,11 +604,27 @@ k_step_aa_odd_staged(const DevLattice L, typename Raw<HALF>::T *A, int *__restri
     }
 }
 
+// Fork the side stream off s before the bulk launch; returns the stream the
+// launch of the sites after the bulk goes to.
+inline cudaStream_t fork_side(cudaStream_t s, const SideStream *side, bool both) {
+    if (!side || !both) return s;
+    if (cudaEventRecord(side->fork, s) != cudaSuccess) return s;
+    if (cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess) return s;
+    return side->s;
+}
+inline cudaError_t join_side(cudaStream_t s, cudaStream_t t, const SideStream *side) {
+    if (t == s) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(side->join, t);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side->join, 0);
+    return e;
+}
+
 template <int Q, bool HALF>
 cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                         const double *rho_io, cudaStream_t s) {
+                         const double *rho_io, cudaStream_t s, const SideStream *side) {
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
     if (odd) {
         if (nb && HGB_AA_STAGED && L.err) {
             static int grid_cache[2] = {0, 0};
@@ -631,19 +647,22 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
         } else if (nb) {
             k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
         }
-        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io);
     } else {
         if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io);
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = join_side(s, t, side);
+    return e;
 }
 
 template <int Q, bool HALF>
 cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                      const double *rho_io, cudaStream_t s) {
+                      const double *rho_io, cudaStream_t s, const SideStream *side) {
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
     if (nb) {
         if (HGB_STEP_STAGED && L.err) {
             static int grid_cache[2] = {0, 0};
@@ -668,10 +687,12 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
         }
     }
     if (ni && L.bfl)
-        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io);
     else if (ni)
-        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
-    return cudaGetLastError();
+        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = join_side(s, t, side);
+    return e;
 }
 
 }  // namespace
@@ -681,9 +702,9 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
                  : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
 
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                        const double *rho_io, cudaStream_t s) {
+                        const double *rho_io, cudaStream_t s, const SideStream *side) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s);
+    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s, side);
 }
 
 cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
@@ -692,9 +713,9 @@ cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
 }
 
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                           const double *rho_io, cudaStream_t s) {
+                           const double *rho_io, cudaStream_t s, const SideStream *side) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s);
+    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s, side);
 }
 
 }  // namespace hemelb_gb300
