@@ -137,10 +137,27 @@ def _scan_box(lo: Sequence[int], hi: Sequence[int],
     return np.concatenate(out)
 
 
+def _scan_all(scans) -> List[np.ndarray]:
+    """_scan_box over a list of (lo, hi, predicate), on a few threads (the
+    array operations release the interpreter lock); results in list order."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    workers = max(1, min(8, os.cpu_count() or 1, len(scans)))
+    if workers == 1:
+        return [_scan_box(lo, hi, pred) for lo, hi, pred in scans]
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda t: _scan_box(*t), scans))
+
+
 def _finish(name: str, fluid_keys: List[np.ndarray], io_sets: List[np.ndarray],
             periodic=(0, 0, 0), rho_mean=(), amp=None, period=None, phase=None,
             meta=None) -> Geometry:
-    fk = np.unique(np.concatenate(fluid_keys)) if fluid_keys else np.empty(0, np.int64)
+    # distinct fluid keys in ascending order (a sort and a neighbour test: on
+    # tens of millions of keys much faster than np.unique's hashing path)
+    fk = np.sort(np.concatenate(fluid_keys)) if fluid_keys else np.empty(0, np.int64)
+    if fk.shape[0] > 1:
+        fk = fk[np.concatenate(([True], fk[1:] != fk[:-1]))]
     # iolet voxels: drop those that are fluid; a voxel claimed by several
     # iolets goes to the lowest id
     if io_sets:
@@ -354,7 +371,7 @@ def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
     shape = dict(kind="tree", seed=int(seed), generations=int(generations), root_r=float(root_r),
                  length_factor=float(length_factor), box=int(box))
     segs = _tree_layout(shape)
-    fluid_keys = []
+    scans = []  # (lo, hi, predicate) per cylinder and per bifurcation sphere
 
     def clip_lo_hi(lo, hi):
         lo = np.maximum(np.floor(lo), 0).astype(int)
@@ -371,14 +388,16 @@ def vessel_tree(seed: int = 1906, generations: int = 6, root_r: float = 48.0,
             qx, qy, qz = px - s * d[0], py - s * d[1], pz - s * d[2]
             return (s >= 0.0) & (s <= L) & (qx * qx + qy * qy + qz * qz <= r * r)
 
-        fluid_keys.append(_scan_box(lo, hi, cyl))
+        scans.append((lo, hi, cyl))
         if not leaf:
             lo, hi = clip_lo_hi(end - r - 1, end + r + 1)
 
             def sph(X, Y, Z, c=end, r=r):
                 return (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
 
-            fluid_keys.append(_scan_box(lo, hi, sph))
+            scans.append((lo, hi, sph))
+
+    fluid_keys = _scan_all(scans)
 
     def end_disk(c, n, r):
         lo = np.floor(c - r - 3).astype(int)
