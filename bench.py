@@ -41,6 +41,7 @@ from paper_1906_11925_gb300 import replicas  # noqa: E402
 LB_STEPS_PER_BENCH_STEP = 100
 PROFILE_SUMMARY = {"pull": os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md"),
                    "aa": os.path.join(ROOT, "profiles", "k_step_aa_q19_vessel_tree.md")}
+PROFILED_WORKLOAD = "vessel_tree"  # the workload the summaries above were captured on
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_step.cu")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -48,6 +49,9 @@ WORKLOADS = {
     "vessel_tree": dict(q=19, tau=0.6, desc="seeded 6-generation bifurcating vessel tree, "
                         "root r=48, Murray exponent 3, asymmetry U(0.7,1), angles U(25,45) deg, "
                         "branch length 5.5 r, 1024^3 box, 1 inlet rho=1.001 + 32 outlets rho=1.0"),
+    "vessel_tree_large": dict(q=19, tau=0.6, desc="the same seeded vessel tree with every length "
+                              "x1.86 (root r=89.28, branch length 5.5 r), 2048^3 box, ~69.5M fluid "
+                              "sites, 1 inlet rho=1.001 + 32 outlets rho=1.0"),
     "aneurysm": dict(q=15, tau=0.55, desc="quarter-arc tube r=20 on R=150 with fused sphere "
                      "r=40, 256^3 box, pulsatile inlet 1+0.001 sin(2 pi t/4000), outlet 1.0"),
     "tube": dict(q=15, tau=0.8, desc="straight tube r=8, 17x17x64, rho 1.001 -> 0.999"),
@@ -75,7 +79,8 @@ def make_geometry(name: str):
         return G.Geometry(name=str(z["name"]), xyz=z["xyz"], io_xyz=z["io_xyz"], io_id=z["io_id"],
                           periodic=z["periodic"], rho_mean=z["rho_mean"], amp=z["amp"],
                           period=z["period"], phase=z["phase"], meta=meta)
-    g = {"vessel_tree": G.vessel_tree, "aneurysm": G.aneurysm, "tube": G.tube}[name]()
+    g = {"vessel_tree": G.vessel_tree, "aneurysm": G.aneurysm, "tube": G.tube,
+         "vessel_tree_large": lambda: G.vessel_tree(root_r=48.0 * 1.86, box=2048)}[name]()
     try:
         np.savez(cache + ".tmp.npz", name=g.name, xyz=g.xyz, io_xyz=g.io_xyz, io_id=g.io_id,
                  periodic=g.periodic, rho_mean=g.rho_mean, amp=g.amp, period=g.period,
@@ -415,7 +420,7 @@ def run_ours(args):
                     frac=round(achieved / peak, 4), peak_source=peak_kind,
                     bytes_per_site_update=bps, launch_us=round(per_launch_s * 1e6, 2))
 
-    traffic = recorded_traffic(PROFILE_SUMMARY[main_form])
+    traffic = recorded_traffic(PROFILE_SUMMARY[main_form]) if args.workload == PROFILED_WORKLOAD else None
     rf32 = roofline(r32, "fp32", main_form)
     rf32["traffic"] = traffic.get("traffic_bytes_per_launch_fp32") if traffic else None
     if r16:
