@@ -182,8 +182,13 @@ const char *lbm_last_error(const lbm_ctx *ctx);
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 
 /* Advance nsteps >= 0 time steps (Section 2: collision then propagation),
- * one fused pull collide-and-stream kernel launch per step, asynchronous on
- * the context's stream.  Step t uses the iolet densities rho_k(t). */
+ * asynchronous on the context's stream.  Step t uses the iolet densities
+ * rho_k(t).  Each step is one fused collide-and-stream launch over the bulk
+ * sites and one over the sites with iolet links; whole chunks of 32 steps
+ * run as one replay of a CUDA graph of those launches (captured on first
+ * use, bitwise the same results), except while the caller is capturing the
+ * context's stream itself.  The host may wait here for the copy of an
+ * earlier chunk's iolet values when it runs more than 8 chunks ahead. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Advance nsteps steps with iolet densities supplied by the caller instead

@@ -23,6 +23,13 @@
 
 using namespace hemelb_gb300;
 
+// lbm_step's CUDA graphs: steps per captured chunk (even, so a chunk leaves
+// the buffer roles and the AA layout as it found them) and pinned iolet
+// record sets in flight
+constexpr int kGraphSteps = 32;
+constexpr int kGraphRing = 8;
+static_assert(kGraphSteps % 2 == 0, "a chunk must restore the buffer roles");
+
 struct lbm_ctx {
     DevLattice L{};
     int q = 0;
@@ -47,6 +54,24 @@ struct lbm_ctx {
     bool has_velocity_iolet = false;
     bool has_bfl = false;  // interpolated wall links in the table
     SideStream side{nullptr, nullptr, nullptr};  // for the launch after the bulk
+    // lbm_step's CUDA graphs (see run_graph_chunks): one captured chunk of
+    // kGraphSteps steps per starting buffer / AA layout
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        void *f_cur = nullptr;
+        bool swapped = false;
+    };
+    struct Graphs {
+        GraphSlot slot[2];
+        int evict = 0;
+        IoletStep *io_dev = nullptr;  // [kGraphSteps] iolet records read by the replay
+        IoletStep *io_pin = nullptr;  // [kGraphRing][kGraphSteps] pinned host records
+        cudaEvent_t ring_ev[kGraphRing] = {};  // a ring slot's copy has been done
+        int ring_next = 0;
+        cudaStream_t cap = nullptr;   // capture stream
+        bool off = false;             // set up failed or a capture failed: one launch per step
+        bool ready = false;           // a step ran through the launchers (their one-time set-up)
+    } graphs;
     float *vel_weight = nullptr;
     double *partials = nullptr, *mass_dev = nullptr;
     int *err_flag = nullptr;
@@ -290,18 +315,137 @@ int cur_layout(const lbm_ctx *c) {
     return c->aa_swapped ? LAYOUT_AA_SWAPPED : LAYOUT_NATURAL;
 }
 
+// The kinds of the iolets (velocity mask and normals) without their values:
+// the record of the steps whose densities or speeds come from elsewhere.
+IoletStep iolet_kinds(const lbm_ctx *c) {
+    IoletStep s{};
+    for (int k = 0; k < c->n_iolets; ++k)
+        if (c->io_kind[k] == LBM_IOLET_VELOCITY) {
+            s.vel_mask |= 1ull << k;
+            for (int a = 0; a < 3; ++a) s.nrm[k][a] = (float)c->io_normal[k][a];
+        }
+    return s;
+}
+
 // One time step of the context's state (pull: two buffers; AA: in place).
-cudaError_t advance_one(lbm_ctx *c, const IoletStep &io, const double *rho_io) {
+// io_dev (device), when set, holds the step's iolet record in place of io.
+cudaError_t advance_one(lbm_ctx *c, const IoletStep &io, const double *rho_io,
+                        const IoletStep *io_dev = nullptr) {
     cudaError_t e;
     const SideStream *side = c->side.s ? &c->side : nullptr;
     if (c->streaming == LBM_STREAM_AA) {
-        e = launch_step_aa(c->L, c->f_cur, c->aa_swapped, io, rho_io, c->stream, side);
+        e = launch_step_aa(c->L, c->f_cur, c->aa_swapped, io, rho_io, c->stream, side, io_dev);
         if (e == cudaSuccess) c->aa_swapped = !c->aa_swapped;
     } else {
-        e = launch_step(c->L, c->f_cur, c->f_nxt, io, rho_io, c->stream, side);
+        e = launch_step(c->L, c->f_cur, c->f_nxt, io, rho_io, c->stream, side, io_dev);
         if (e == cudaSuccess) std::swap(c->f_cur, c->f_nxt);
     }
     return e;
+}
+
+// ---- CUDA graphs of lbm_step ----------------------------------------------
+// lbm_step runs whole chunks of kGraphSteps steps as one replay of a captured
+// CUDA graph: the same kernels with the same arguments as one launch per
+// step, except that each step reads its iolet record (iolet_step, computed on
+// the host as for a launch) from io_dev, which the host refills, stream-
+// ordered, before every replay from a ring of pinned records.  The chunk is
+// even, so it leaves the buffer roles (pull) and the layout (AA) as it found
+// them; one graph is kept per starting buffer / layout.  On small lattices
+// the per-launch host cost, not the kernels, sets the step rate.
+
+void graphs_reset(lbm_ctx *c) {
+    for (auto &g : c->graphs.slot) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = lbm_ctx::GraphSlot{};
+    }
+}
+
+bool graphs_setup(lbm_ctx *c) {
+    auto &G = c->graphs;
+    if (G.io_dev) return true;
+    cudaError_t e = cudaMalloc((void **)&G.io_dev, sizeof(IoletStep) * kGraphSteps);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&G.io_pin, sizeof(IoletStep) * kGraphSteps * kGraphRing);
+    for (int r = 0; r < kGraphRing && e == cudaSuccess; ++r)
+        e = cudaEventCreateWithFlags(&G.ring_ev[r], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        G.off = true;
+        return false;
+    }
+    return true;
+}
+
+// The graph of one chunk from the current buffer / layout (captured on first
+// use), or null: the caller then launches step by step.
+cudaGraphExec_t graph_for(lbm_ctx *c) {
+    auto &G = c->graphs;
+    for (auto &g : G.slot)
+        if (g.exec && g.f_cur == c->f_cur && g.swapped == c->aa_swapped) return g.exec;
+    if (!graphs_setup(c)) return nullptr;
+    void *cur = c->f_cur, *nxt = c->f_nxt;
+    const bool sw = c->aa_swapped;
+    const cudaStream_t user = c->stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    c->stream = G.cap;
+    cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const IoletStep none{};
+        for (int j = 0; j < kGraphSteps && e == cudaSuccess; ++j) e = advance_one(c, none, nullptr, G.io_dev + j);
+        const cudaError_t e2 = cudaStreamEndCapture(G.cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    c->f_cur = cur;
+    c->f_nxt = nxt;
+    c->aa_swapped = sw;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0ULL);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        G.off = true;
+        return nullptr;
+    }
+    auto &g = G.slot[G.evict];
+    G.evict ^= 1;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = exec;
+    g.f_cur = cur;
+    g.swapped = sw;
+    return exec;
+}
+
+// Whole chunks of the next `steps` steps as graph replays; returns the number
+// of steps done (a multiple of kGraphSteps, 0 when graphs are not in use).
+cudaError_t run_graph_chunks(lbm_ctx *c, int64_t steps, int64_t *done) {
+    *done = 0;
+    auto &G = c->graphs;
+    if (G.off || !G.ready || c->n == 0 || steps < kGraphSteps) return cudaSuccess;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return cudaSuccess;  // the caller is capturing this stream itself
+    }
+    while (steps - *done >= kGraphSteps) {
+        const cudaGraphExec_t exec = graph_for(c);
+        if (!exec) return cudaSuccess;
+        const int r = G.ring_next;
+        G.ring_next = (r + 1) % kGraphRing;
+        cudaError_t e = cudaEventSynchronize(G.ring_ev[r]);  // the ring slot's last copy is done
+        if (e != cudaSuccess) return e;
+        IoletStep *h = G.io_pin + (size_t)r * kGraphSteps;
+        for (int j = 0; j < kGraphSteps; ++j) h[j] = iolet_step(c, c->t + j);
+        e = cudaMemcpyAsync(G.io_dev, h, sizeof(IoletStep) * kGraphSteps, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(G.ring_ev[r], c->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, c->stream);
+        if (e != cudaSuccess) return e;
+        c->t += kGraphSteps;
+        *done += kGraphSteps;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -490,6 +634,12 @@ void free_ctx(lbm_ctx *c) {
     if (c->side.s) cudaStreamDestroy(c->side.s);
     if (c->side.fork) cudaEventDestroy(c->side.fork);
     if (c->side.join) cudaEventDestroy(c->side.join);
+    graphs_reset(c);
+    cudaFree(c->graphs.io_dev);
+    if (c->graphs.io_pin) cudaFreeHost(c->graphs.io_pin);
+    for (cudaEvent_t ev : c->graphs.ring_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->graphs.cap) cudaStreamDestroy(c->graphs.cap);
     delete c;
 }
 
@@ -747,7 +897,18 @@ HGB_API lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
-    for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t s = 0;
+    if (nsteps > 0 && !ctx->graphs.ready) {
+        // the first step goes through the launchers directly (their one-time
+        // set-up must not happen inside a capture)
+        CK(ctx, advance_one(ctx, iolet_step(ctx, ctx->t), nullptr));
+        ++ctx->t;
+        ctx->graphs.ready = true;
+        s = 1;
+    }
+    int64_t done = 0;
+    CK(ctx, run_graph_chunks(ctx, nsteps - s, &done));
+    for (s += done; s < nsteps; ++s) {
         CK(ctx, advance_one(ctx, iolet_step(ctx, ctx->t), nullptr));
         ++ctx->t;
     }
@@ -779,8 +940,9 @@ HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *r
     if (K > 0)
         CK(ctx, cudaMemcpyAsync(ctx->rho_io, rho_io_host, (size_t)nsteps * K * 8,
                                 cudaMemcpyHostToDevice, ctx->stream));
+    const IoletStep kinds = iolet_kinds(ctx);  // velocity iolets take the driven values as speeds
     for (int64_t s = 0; s < nsteps; ++s) {
-        CK(ctx, advance_one(ctx, IoletStep{}, ctx->rho_io + s * K));
+        CK(ctx, advance_one(ctx, kinds, ctx->rho_io + s * K));
         ++ctx->t;
         if (mass_host)
             CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_series + s, ctx->stream));
@@ -1131,6 +1293,7 @@ HGB_API lbm_status lbm_set_tau(lbm_ctx *ctx, double tau) {
     ctx->tau = tau;
     ctx->L.omega = (float)(1.0 / tau);
     ctx->L.tau = (float)tau;
+    graphs_reset(ctx);  // the captured launches hold the old value
     return LBM_OK;
 }
 

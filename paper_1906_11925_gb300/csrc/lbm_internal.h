@@ -119,13 +119,17 @@ struct SideStream {
     cudaEvent_t fork, join;
 };
 
+// io_dev (device, one IoletStep), when not null, replaces io: the steps of a
+// CUDA graph read their iolet values from memory the host refills per replay.
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                        const double *rho_io, cudaStream_t s, const SideStream *side = nullptr);
+                        const double *rho_io, cudaStream_t s, const SideStream *side = nullptr,
+                        const IoletStep *io_dev = nullptr);
 
 // One in-place AA-pattern step on the single buffer A: the even kernel
 // (A in natural layout -> swapped) or the odd kernel (swapped -> natural).
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                           const double *rho_io, cudaStream_t s, const SideStream *side = nullptr);
+                           const double *rho_io, cudaStream_t s, const SideStream *side = nullptr,
+                           const IoletStep *io_dev = nullptr);
 
 // The bounded mbarrier wait of the staged step on a barrier no copy
 // completes: sets *err when it gives up after limit polls.

@@ -147,7 +147,11 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
 template <int Q, bool HALF>
 __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const int (&s)[Q],
                                                const Velocity &v, const IoletStep &io,
-                                               const double *__restrict__ rho_io, float (&out)[Q]) {
+                                               const double *__restrict__ rho_io,
+                                               const IoletStep *__restrict__ io_dev, float (&out)[Q]) {
+    // the step's iolet values: io (a kernel parameter), or the same record in
+    // device memory when io_dev is set (the steps of a CUDA graph)
+    const unsigned long long vel_mask = io_dev ? io_dev->vel_mask : io.vel_mask;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (s[i] <= -2 && !is_bfl(s[i])) {
@@ -157,15 +161,18 @@ __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const
                 const double r = rho_io[k];
                 drk = (float)(r - (double)L.rho0);
                 rk = (float)r;
+            } else if (io_dev) {
+                drk = io_dev->drho[k];
+                rk = io_dev->rho[k];
             } else {
                 drk = io.drho[k];
                 rk = io.rho[k];
             }
-            if ((io.vel_mask >> k) & 1ull) {
+            if ((vel_mask >> k) & 1ull) {
                 // rk is the speed U_k(t)
+                const float *nk = io_dev ? io_dev->nrm[k] : io.nrm[k];
                 const float wu = L.vel_weight[x - L.n_bulk] * rk;
-                const float cn = cdir<Q>(i, 0) * io.nrm[k][0] + cdir<Q>(i, 1) * io.nrm[k][1] +
-                                 cdir<Q>(i, 2) * io.nrm[k][2];
+                const float cn = cdir<Q>(i, 0) * nk[0] + cdir<Q>(i, 1) * nk[1] + cdir<Q>(i, 2) * nk[2];
                 out[opp(i)] += 6.0f * (float)wdir<Q>(i) * v.rs * wu * cn;
                 continue;
             }
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(kBlock, IO ? (HALF ? HGB_TAIL_MINB_FP16 : HGB_
                                              : (HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32))
 k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
        typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
-       const double *__restrict__ rho_io) {
+       const double *__restrict__ rho_io, const IoletStep *__restrict__ io_dev) {
     using R = Raw<HALF>;
     const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
     if (x >= (IO ? L.n : L.n_bulk)) return;
@@ -271,7 +278,7 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
     float out[Q];
     const Velocity v = collide<Q, HALF>(L, d, out);
     if (BFL) bfl_scatter<Q>(s, out);
-    if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
+    if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
 }
@@ -480,7 +487,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 template <int Q, bool HALF, bool ODD, bool IO>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
 k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const IoletStep io,
-          const double *__restrict__ rho_io) {
+          const double *__restrict__ rho_io, const IoletStep *__restrict__ io_dev) {
     using R = Raw<HALF>;
     const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
     if (x >= (IO ? L.n : L.n_bulk)) return;
@@ -499,7 +506,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
         const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
+        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
     } else {
@@ -511,7 +518,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
         const Velocity v = collide<Q, HALF>(L, d, out);
-        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, out);
+        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
     }
@@ -621,7 +628,8 @@ inline cudaError_t join_side(cudaStream_t s, cudaStream_t t, const SideStream *s
 
 template <int Q, bool HALF>
 cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                         const double *rho_io, cudaStream_t s, const SideStream *side) {
+                         const double *rho_io, cudaStream_t s, const SideStream *side,
+                         const IoletStep *io_dev) {
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
@@ -645,12 +653,12 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
             const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
             k_step_aa_odd_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (T *)A, L.err);
         } else if (nb) {
-            k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
+            k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
         }
-        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io);
+        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io, io_dev);
     } else {
-        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io);
-        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io);
+        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
+        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io, io_dev);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = join_side(s, t, side);
@@ -659,7 +667,8 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
 
 template <int Q, bool HALF>
 cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                      const double *rho_io, cudaStream_t s, const SideStream *side) {
+                      const double *rho_io, cudaStream_t s, const SideStream *side,
+                      const IoletStep *io_dev) {
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
@@ -683,13 +692,13 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
             const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
             k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, (T *)fout, L.err);
         } else {
-            k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+            k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
         }
     }
     if (ni && L.bfl)
-        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
     else if (ni)
-        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io);
+        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = join_side(s, t, side);
     return e;
@@ -702,9 +711,10 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
                  : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
 
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
-                        const double *rho_io, cudaStream_t s, const SideStream *side) {
+                        const double *rho_io, cudaStream_t s, const SideStream *side,
+                        const IoletStep *io_dev) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s, side);
+    return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s, side, io_dev);
 }
 
 cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
@@ -713,9 +723,10 @@ cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
 }
 
 cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletStep &io,
-                           const double *rho_io, cudaStream_t s, const SideStream *side) {
+                           const double *rho_io, cudaStream_t s, const SideStream *side,
+                           const IoletStep *io_dev) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s, side);
+    return HGB_DISPATCH(L, step_aa_impl, L, A, odd, io, rho_io, s, side, io_dev);
 }
 
 }  // namespace hemelb_gb300
