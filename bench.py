@@ -44,6 +44,7 @@ PROFILE_SUMMARY = {"pull": os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_t
 PROFILED_WORKLOAD = "vessel_tree"  # the workload the summaries above were captured on
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_step.cu")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # HBM3e data-sheet figure, for context beside the measured peak
 
 WORKLOADS = {
     "vessel_tree": dict(q=19, tau=0.6, desc="seeded 6-generation bifurcating vessel tree, "
@@ -418,6 +419,8 @@ def run_ours(args):
         achieved = bps * g.n / per_launch_s / 1e9
         return dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
                     frac=round(achieved / peak, 4), peak_source=peak_kind,
+                    frac_of_nominal=round(achieved / NOMINAL_HBM_GBS, 4),
+                    nominal_peak=NOMINAL_HBM_GBS,
                     bytes_per_site_update=bps, launch_us=round(per_launch_s * 1e6, 2))
 
     traffic = recorded_traffic(PROFILE_SUMMARY[main_form]) if args.workload == PROFILED_WORKLOAD else None
