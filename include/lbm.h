@@ -236,6 +236,28 @@ lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, 
  * paper has no counterpart. */
 lbm_status lbm_check_wait_timeout(uint32_t limit, void *cuda_stream, int32_t *gave_up);
 
+/* Failure detection: an instability check on the stored state.  With
+ * every > 0, lbm_step checks the state after every `every` of its steps and
+ * after its last one: a stored value that is not finite, or a site whose own
+ * stored slots give a density <= 0 or a speed |j| / rho above u_max (lattice
+ * units; the collision keeps rho and j, so these are the moments of the
+ * site's last post-collision state, approximately so at iolet and
+ * interpolated-wall sites), is reported as LBM_ERR_UNSTABLE with the step
+ * range of the first failing check; lbm_step then waits for its stream
+ * before returning.  every = 0 (the default) turns the check off and leaves
+ * lbm_step asynchronous.  every < 0 or u_max not finite and > 0: LBM_ERR_ARG.
+ * The paper has no counterpart (its GUI can only interrupt a run). */
+lbm_status lbm_set_stability_check(lbm_ctx *ctx, int64_t every, double u_max);
+
+/* Guard words (an out-of-range write check in place of a memory sanitizer):
+ * the padding slots [n, npad) of every plane of the context's population
+ * buffers and one extra row of 128 slots after the last plane hold a fixed
+ * NaN bit pattern that no kernel writes.  Stores 1 in *intact when every
+ * guard word still holds it, else 0.  The raw state blob of lbm_get_state
+ * includes the plane padding, so lbm_set_state of a blob whose padding was
+ * changed shows here.  Synchronous. */
+lbm_status lbm_check_guards(lbm_ctx *ctx, int32_t *intact);
+
 /* Populations f(t) as float64 [q][n], caller order (host memory).  Sync. */
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
 
@@ -257,7 +279,10 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
 lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host);
 
 /* Replace the state by f (float64 [q][n], caller order, host memory),
- * rounded to the storage format.  Does not change t.  Synchronous. */
+ * rounded to the storage format.  Does not change t.  A value that is not
+ * finite, or whose deviation f_i - w_i rho0 does not fit the storage format
+ * (|deviation| * 2^S > 65504 for fp16), gives LBM_ERR_UNSTABLE and leaves
+ * the state unchanged.  Synchronous. */
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host);
 
 /* Raw stored state (checkpoint/resume): lbm_state_bytes gives the size of

@@ -5,6 +5,8 @@
 // every per-step operation is a kernel launch on the context's stream.
 #include <algorithm>
 #include <atomic>
+#include <climits>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -54,6 +56,9 @@ struct lbm_ctx {
     bool has_velocity_iolet = false;
     bool has_bfl = false;  // interpolated wall links in the table
     SideStream side{nullptr, nullptr, nullptr};  // for the launch after the bulk
+    int *flags = nullptr;        // device: [0] instability check, [1] guard check
+    int64_t check_every = 0;     // lbm_set_stability_check (0: off)
+    double check_umax = 0.3;
     // lbm_step's CUDA graphs (see run_graph_chunks): one captured chunk of
     // kGraphSteps steps per starting buffer / AA layout
     struct GraphSlot {
@@ -631,6 +636,7 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->rho_io);
     cudaFree(c->mass_series);
     cudaFree(c->vox);
+    cudaFree(c->flags);
     if (c->side.s) cudaStreamDestroy(c->side.s);
     if (c->side.fork) cudaEventDestroy(c->side.fork);
     if (c->side.join) cudaEventDestroy(c->side.join);
@@ -686,7 +692,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     const size_t eb = elem_bytes(p->storage);
     const size_t nbuf = p->streaming == LBM_STREAM_AA ? 1 : 2;
-    const size_t need = nbuf * (size_t)q * npad * eb + (size_t)(q - 1) * npad * 4 + (size_t)n * 4 +
+    const size_t need = nbuf * ((size_t)q * npad + (size_t)kGuardSlots) * eb + (size_t)(q - 1) * npad * 4 +
+                        (size_t)n * 4 +
                         (kUseCompressedTable ? ((size_t)npad / kTile + 1) * (size_t)tile_record_bytes(q) +
                                                    (size_t)npad * 8
                                              : 0) +
@@ -787,8 +794,9 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             return s_;                              \
         }                                           \
     } while (0)
-    const size_t fbytes = (size_t)q * npad * eb;
+    const size_t fbytes = ((size_t)q * npad + (size_t)kGuardSlots) * eb;  // planes + guard row
     CKC(dmalloc(c, &c->f_cur, fbytes));
+    CKC(dmalloc(c, &c->flags, 16));
     if (c->streaming == LBM_STREAM_PULL) CKC(dmalloc(c, &c->f_nxt, fbytes));
     CKC(dmalloc(c, &c->tab, tab.size() * 4));
     CKC(dmalloc(c, &c->perm, (size_t)n * 4));
@@ -851,6 +859,9 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     }
     CKC(launch_zero(L, c->f_cur, c->stream));
     if (c->f_nxt) CKC(launch_zero(L, c->f_nxt, c->stream));
+    CKC(launch_guards(L, c->f_cur, false, nullptr, c->stream));
+    if (c->f_nxt) CKC(launch_guards(L, c->f_nxt, false, nullptr, c->stream));
+    CKC(cudaMemsetAsync(c->flags, 0, 16, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
 #undef CKC
     c->perm_host.swap(perm);
@@ -894,9 +905,9 @@ HGB_API lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
     return LBM_OK;
 }
 
-HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
-    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
-    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+namespace {
+// nsteps steps: whole graph chunks, then one launch per step
+lbm_status run_steps(lbm_ctx *ctx, int64_t nsteps) {
     int64_t s = 0;
     if (nsteps > 0 && !ctx->graphs.ready) {
         // the first step goes through the launchers directly (their one-time
@@ -912,6 +923,63 @@ HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
         CK(ctx, advance_one(ctx, iolet_step(ctx, ctx->t), nullptr));
         ++ctx->t;
     }
+    return LBM_OK;
+}
+}  // namespace
+
+HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    const int64_t every = ctx->check_every;
+    if (every <= 0 || nsteps == 0) return run_steps(ctx, nsteps);
+    // checked: a check after every `every` steps and after the last; check j
+    // (1-based) covers the steps up to t0 + min(j every, nsteps)
+    const int64_t t0 = ctx->t;
+    CK(ctx, cudaMemsetAsync(ctx->flags, 0, 4, ctx->stream));
+    int64_t done = 0, j = 0;
+    while (done < nsteps) {
+        const int64_t m = std::min(every, nsteps - done);
+        const lbm_status st = run_steps(ctx, m);
+        if (st != LBM_OK) return st;
+        done += m;
+        ++j;
+        const int tag = (int)std::min<int64_t>(j, INT32_MAX);
+        CK(ctx, launch_stability(ctx->L, ctx->f_cur, (float)ctx->check_umax, tag, ctx->flags, ctx->stream));
+    }
+    int h = 0;
+    CK(ctx, cudaMemcpyAsync(&h, ctx->flags, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h > 0) {
+        const int64_t lo = t0 + std::min((int64_t)(h - 1) * every, nsteps);
+        const int64_t hi = h == INT32_MAX ? t0 + nsteps : t0 + std::min((int64_t)h * every, nsteps);
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "unstable: a stored value is not finite, or rho <= 0 or |u| > %g at a site, after the "
+                 "steps of times %lld .. %lld",
+                 ctx->check_umax, (long long)lo, (long long)(hi - 1));
+        return fail(ctx, LBM_ERR_UNSTABLE, msg);
+    }
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_set_stability_check(lbm_ctx *ctx, int64_t every, double u_max) {
+    if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (every < 0) return fail(ctx, LBM_ERR_ARG, "every < 0");
+    if (!(u_max > 0) || !std::isfinite(u_max)) return fail(ctx, LBM_ERR_ARG, "u_max must be finite and > 0");
+    ctx->check_every = every;
+    ctx->check_umax = u_max;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_check_guards(lbm_ctx *ctx, int32_t *intact) {
+    if (!ctx || !intact) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+    CK(ctx, cudaMemsetAsync(ctx->flags + 1, 0, 4, ctx->stream));
+    CK(ctx, launch_guards(ctx->L, ctx->f_cur, true, ctx->flags + 1, ctx->stream));
+    if (ctx->f_nxt) CK(ctx, launch_guards(ctx->L, ctx->f_nxt, true, ctx->flags + 1, ctx->stream));
+    int h = 0;
+    CK(ctx, cudaMemcpyAsync(&h, ctx->flags + 1, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *intact = h == 0 ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1033,6 +1101,21 @@ HGB_API lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host) {
 HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
     if (!ctx || (!f_host && ctx->n)) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     if (ctx->n == 0) return LBM_OK;
+    {
+        // every value finite and its deviation representable in the storage
+        const double lim = ctx->storage ? 65504.0 / std::ldexp(1.0, ctx->scale_log2) : 3.4028234663852886e38;
+        for (int i = 0; i < ctx->q; ++i) {
+            const double w = wdir_q(ctx->q, i) * ctx->rho0;
+            const double *row = f_host + (size_t)i * ctx->n;
+            for (int64_t x = 0; x < ctx->n; ++x)
+                if (!(std::fabs(row[x] - w) <= lim)) {
+                    char msg[160];
+                    snprintf(msg, sizeof msg, "population %d of site %lld is %g: not finite or out of the "
+                             "storage range", i, (long long)x, row[x]);
+                    return fail(ctx, LBM_ERR_UNSTABLE, msg);
+                }
+        }
+    }
     const size_t bytes = (size_t)ctx->q * ctx->n * 8;
     double *tmp = nullptr;
     CK(ctx, cudaMalloc((void **)&tmp, bytes));

@@ -106,6 +106,19 @@ struct DevLattice {
     int bfl;                      // the table holds interpolated wall links
 };
 
+// Slots after the last plane of a population buffer that hold guard words
+// (the plane padding [n, npad) holds them too).
+constexpr int64_t kGuardSlots = 128;
+
+// Instability check of the stored state f (any layout): on a non-finite
+// slot, rho <= 0 or |u| > u_max at a site, stores tag in *flag if *flag is 0.
+cudaError_t launch_stability(const DevLattice &L, const void *f, float u_max, int tag, int *flag,
+                             cudaStream_t s);
+
+// Write (check = false) or compare (check = true; mismatch: *flag = 1) the
+// guard words of the population buffer f.
+cudaError_t launch_guards(const DevLattice &L, void *f, bool check, int *flag, cudaStream_t s);
+
 // One fused pull collide-and-stream step from fin into fout.  The iolet
 // densities come from io, or, when rho_io (device, float64 [n_iolets]) is not
 // null, from rho_io.

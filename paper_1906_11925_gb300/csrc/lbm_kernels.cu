@@ -530,6 +530,81 @@ cudaError_t launch_scatter_f64(const DevLattice &L, const double *in, int layout
     return HGB_DISPATCH(L, scatter_impl, L, in, layout, f, s);
 }
 
+namespace {
+// Instability check of a stored state (no table): every slot finite, and the
+// moments of each site's own slots give rho > 0 and |j|^2 <= u_max^2 rho^2.
+// A failing block writes `tag` into *flag if it is still 0, so the flag
+// keeps the first failing check of a series.
+template <int Q, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+k_stability(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, float u_max2, int tag,
+            int *__restrict__ flag) {
+    using S = Store<HALF>;
+    const int x = blockIdx.x * kBlock + threadIdx.x;
+    bool bad = false;
+    if (x < L.n) {
+        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float d = S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
+            finite = finite && isfinite(d);
+            drho += d;
+            if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * d;
+            if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * d;
+            if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * d;
+        }
+        const float rho = L.rho0 + drho;
+        bad = !finite || !(rho > 0.f) || !(jx * jx + jy * jy + jz * jz <= u_max2 * rho * rho);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(flag, 0, tag);
+}
+
+// Guard words: the padding slots [n, npad) of every plane and `extra` slots
+// after the last plane, set to (fill) or compared with (check) a NaN bit
+// pattern; a mismatch sets *flag.
+template <typename W>
+__global__ void __launch_bounds__(kBlock)
+k_guards(W *__restrict__ f, int q, int64_t n, int64_t npad, int64_t extra, W pattern, int check,
+         int *__restrict__ flag) {
+    const int64_t pad = npad - n;
+    const int64_t total = (int64_t)q * pad + extra;
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kBlock) {
+        const int64_t off = e < (int64_t)q * pad ? (e / pad) * npad + n + e % pad : (int64_t)q * npad + (e - (int64_t)q * pad);
+        if (check) bad = bad || f[off] != pattern;
+        else f[off] = pattern;
+    }
+    if (check && __syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+template <int Q, bool HALF>
+cudaError_t stability_impl(const DevLattice &L, const void *f, float u_max2, int tag, int *flag,
+                           cudaStream_t s) {
+    k_stability<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const typename Store<HALF>::T *)f, u_max2, tag,
+                                                          flag);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_stability(const DevLattice &L, const void *f, float u_max, int tag, int *flag,
+                             cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, stability_impl, L, f, u_max * u_max, tag, flag, s);
+}
+
+cudaError_t launch_guards(const DevLattice &L, void *f, bool check, int *flag, cudaStream_t s) {
+    const int64_t total = (int64_t)L.q * (L.npad - L.n) + kGuardSlots;
+    const unsigned g = (unsigned)std::min<int64_t>((total + kBlock - 1) / kBlock, 4 * 152);
+    if (L.storage)
+        k_guards<unsigned short><<<g, kBlock, 0, s>>>((unsigned short *)f, L.q, L.n, L.npad, kGuardSlots,
+                                                      (unsigned short)0x7DA5u, check ? 1 : 0, flag);
+    else
+        k_guards<unsigned><<<g, kBlock, 0, s>>>((unsigned *)f, L.q, L.n, L.npad, kGuardSlots, 0x7FA5A5A5u,
+                                                check ? 1 : 0, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_zero(const DevLattice &L, void *f, cudaStream_t s) {
     const size_t elem = L.storage ? 2 : 4;
     return cudaMemsetAsync(f, 0, elem * (size_t)L.q * (size_t)L.npad, s);

@@ -33,7 +33,7 @@ _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM"
 EXPORTED = (
     "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
     "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
-    "lbm_weighted_sum", "lbm_check_wait_timeout",
+    "lbm_weighted_sum", "lbm_check_wait_timeout", "lbm_set_stability_check", "lbm_check_guards",
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
     "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_get_links", "lbm_info",
@@ -128,6 +128,8 @@ def load_library(build_if_missing: bool = True):
         "lbm_mass": [P, P],
         "lbm_weighted_sum": [P, i32, P, P],
         "lbm_check_wait_timeout": [C.c_uint32, P, P],
+        "lbm_set_stability_check": [P, i64, C.c_double],
+        "lbm_check_guards": [P, P],
         "lbm_get_populations": [P, P],
         "lbm_get_populations_noalloc": [P, P],
         "lbm_set_populations": [P, P],
@@ -391,6 +393,19 @@ class Lattice:
         link = np.empty((self.q, self.n), np.uint8)
         self._ck(self._lib.lbm_get_links(self._ctx, _p(nbr), _p(link)))
         return nbr, link
+
+    def set_stability_check(self, every: int, u_max: float = 0.3):
+        """From now on lbm_step checks the state after every `every` steps (and
+        after its last): LbmError LBM_ERR_UNSTABLE on a non-finite value or
+        a site with rho <= 0 or |u| > u_max.  every = 0 turns it off."""
+        self._ck(self._lib.lbm_set_stability_check(self._ctx, int(every), float(u_max)))
+
+    def check_guards(self) -> bool:
+        """True when every guard word after the planes of the population
+        buffers is intact (no kernel wrote out of range)."""
+        v = C.c_int32(0)
+        self._ck(self._lib.lbm_check_guards(self._ctx, C.byref(v)))
+        return bool(v.value)
 
     def set_tau(self, tau: float):
         self._ck(self._lib.lbm_set_tau(self._ctx, float(tau)))

@@ -136,4 +136,5 @@ def test_aa_uses_one_population_buffer():
     A, _, _ = make(g, 19, 0.7, FP32, AA)
     P, _, _ = make(g, 19, 0.7, FP32, PULL)
     ia, ip = A.info(), P.info()
-    assert ip["device_bytes"] - ia["device_bytes"] == 19 * ip["npad"] * 4
+    # one buffer of 19 planes plus its 128 guard slots
+    assert ip["device_bytes"] - ia["device_bytes"] == (19 * ip["npad"] + 128) * 4

@@ -209,12 +209,20 @@ def test_set_get_round_trip():
 
 
 def test_non_finite_state_is_reported():
+    """A NaN input is refused by lbm_set_populations; one that reaches the
+    stored state (a raw blob) makes lbm_mass report the instability."""
     g = G.tube(radius=3, length=6, nx=7, ny=7)
     q = 15
     L, _, _ = make(g, q, 0.8)
     f = oracle.rest_state(q, g.n)
     f[3, 5] = np.nan
-    L.set_populations(f)
+    with pytest.raises(lbm.LbmError) as ei:
+        L.set_populations(f)
+    assert ei.value.name == "LBM_ERR_UNSTABLE"
+    blob = L.get_state().copy()
+    npad = (blob.nbytes - 8) // (q * 4)
+    blob[(3 * npad + 5) * 4:(3 * npad + 6) * 4] = np.array([np.nan], np.float32).view(np.uint8)
+    L.set_state(blob)
     L.step(2)
     with pytest.raises(lbm.LbmError) as ei:
         L.mass()
