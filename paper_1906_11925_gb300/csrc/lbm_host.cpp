@@ -16,12 +16,24 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
 #include "lattice.h"
 #include "lbm_internal.h"
 
 #define HGB_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+// NVTX range over one ABI call (visible to profilers that record NVTX, e.g.
+// ncu --nvtx --nvtx-include); header-only NVTX, free when no tool is attached
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 using namespace hemelb_gb300;
 
@@ -661,6 +673,7 @@ cudaError_t dmalloc(lbm_ctx *c, T **p, size_t bytes) {
 HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, const int32_t *xyz,
                               const int32_t *nbr, const uint8_t *link, void *cuda_stream) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    const Range range("lbm_create");
     *out = nullptr;
     lbm_status st = validate_params(p);
     if (st != LBM_OK) return st;
@@ -928,6 +941,7 @@ lbm_status run_steps(lbm_ctx *ctx, int64_t nsteps) {
 }  // namespace
 
 HGB_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
+    const Range range("lbm_step");
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     const int64_t every = ctx->check_every;
@@ -985,6 +999,7 @@ HGB_API lbm_status lbm_check_guards(lbm_ctx *ctx, int32_t *intact) {
 
 HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *rho_io_host,
                                    double *mass_host) {
+    const Range range("lbm_step_driven");
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return LBM_OK;
@@ -1039,6 +1054,7 @@ HGB_API lbm_status lbm_set_time(lbm_ctx *ctx, int64_t t) {
 }
 
 HGB_API lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d) {
+    const Range range("lbm_macros");
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     CK(ctx, launch_macros(ctx->L, ctx->f_cur, cur_layout(ctx), rho_d, u_d, wss_d, ctx->stream));
     return LBM_OK;
@@ -1411,6 +1427,7 @@ HGB_API lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *
 HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, int64_t nsteps,
                                       int32_t n_snap, double *J, double *dJ_dtau, double *dJ_dmean,
                                       double *dJ_damp, double *dJ_dphase, double *dJ_df0) {
+    const Range range("lbm_objective_grad");
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (!obj || (obj->kind != LBM_OBJ_WSS && obj->kind != LBM_OBJ_DENSITY))
         return fail(ctx, LBM_ERR_ARG, "objective kind must be LBM_OBJ_WSS or LBM_OBJ_DENSITY");
@@ -1710,6 +1727,7 @@ HGB_API lbm_status lbm_lattice_box(const lbm_ctx *ctx, int32_t *lo, int32_t *dim
 
 HGB_API lbm_status lbm_volume_from_lattice(lbm_volume *vol, lbm_ctx *ctx, int32_t quantity,
                                            const int32_t *origin) {
+    const Range range("lbm_volume_from_lattice");
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (!vol || !origin) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     if (quantity < LBM_QTY_DENSITY || quantity > LBM_QTY_WSS)
@@ -1747,6 +1765,7 @@ HGB_API lbm_status lbm_volume_from_lattice(lbm_volume *vol, lbm_ctx *ctx, int32_
 
 HGB_API lbm_status lbm_render(const lbm_volume *vol, const lbm_view *view, float *rgba_d,
                               void *cuda_stream) {
+    const Range range("lbm_render");
     if (!vol || !view || !rgba_d) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
     if (((uintptr_t)rgba_d & 15) != 0) return fail(nullptr, LBM_ERR_ARG, "rgba_d must be 16-byte aligned");
     const lbm_view &w = *view;
