@@ -18,6 +18,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhemelb_gb300.so")
+# the same library with range-checked table loads in the step kernels
+# (HGB_CHECK_TABLE=1); loaded instead of LIB when HEMELB_GB300_CHECKED=1
+CHECKED_LIB = os.path.join(BUILD, "libhemelb_gb300_checked.so")
+CHECKED_SOURCE = "lbm_step.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,9 +42,9 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(CHECKED_LIB):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(CHECKED_LIB))
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
@@ -53,6 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
               "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH
     procs = []
     objs = []
+    checked_objs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
@@ -61,6 +66,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd += ["-Xptxas", "-v"]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
                                             text=True)))
+        if os.path.basename(src) == CHECKED_SOURCE:
+            cobj = os.path.join(BUILD, os.path.basename(src) + ".checked.o")
+            checked_objs.append(cobj)
+            ccmd = [nvcc, "-c", src, "-o", cobj, "-DHGB_CHECK_TABLE=1"] + common
+            procs.append((src + " (checked)", subprocess.Popen(ccmd, stdout=subprocess.PIPE,
+                                                               stderr=subprocess.STDOUT, text=True)))
+        else:
+            checked_objs.append(obj)
     logs = []
     failed = []
     for src, p in procs:
@@ -73,13 +86,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         sys.stderr.write("\n".join(logs))
         raise RuntimeError("nvcc failed for %s" % ", ".join(os.path.basename(f) for f in failed))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fopenmp"]
-    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout)
-        raise RuntimeError("linking libhemelb_gb300.so failed")
-    os.replace(tmp, LIB)
+    for lib, lib_objs in ((CHECKED_LIB, checked_objs), (LIB, objs)):
+        tmp = lib + ".tmp"
+        cmd = [nvcc, "-shared", "-o", tmp] + lib_objs + ARCH + ["-Xcompiler", "-fopenmp"]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout)
+            raise RuntimeError("linking %s failed" % os.path.basename(lib))
+        os.replace(tmp, lib)
     if verbose:
         print("\n".join(logs))
     return LIB

@@ -1067,6 +1067,7 @@ HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(&flag, ctx->err_flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag == 2) return fail(ctx, LBM_ERR_CUDA, "a step kernel read a table entry out of range (checked build)");
     if (flag) return fail(ctx, LBM_ERR_CUDA, "a step kernel gave up waiting for its table copies");
     if (!std::isfinite(*out)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite mass");
     return LBM_OK;

@@ -22,6 +22,7 @@
 // (or staged in shared memory by bulk asynchronous copies); the q population
 // reads are gathers through the read-only path, made local by the Morton
 // order; the q stores are coalesced and streamed.
+#include <climits>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -86,6 +87,23 @@ struct Raw<true> {
         __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
     }
 };
+
+// Checked builds (HGB_CHECK_TABLE=1, libhemelb_gb300_checked.so): every table
+// entry a step kernel loads is range-checked.  An entry that is none of a
+// site index in [0, n), -1 (wall), -2 - k for an iolet k of the lattice or an
+// interpolated-wall code sets *L.err = 2 (lbm_mass reports it) and is read as
+// a wall link, so that no access leaves the buffers.  No trap.
+#ifndef HGB_CHECK_TABLE
+#define HGB_CHECK_TABLE 0
+#endif
+__device__ __forceinline__ int checked_entry(const DevLattice &L, int e) {
+    if (!HGB_CHECK_TABLE) return e;
+    const bool ok = (e >= 0 && e < L.n) || e == -1 || (e <= -2 && e >= -1 - L.n_iolets) ||
+                    (is_bfl(e) && e != INT_MIN);
+    if (ok) return e;
+    atomicExch(L.err, 2);
+    return -1;
+}
 
 // Velocity moments of one site after its collision (for the iolet values).
 struct Velocity {
@@ -265,7 +283,7 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
     const unsigned np = (unsigned)L.npad;
     int s[Q];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
     float d[Q];
     d[0] = R::ld(fin + x);
 #pragma unroll
@@ -444,6 +462,10 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
             for (int i = 1; i < Q; ++i) s[i] = r32[(i - 1) * kTile + tid];
         }
         if (x < L.n_bulk) {
+            // (the rows of a ragged last tile run past n_bulk: only the
+            // entries of the tile's sites are checked)
+#pragma unroll
+            for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, s[i]);
             float d[Q];
             d[0] = R::ld(fin + x);
 #pragma unroll
@@ -496,7 +518,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
     s[0] = 0;
     if (ODD || IO) {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) s[i] = __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+        for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
     }
     float d[Q];
     float out[Q];

@@ -107,7 +107,8 @@ def load_library(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    # HEMELB_GB300_CHECKED=1: the build with range-checked table loads
+    path = _build.CHECKED_LIB if os.environ.get("HEMELB_GB300_CHECKED") == "1" else _build.LIB
     if not os.path.exists(path) or not _build.up_to_date():
         if not build_if_missing:
             raise OSError("libhemelb_gb300.so is not built: %s" % path)

@@ -24,7 +24,8 @@ def case(q, seed=81, velocity=True, bfl=False):
     rng = np.random.default_rng(seed)
     kw = dict(rho_mean=[1.002, 0.999], amp=[0.001, 0.0005], period=[17.0, 29.0], phase=[0.3, 1.1])
     if velocity:
-        kw.update(iolet_kind=[0, 1], iolet_normal=[[0, 0, 0], [0.6, 0.0, 0.8]],
+        # iolet 1 a velocity iolet: its schedule is a speed
+        kw.update(rho_mean=[1.002, 0.02], iolet_kind=[0, 1], iolet_normal=[[0, 0, 0], [0.6, 0.0, 0.8]],
                   velocity_weight=0.5 + rng.random(g.n))
     if bfl:
         kw["wall_q"] = np.round(rng.uniform(0.0, 1.0, (q, g.n)) * 2 ** 24).clip(1) / 2 ** 24
@@ -54,6 +55,7 @@ def test_graph_chunks_equal_launch_per_step(q, storage, streaming):
     for _ in range(70):
         B.step(1)
     assert np.array_equal(A.get_state(), B.get_state())
+    assert np.isfinite(A.mass())
 
 
 def test_graph_inside_a_caller_capture():
@@ -88,4 +90,5 @@ def test_driven_velocity_iolets_match_schedule(streaming):
     B = lbm.Lattice(q, g.xyz, nbr, link, 0.7, streaming=streaming, **kw)
     A.step(40)
     B.step_driven(np.tile(kw["rho_mean"], (40, 1)), mass=False)
+    assert np.isfinite(A.mass())
     assert np.array_equal(A.get_state(), B.get_state())
