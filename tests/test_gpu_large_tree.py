@@ -75,3 +75,37 @@ def test_large_tree_aa_equals_pull(big, storage):
     assert abs(A.mass() - P.mass()) <= 1e-9 * P.mass()
     A.close()
     P.close()
+
+
+def test_large_tree_pressure_drop_gradient(big):
+    """The gradient of the pressure-drop objective at this scale (fp16
+    forward, float32 adjoint, float64 accumulation, binomial checkpointing):
+    dJ/d(inlet mean density) and dJ/d(mean of one outlet) against central
+    differences of the GPU forward (h = 1e-4)."""
+    g, nbr, link = big
+    L = lattice(big, lbm.STORE_FP16, lbm.STREAM_PULL)
+    L.step(200)
+    inlet = (link == 2).any(axis=0)
+    outlet = (link >= 3).any(axis=0)
+    weight = np.where(inlet, 1.0 / (3.0 * inlet.sum()), 0.0) - np.where(outlet, 1.0 / (3.0 * outlet.sum()), 0.0)
+    n, t0 = 60, L.time
+    state0 = L.get_state()
+    sc = 1.0 / (n + 1)
+    r = L.objective_grad(lbm.OBJ_DENSITY, weight, n, t0, t0 + n + 1, scale=sc, n_snap=8)
+
+    def J(mean):
+        L.set_state(state0)
+        L.set_time(t0)
+        L.set_iolets(mean, g.amp, g.period, g.phase)
+        return L.objective_grad(lbm.OBJ_DENSITY, weight, n, t0, t0 + n + 1, scale=sc, n_snap=8)["J"]
+
+    assert J(g.rho_mean) == r["J"]  # bitwise reproducible
+    h = 1e-4
+    for k in (0, 7):
+        mp, mm = g.rho_mean.copy(), g.rho_mean.copy()
+        mp[k] += h
+        mm[k] -= h
+        d = (J(mp) - J(mm)) / (2 * h)
+        print("tree x1.86 gradient: dJ/dmean[%d] %.6e vs FD %.6e" % (k, r["dmean"][k], d))
+        assert abs(r["dmean"][k] / d - 1) < 1e-2
+    L.close()
