@@ -42,7 +42,17 @@ LB_STEPS_PER_BENCH_STEP = 100
 PROFILE_SUMMARY = {"pull": os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md"),
                    "aa": os.path.join(ROOT, "profiles", "k_step_aa_q19_vessel_tree.md")}
 PROFILED_WORKLOAD = "vessel_tree"  # the workload the summaries above were captured on
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", "lbm_step.cu")
+# the step kernels' sources: the summaries' hash is over these files' bytes in this order
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", f)
+                  for f in ("lbm_step.cu", "staging.cuh")]
+
+
+def kernel_source_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0  # HBM3e data-sheet figure, for context beside the measured peak
 
@@ -131,7 +141,7 @@ def recorded_traffic(summary=None):
     (of the AA kernels by default), or None when it is missing or was taken
     on a different kernel source."""
     try:
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        src = kernel_source_sha256()
         fields = {}
         for line in open(summary or PROFILE_SUMMARY["aa"]):
             if ":" in line and line.startswith("- "):

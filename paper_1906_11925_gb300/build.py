@@ -37,7 +37,7 @@ def sources():
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [
+    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [
         os.path.join(ROOT, "include", "lbm.h"), os.path.abspath(__file__)]
 
 

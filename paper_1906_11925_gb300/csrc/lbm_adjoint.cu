@@ -34,13 +34,17 @@
 // Nothing uses atomics, so gradients are bitwise reproducible.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lattice.h"
 #include "lbm_internal.h"
+#include "staging.cuh"
 
 namespace hemelb_gb300 {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kAdjStages = 2;  // table tiles in flight per CTA of the staged kernel
 // resident blocks per SM requested from the register allocator for the
 // adjoint kernel without and with the wall-shear-stress objective term
 #ifndef HGB_ADJ_MINB
@@ -49,11 +53,18 @@ constexpr int kBlock = 256;
 #ifndef HGB_ADJ_MINB_WSS
 #define HGB_ADJ_MINB_WSS 2
 #endif
-// 1: the block's table rows go through shared memory instead of registers
-// (fewer registers, one barrier); measured on the tree it was not faster
-// (fp16 forward state: 0.97 against 0.93 ms per adjoint step), so it is off
-#ifndef HGB_ADJ_SMEM_TAB
-#define HGB_ADJ_SMEM_TAB 0
+// resident blocks per SM of the table-staged persistent adjoint kernel
+#ifndef HGB_ADJ_MINB_STAGED
+#define HGB_ADJ_MINB_STAGED 3
+#endif
+// 1: the bulk sites of an adjoint step run in the table-staged persistent
+// kernel (the table rows of each 256-site tile copied into shared memory by
+// bulk asynchronous copies, two tiles ahead), 0: one block per tile.  On the
+// vessel tree (fp16 forward state) the staged kernel measured slower: 0.764
+// ms per adjoint step against 0.676 (2 or 4 CTAs per SM: 0.855, 0.812), with
+// the same bits; so it is off
+#ifndef HGB_ADJ_STAGED
+#define HGB_ADJ_STAGED 0
 #endif
 
 template <bool HALF>
@@ -194,184 +205,260 @@ __device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q]
     return mx * wss;
 }
 
+// The adjoint of step t at one site x (lam_out at x from lam_next and the
+// state P of time t); tab(i) is the table entry of population i at x (from
+// registers or from a staged copy in shared memory).  Adds the site's terms
+// of J and dJ/dtau to j_site and dtau_site (float).
+template <int Q, bool HALF, bool WSS, bool IO, typename Tab>
+__device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename AdjLoad<HALF>::T *__restrict__ P,
+                                             const float *__restrict__ lam_next, float *__restrict__ lam_out,
+                                             const AdjStep &st, const AdjObjective &obj, int x, const Tab &tab,
+                                             double *__restrict__ io_acc, float &j_site, float &dtau_site) {
+    using R = AdjLoad<HALF>;
+    const unsigned np = (unsigned)L.npad;
+    float ne[Q];
+    ne[0] = R::ld(P + x, L.inv_scale);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int si = tab(i);
+        const unsigned e = si >= 0 ? (unsigned)i * np + (unsigned)si : (unsigned)opp(i) * np + (unsigned)x;
+        ne[i] = R::ld(P + e, L.inv_scale);
+    }
+    float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sum = ne[i] + ne[i + 1], dif = ne[i] - ne[i + 1];
+        drho += sum;
+        if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
+        if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
+        if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
+    }
+    const float rho = L.rho0 + drho;
+    const float ir = 1.0f / rho;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    // non-equilibrium parts f_i - feq_i (in place of the deviations)
+    ne[0] -= (float)wdir<Q>(0) * (drho - rho * usq15);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = (float)wdir<Q>(i);
+        const float cu = cdot<Q>(i, ux, uy, uz);
+        const float sym = w * (drho + rho * fmaf(4.5f * cu, cu, -usq15));
+        const float asym = 3.0f * w * rho * cu;
+        ne[i] -= sym + asym;
+        ne[i + 1] -= sym - asym;
+    }
+    Stress Pst{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (WSS) Pst = stress<Q>(ne);
+    // (no ordering fence here: overlapping the forward-state and adjoint
+    // gathers is worth more than the registers it costs; fencing them
+    // apart measured 1.50 ms per step against 1.06 ms)
+    // adjoint of the post-collision populations, with the iolet terms
+    // (all gathers issued first, then the pairwise sums: keeping the loads
+    // back to back measured faster than accumulating as they arrive)
+    float ls[Q];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    const bool has_next = lam_next != nullptr;
+    ls[0] = has_next ? lam_next[x] : 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int sp = tab(opp(i));  // link i of x: >= 0 -> the site x + c_i
+        ls[i] = 0.f;
+        if (has_next) {
+            if (sp >= 0) {
+                ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
+            } else if (!IO || sp == -1) {
+                ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+            } else {
+                const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+                const int k = -2 - sp;
+                const int o = opp(i);
+                const float rk = st.io.rho[k];
+                const float cu = cdot<Q>(o, ux, uy, uz);
+                const float wo = (float)wdir<Q>(o);
+                const float drk = lo * wo * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
+                const float gc = lo * wo * rk;
+                gx += gc * (3.0f * cdir<Q>(o, 0) + 9.0f * cu * cdir<Q>(o, 0) - 3.0f * ux);
+                gy += gc * (3.0f * cdir<Q>(o, 1) + 9.0f * cu * cdir<Q>(o, 1) - 3.0f * uy);
+                gz += gc * (3.0f * cdir<Q>(o, 2) + 9.0f * cu * cdir<Q>(o, 2) - 3.0f * uz);
+                const size_t slot = (size_t)(x - L.n_bulk) * (Q - 1) + (i - 1);
+                const size_t plane = (size_t)(L.n - L.n_bulk) * (Q - 1);
+                io_acc[slot] += (double)drk;
+                io_acc[plane + slot] += (double)drk * st.dsin[k];
+                io_acc[2 * plane + slot] += (double)drk * st.dacos[k];
+            }
+        }
+    }
+    // a = sum_i lam*_i feq_i/rho, b = sum_i lam*_i dfeq_i/du (pairwise),
+    // dt = sum_i lam*_i (f_i - feq_i)
+    float a = (float)wdir<Q>(0) * ls[0] * (1.0f - usq15);
+    float bx = 0.f, by = 0.f, bz = 0.f;
+    float sb = (float)wdir<Q>(0) * ls[0];
+    float dt = ls[0] * ne[0];
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float w = (float)wdir<Q>(i);
+        const float cu = cdot<Q>(i, ux, uy, uz);
+        const float sum = ls[i] + ls[i + 1], dif = ls[i] - ls[i + 1];
+        a += w * fmaf(sum, 1.0f + fmaf(4.5f * cu, cu, -usq15), 3.0f * cu * dif);
+        const float bc = w * fmaf(9.0f * cu, sum, 3.0f * dif);
+        if (cdir<Q>(i, 0)) bx += cdir<Q>(i, 0) * bc;
+        if (cdir<Q>(i, 1)) by += cdir<Q>(i, 1) * bc;
+        if (cdir<Q>(i, 2)) bz += cdir<Q>(i, 2) * bc;
+        sb += w * sum;
+        dt = fmaf(ls[i], ne[i], dt);
+        dt = fmaf(ls[i + 1], ne[i + 1], dt);
+    }
+    // b = rho (bc-sum - 3 u sb)
+    bx = rho * (bx - 3.0f * ux * sb);
+    by = rho * (by - 3.0f * uy * sb);
+    bz = rho * (bz - 3.0f * uz * sb);
+    dtau_site = dt * obj.inv_tau2_f;
+    const float om = L.omega, omc = 1.0f - L.omega;
+    // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
+    const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
+    const float base = om * a - (Bx * ux + By * uy + Bz * uz);
+    float lam[Q];
+    lam[0] = fmaf(omc, ls[0], base);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float bcj = cdot<Q>(i, Bx, By, Bz);
+        lam[i] = fmaf(omc, ls[i], base + bcj);
+        lam[i + 1] = fmaf(omc, ls[i + 1], base - bcj);
+    }
+    // explicit objective terms of the state f(t)
+    if (obj.active) {
+        // a non-zero weight, tested on its bits (no float64 instruction)
+        const double mxd = obj.weight[x];
+        if ((__double_as_longlong(mxd) << 1) != 0) {
+            const float mx = (float)mxd;
+            if (WSS) {
+                int s[Q];
+                s[0] = 0;
+#pragma unroll
+                for (int i = 1; i < Q; ++i) s[i] = tab(i);
+                j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
+                                     obj.wss_dlog_f, lam, &dtau_site);
+            } else if (obj.kind == 1) {
+                // m (rho - rho0): the host adds rho0 sum(m) per state in
+                // float64, so the float block sums carry only the small part
+                j_site = mx * drho;
+                const float sm = obj.scale_f * mx;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) lam[j] += sm;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
+}
+
 // One adjoint step over the sites [x_begin, x_end): the bulk sites (no
-// iolet link, IO = false) or the iolet sites (IO = true).  WSS = the
-// wall-shear-stress objective term is active at this step.
+// iolet link, IO = false) or the iolet sites (IO = true), one block per
+// 256-site tile.  WSS = the wall-shear-stress objective term is active at
+// this step.
 template <int Q, bool HALF, bool WSS, bool IO>
 __global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB)
 k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
           const AdjObjective obj, int x_begin, int x_end, double *__restrict__ acc_block,
           double *__restrict__ io_acc) {
-    using R = AdjLoad<HALF>;
     __shared__ float2 part[kBlock / 32];
-#if HGB_ADJ_SMEM_TAB
-    // the block's table rows, read once (coalesced) and then from shared
-    // memory where needed, instead of being held in registers
-    __shared__ int32_t stab[Q - 1][kBlock];
-#endif
     const int x = x_begin + blockIdx.x * kBlock + threadIdx.x;
-    const bool valid = x < x_end;
     const unsigned np = (unsigned)L.npad;
-#if HGB_ADJ_SMEM_TAB
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-        stab[i - 1][threadIdx.x] = valid ? __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x) : 0;
-    __syncthreads();
-#define HGB_S(i) stab[(i) - 1][threadIdx.x]
-#else
-#define HGB_S(i) s[i]
-#endif
     float j_site = 0.f, dtau_site = 0.f;
-    if (valid) {
-#if !HGB_ADJ_SMEM_TAB
+    if (x < x_end) {
         int s[Q];
+        s[0] = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
-#endif
-        float ne[Q];
-        ne[0] = R::ld(P + x, L.inv_scale);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int si = HGB_S(i);
-            const unsigned e = si >= 0 ? (unsigned)i * np + (unsigned)si : (unsigned)opp(i) * np + (unsigned)x;
-            ne[i] = R::ld(P + e, L.inv_scale);
-        }
-        float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const float sum = ne[i] + ne[i + 1], dif = ne[i] - ne[i + 1];
-            drho += sum;
-            if (cdir<Q>(i, 0)) jx += cdir<Q>(i, 0) * dif;
-            if (cdir<Q>(i, 1)) jy += cdir<Q>(i, 1) * dif;
-            if (cdir<Q>(i, 2)) jz += cdir<Q>(i, 2) * dif;
-        }
-        const float rho = L.rho0 + drho;
-        const float ir = 1.0f / rho;
-        const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-        const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        // non-equilibrium parts f_i - feq_i (in place of the deviations)
-        ne[0] -= (float)wdir<Q>(0) * (drho - rho * usq15);
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const float w = (float)wdir<Q>(i);
-            const float cu = cdot<Q>(i, ux, uy, uz);
-            const float sym = w * (drho + rho * fmaf(4.5f * cu, cu, -usq15));
-            const float asym = 3.0f * w * rho * cu;
-            ne[i] -= sym + asym;
-            ne[i + 1] -= sym - asym;
-        }
-        Stress Pst{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (WSS) Pst = stress<Q>(ne);
-        // (no ordering fence here: overlapping the forward-state and adjoint
-        // gathers is worth more than the registers it costs; fencing them
-        // apart measured 1.50 ms per step against 1.06 ms)
-        // adjoint of the post-collision populations, with the iolet terms
-        // (all gathers issued first, then the pairwise sums: keeping the loads
-        // back to back measured faster than accumulating as they arrive)
-        float ls[Q];
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        const bool has_next = lam_next != nullptr;
-        ls[0] = has_next ? lam_next[x] : 0.f;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int sp = HGB_S(opp(i));  // link i of x: >= 0 -> the site x + c_i
-            ls[i] = 0.f;
-            if (has_next) {
-                if (sp >= 0) {
-                    ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
-                } else if (!IO || sp == -1) {
-                    ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
-                } else {
-                    const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
-                    const int k = -2 - sp;
-                    const int o = opp(i);
-                    const float rk = st.io.rho[k];
-                    const float cu = cdot<Q>(o, ux, uy, uz);
-                    const float wo = (float)wdir<Q>(o);
-                    const float drk = lo * wo * (1.0f + 3.0f * cu + 4.5f * cu * cu - usq15);
-                    const float gc = lo * wo * rk;
-                    gx += gc * (3.0f * cdir<Q>(o, 0) + 9.0f * cu * cdir<Q>(o, 0) - 3.0f * ux);
-                    gy += gc * (3.0f * cdir<Q>(o, 1) + 9.0f * cu * cdir<Q>(o, 1) - 3.0f * uy);
-                    gz += gc * (3.0f * cdir<Q>(o, 2) + 9.0f * cu * cdir<Q>(o, 2) - 3.0f * uz);
-                    const size_t slot = (size_t)(x - L.n_bulk) * (Q - 1) + (i - 1);
-                    const size_t plane = (size_t)(L.n - L.n_bulk) * (Q - 1);
-                    io_acc[slot] += (double)drk;
-                    io_acc[plane + slot] += (double)drk * st.dsin[k];
-                    io_acc[2 * plane + slot] += (double)drk * st.dacos[k];
-                }
-            }
-        }
-        // a = sum_i lam*_i feq_i/rho, b = sum_i lam*_i dfeq_i/du (pairwise),
-        // dt = sum_i lam*_i (f_i - feq_i)
-        float a = (float)wdir<Q>(0) * ls[0] * (1.0f - usq15);
-        float bx = 0.f, by = 0.f, bz = 0.f;
-        float sb = (float)wdir<Q>(0) * ls[0];
-        float dt = ls[0] * ne[0];
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const float w = (float)wdir<Q>(i);
-            const float cu = cdot<Q>(i, ux, uy, uz);
-            const float sum = ls[i] + ls[i + 1], dif = ls[i] - ls[i + 1];
-            a += w * fmaf(sum, 1.0f + fmaf(4.5f * cu, cu, -usq15), 3.0f * cu * dif);
-            const float bc = w * fmaf(9.0f * cu, sum, 3.0f * dif);
-            if (cdir<Q>(i, 0)) bx += cdir<Q>(i, 0) * bc;
-            if (cdir<Q>(i, 1)) by += cdir<Q>(i, 1) * bc;
-            if (cdir<Q>(i, 2)) bz += cdir<Q>(i, 2) * bc;
-            sb += w * sum;
-            dt = fmaf(ls[i], ne[i], dt);
-            dt = fmaf(ls[i + 1], ne[i + 1], dt);
-        }
-        // b = rho (bc-sum - 3 u sb)
-        bx = rho * (bx - 3.0f * ux * sb);
-        by = rho * (by - 3.0f * uy * sb);
-        bz = rho * (bz - 3.0f * uz * sb);
-        dtau_site = dt * obj.inv_tau2_f;
-        const float om = L.omega, omc = 1.0f - L.omega;
-        // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
-        const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
-        const float base = om * a - (Bx * ux + By * uy + Bz * uz);
-        float lam[Q];
-        lam[0] = fmaf(omc, ls[0], base);
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const float bcj = cdot<Q>(i, Bx, By, Bz);
-            lam[i] = fmaf(omc, ls[i], base + bcj);
-            lam[i + 1] = fmaf(omc, ls[i + 1], base - bcj);
-        }
-        // explicit objective terms of the state f(t)
-        if (obj.active) {
-            // a non-zero weight, tested on its bits (no float64 instruction)
-            const double mxd = obj.weight[x];
-            if ((__double_as_longlong(mxd) << 1) != 0) {
-                const float mx = (float)mxd;
-                if (WSS) {
-#if HGB_ADJ_SMEM_TAB
-                    int s[Q];
-#pragma unroll
-                    for (int i = 1; i < Q; ++i) s[i] = HGB_S(i);
-#endif
-                    j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
-                                         obj.wss_dlog_f, lam, &dtau_site);
-                } else if (obj.kind == 1) {
-                    // m (rho - rho0): the host adds rho0 sum(m) per state in
-                    // float64, so the float block sums carry only the small part
-                    j_site = mx * drho;
-                    const float sm = obj.scale_f * mx;
-#pragma unroll
-                    for (int j = 0; j < Q; ++j) lam[j] += sm;
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
+        adjoint_site<Q, HALF, WSS, IO>(L, P, lam_next, lam_out, st, obj, x, [&](int i) { return s[i]; },
+                                       io_acc, j_site, dtau_site);
     }
-#undef HGB_S
     const float2 bsum = block_sum_f2(j_site, dtau_site, part);
     if (threadIdx.x == 0) {
         const int b = (x_begin == 0 ? 0 : (L.n_bulk + kBlock - 1) / kBlock) + blockIdx.x;
         acc_block[2 * b] += (double)bsum.x;
         acc_block[2 * b + 1] += (double)bsum.y;
+    }
+}
+
+// The bulk sites of one adjoint step in persistent CTAs walking the 256-site
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ...: thread 0 copies the q - 1
+// table rows of a tile into shared memory with bulk asynchronous copies
+// completing on an mbarrier, two tiles ahead, so the table reads leave the
+// threads' load path and the registers that held them.  The per-site
+// arithmetic and the per-tile float block sums are those of k_adjoint (the
+// same acc_block slot per tile, the same order), so both give the same bits.
+// Every wait is bounded: on a timeout the CTA sets *err, waits (bounded) for
+// its other copy in flight, and returns.
+template <int Q, bool HALF, bool WSS>
+__global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB_STAGED)
+k_adjoint_staged(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
+                 const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
+                 const AdjObjective obj, double *__restrict__ acc_block, int *__restrict__ err) {
+    constexpr int NE = Q - 1;
+    constexpr int SB = NE * kBlock * 4;
+    extern __shared__ __align__(128) unsigned char sbuf[];  // [kAdjStages][SB]
+    __shared__ __align__(8) uint64_t bar[kAdjStages];
+    __shared__ float2 part[kBlock / 32];
+    __shared__ int ok;
+    const int tid = threadIdx.x;
+    const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
+    const unsigned np = (unsigned)L.npad;
+    auto issue = [&](int stage, int tile) {
+        // ragged last tile: the row rounded up to 16 bytes stays inside the
+        // plane (npad is a multiple of 128 and >= n_bulk)
+        const int count = min(kBlock, L.n_bulk - tile * kBlock);
+        const unsigned bytes = ((unsigned)count * 4u + 15u) & ~15u;
+        unsigned char *dst = sbuf + stage * SB;
+        mbar_expect_tx(&bar[stage], bytes * NE);
+#pragma unroll 1
+        for (int i = 0; i < NE; ++i)
+            bulk_g2s(dst + i * kBlock * 4, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
+    };
+    if (tid == 0) {
+        for (int k = 0; k < kAdjStages; ++k) mbar_init(&bar[k], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int k = 0; k < kAdjStages; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile < ntiles) issue(k, tile);
+        }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int stage = k % kAdjStages;
+        const unsigned parity = (unsigned)(k / kAdjStages) & 1u;
+        if (tid == 0) ok = mbar_wait_bounded(&bar[stage], parity) ? 1 : 0;
+        __syncthreads();
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                const int other = tile + gridDim.x;
+                if (other < ntiles) mbar_wait_bounded(&bar[(k + 1) % kAdjStages], (unsigned)((k + 1) / kAdjStages) & 1u);
+            }
+            return;
+        }
+        const int32_t *rows = reinterpret_cast<const int32_t *>(sbuf + stage * SB);
+        const int x = tile * kBlock + tid;
+        float j_site = 0.f, dtau_site = 0.f;
+        if (x < L.n_bulk)
+            adjoint_site<Q, HALF, WSS, false>(L, P, lam_next, lam_out, st, obj, x,
+                                              [&](int i) { return rows[(i - 1) * kBlock + tid]; }, nullptr,
+                                              j_site, dtau_site);
+        // (its barriers also tell thread 0 that every thread is done with
+        // this stage's rows)
+        const float2 bsum = block_sum_f2(j_site, dtau_site, part);
+        if (tid == 0) {
+            acc_block[2 * tile] += (double)bsum.x;
+            acc_block[2 * tile + 1] += (double)bsum.y;
+            const int nt = tile + kAdjStages * gridDim.x;
+            if (nt < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(stage, nt);
+            }
+        }
     }
 }
 
@@ -440,9 +527,29 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
                          double *io_acc, cudaStream_t s) {
     using T = typename AdjLoad<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
-    if (nb > 0)
+    if (nb > 0 && HGB_ADJ_STAGED && L.err) {
+        static int grid_cache[2][2] = {{0, 0}, {0, 0}};
+        const size_t smem = (size_t)kAdjStages * (Q - 1) * kBlock * 4;
+        int &g = grid_cache[HALF ? 1 : 0][WSS ? 1 : 0];
+        if (g == 0) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (smem > 48 * 1024) {
+                const cudaError_t e = cudaFuncSetAttribute(k_adjoint_staged<Q, HALF, WSS>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint_staged<Q, HALF, WSS>, kBlock, smem);
+            g = std::max(1, sms * std::max(per, 1));
+        }
+        const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
+        k_adjoint_staged<Q, HALF, WSS><<<grid, kBlock, smem, s>>>(L, (const T *)P, lam_next, lam_out, st, obj,
+                                                                  acc_block, L.err);
+    } else if (nb > 0) {
         k_adjoint<Q, HALF, WSS, false><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, 0, nb, acc_block, io_acc);
+    }
     if (ni > 0)
         k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);

@@ -29,6 +29,7 @@
 
 #include "lattice.h"
 #include "lbm_internal.h"
+#include "staging.cuh"
 
 namespace hemelb_gb300 {
 namespace {
@@ -316,38 +317,6 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #define HGB_STAGES 2
 #endif
 constexpr int kStages = HGB_STAGES;
-constexpr unsigned kWaitLimit = 1u << 22;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
-                                                  unsigned limit = kWaitLimit) {
-    for (unsigned it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
 // The failure path of the staged step, on its own: an mbarrier that expects
 // 16 bytes no copy will ever deliver, waited on with the same bounded wait;
 // on giving up the kernel sets *err and returns (no copy was issued, so
@@ -360,13 +329,6 @@ __global__ void k_wait_probe(int *err, unsigned limit) {
     if (!mbar_wait_bounded(&bar, 0u, limit)) atomicExch(err, 1);
 }
 
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 
 // bytes of one stage buffer: the larger of the int32 rows and the compressed
