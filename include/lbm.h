@@ -178,7 +178,9 @@ void lbm_destroy(lbm_ctx *ctx);
  * without a context on this thread when ctx is NULL.  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Change the stream used by later calls. */
+/* Change the stream used by later calls.  Work that later calls queue on
+ * the new stream starts after the work already queued on the old one (an
+ * event recorded on the old stream, waited for by the new one). */
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 
 /* Advance nsteps >= 0 time steps (Section 2: collision then propagation),

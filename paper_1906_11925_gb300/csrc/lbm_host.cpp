@@ -69,6 +69,7 @@ struct lbm_ctx {
     bool has_bfl = false;  // interpolated wall links in the table
     SideStream side{nullptr, nullptr, nullptr};  // for the launch after the bulk
     int *flags = nullptr;        // device: [0] instability check, [1] guard check
+    cudaEvent_t handover = nullptr;  // lbm_set_stream: old stream -> new stream
     int64_t check_every = 0;     // lbm_set_stability_check (0: off)
     double check_umax = 0.3;
     // lbm_step's CUDA graphs (see run_graph_chunks): one captured chunk of
@@ -652,6 +653,7 @@ void free_ctx(lbm_ctx *c) {
     if (c->side.s) cudaStreamDestroy(c->side.s);
     if (c->side.fork) cudaEventDestroy(c->side.fork);
     if (c->side.join) cudaEventDestroy(c->side.join);
+    if (c->handover) cudaEventDestroy(c->handover);
     graphs_reset(c);
     cudaFree(c->graphs.io_dev);
     if (c->graphs.io_pin) cudaFreeHost(c->graphs.io_pin);
@@ -914,7 +916,14 @@ HGB_API void lbm_destroy(lbm_ctx *ctx) {
 
 HGB_API lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
-    ctx->stream = (cudaStream_t)cuda_stream;
+    const cudaStream_t next = (cudaStream_t)cuda_stream;
+    if (next != ctx->stream) {
+        // the new stream waits for the work already queued on the old one
+        if (!ctx->handover) CK(ctx, cudaEventCreateWithFlags(&ctx->handover, cudaEventDisableTiming));
+        CK(ctx, cudaEventRecord(ctx->handover, ctx->stream));
+        CK(ctx, cudaStreamWaitEvent(next, ctx->handover, 0));
+    }
+    ctx->stream = next;
     return LBM_OK;
 }
 

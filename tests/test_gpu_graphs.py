@@ -92,3 +92,20 @@ def test_driven_velocity_iolets_match_schedule(streaming):
     B.step_driven(np.tile(kw["rho_mean"], (40, 1)), mass=False)
     assert np.isfinite(A.mass())
     assert np.array_equal(A.get_state(), B.get_state())
+
+
+def test_set_stream_orders_the_new_stream_after_the_old():
+    """Steps queued on a second stream after lbm_set_stream start after the
+    steps still queued on the first (no host synchronisation in between)."""
+    q = 19
+    g, nbr, link, kw = case(q, seed=84)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    A = lbm.Lattice(q, g.xyz, nbr, link, 0.7, stream=s1, **kw)
+    B = lbm.Lattice(q, g.xyz, nbr, link, 0.7, **kw)
+    A.step(300)
+    A.set_stream(s2)
+    A.step(45)
+    A.set_stream(s1)
+    A.step(33)
+    B.step(378)
+    assert np.array_equal(A.get_state(), B.get_state())
