@@ -683,6 +683,10 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     if (n >= (1LL << 31) - 1024) return fail(nullptr, LBM_ERR_ARG, "too many sites");
     if (n > 0 && (!xyz || !nbr || !link)) return fail(nullptr, LBM_ERR_ARG, "NULL array");
     const int q = p->q;
+    // the kernels address a population plane slot as a 32-bit offset
+    const int64_t npad = std::max<int64_t>(128, (n + 127) / 128 * 128);
+    if ((int64_t)q * npad >= (1LL << 31))
+        return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     st = validate_tables(q, p->n_iolets, n, nbr, link);
     if (st != LBM_OK) return st;
     // interpolated walls: q in (0, 1] on every wall link; pull streaming only
@@ -702,9 +706,6 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     for (int64_t i = 0; i < 3 * n; ++i)
         if (xyz[i] < -lim || xyz[i] >= lim) return fail(nullptr, LBM_ERR_ARG, "coordinate out of range");
 
-    const int64_t npad = std::max<int64_t>(128, (n + 127) / 128 * 128);
-    if ((int64_t)q * npad >= (1LL << 31))
-        return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     const size_t eb = elem_bytes(p->storage);
     const size_t nbuf = p->streaming == LBM_STREAM_AA ? 1 : 2;
     const size_t need = nbuf * ((size_t)q * npad + (size_t)kGuardSlots) * eb + (size_t)(q - 1) * npad * 4 +

@@ -253,3 +253,26 @@ def test_wall_fractions_of_the_tube_are_exact():
     assert np.abs(r - 5.3).max() < 1e-5
     assert np.all((wq[ii, xx] > 0) & (wq[ii, xx] <= 1)) and np.all(wq[link != 1] == 0.5)
     assert np.all(np.round(wq * 2 ** 24) == wq * 2 ** 24)
+
+
+@pytest.mark.parametrize("q,n", [(19, 113_025_409), (19, 120_000_000), (15, 143_165_569),
+                                 (15, (1 << 31) - 1024)])
+def test_size_limit_is_checked_before_any_table_read(q, n):
+    """The kernels address population slots with 32-bit offsets: lbm_create
+    refuses q * npad >= 2^31 (npad = n rounded up to 128; largest D3Q19
+    lattice 113,025,408 sites) before it reads the site arrays, so that
+    one-element stand-ins for them are never touched."""
+    import ctypes as C
+
+    npad = max(128, -(-n // 128) * 128)
+    assert q * npad >= 2 ** 31  # (a size below the limit would read the stand-ins)
+    lib = lbm.load_library()
+    p = lbm._Params(q=q, storage=0, tau=0.8, rho0=1.0, fp16_scale_log2=14, n_iolets=0)
+    tiny_i32 = np.zeros(4, np.int32)
+    tiny_u8 = np.zeros(4, np.uint8)
+    ctx = C.c_void_p()
+    st = lib.lbm_create(C.byref(ctx), C.byref(p), n, tiny_i32.ctypes.data_as(C.c_void_p),
+                        tiny_i32.ctypes.data_as(C.c_void_p), tiny_u8.ctypes.data_as(C.c_void_p), None)
+    msg = lib.lbm_last_error(None).decode()
+    assert st == 1 and not ctx.value  # LBM_ERR_ARG
+    assert "too many sites" in msg, msg
