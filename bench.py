@@ -310,7 +310,8 @@ def run_ours(args):
         # iolets: fp16-deviation forward, float32 adjoint, float64 accumulation,
         # binomial checkpointing with as many snapshots as fit in 150 GB
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP16, rho_mean=g.rho_mean,
-                        amp=g.amp, period=g.period, phase=g.phase, stream=stream)
+                        amp=g.amp, period=g.period, phase=g.phase, stream=stream,
+                        streaming=stream_id[main_form])
         nsteps = args.adjoint_steps
         inlet = (link == 2).any(axis=0)
         outlet = (link >= 3).any(axis=0)
@@ -341,7 +342,8 @@ def run_ours(args):
         adj_ms = (sweep - fw * fwd_ms) / ad
         return {"objective": "pressure drop, inlet-adjacent minus outlet-adjacent mean c_s^2 rho, "
                              "averaged over all states",
-                "storage": "fp16 forward, fp32 adjoint, fp64 accumulation", "steps": nsteps,
+                "storage": "fp16 forward, fp32 adjoint, fp64 accumulation", "streaming": main_form,
+                "steps": nsteps,
                 "snapshots": n_snap, "snapshot_gb": round(n_snap * state_bytes / 2 ** 30, 1),
                 "forward_steps": fw, "adjoint_steps": ad, "sweep_ms": round(sweep, 2),
                 "wall_s": round(wall, 3), "fwd_step_ms": round(fwd_ms, 4),

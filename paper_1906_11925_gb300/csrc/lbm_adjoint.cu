@@ -53,6 +53,20 @@ constexpr int kAdjStages = 2;  // table tiles in flight per CTA of the staged ke
 #ifndef HGB_ADJ_MINB_WSS
 #define HGB_ADJ_MINB_WSS 2
 #endif
+// 1: the adjoint of an odd AA step loads its table entries a second time for
+// its stores instead of holding them in registers
+#ifndef HGB_ADJ_AA_RELOAD
+#define HGB_ADJ_AA_RELOAD 1
+#endif
+// resident blocks per SM of the adjoint of an odd AA step
+#ifndef HGB_ADJ_MINB_AA_ODD
+#define HGB_ADJ_MINB_AA_ODD 3
+#endif
+// resident blocks per SM of the adjoint of an even AA step (bulk sites: no
+// table, every access coalesced)
+#ifndef HGB_ADJ_MINB_AA_EVEN
+#define HGB_ADJ_MINB_AA_EVEN 4
+#endif
 // resident blocks per SM of the table-staged persistent adjoint kernel
 #ifndef HGB_ADJ_MINB_STAGED
 #define HGB_ADJ_MINB_STAGED 3
@@ -205,23 +219,51 @@ __device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q]
     return mx * wss;
 }
 
-// The adjoint of step t at one site x (lam_out at x from lam_next and the
+// Storage forms of one adjoint step (the forward state P of time t and the
+// adjoint buffers):
+//   FORM_PULL     P in pull layout (gathered through the table); lam_next =
+//                 lam(t+1) and lam_out = lam(t) in site form, two buffers.
+//   FORM_AA_EVEN  the adjoint of an even (site-local) AA step: P in natural
+//                 layout (own slots); one buffer, read as lam(t+1) in swapped
+//                 form (every mu_i of site x in its own slot opp(i)) and
+//                 written in place as lam(t) in site form; no table, except
+//                 for iolet links and the wall-shear-stress normals.
+//   FORM_AA_ODD   the adjoint of an odd AA step: P in swapped layout (its
+//                 slots through the table); one buffer, read as lam(t+1) in
+//                 site form (as FORM_PULL) and written in place as lam(t) in
+//                 swapped form (lam_j(x) into slot opp(j) of the site x - c_j,
+//                 or own slot j for a wall or iolet link): the slots read and
+//                 written by a site are the same set, and no other site's.
+// The adjoint of the AA form is AA-like itself (the streaming reversed), so
+// the two alternate exactly as the forward kernels do; the arithmetic is the
+// same in every form, so all give the same bits.
+enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2 };
+
+// The adjoint of step t at one site x (lam(t) at x from lam(t+1) and the
 // state P of time t); tab(i) is the table entry of population i at x (from
-// registers or from a staged copy in shared memory).  Adds the site's terms
-// of J and dJ/dtau to j_site and dtau_site (float).
-template <int Q, bool HALF, bool WSS, bool IO, typename Tab>
+// registers, global memory or a staged copy in shared memory).  Adds the
+// site's terms of J and dJ/dtau to j_site and dtau_site (float).
+template <int Q, bool HALF, bool WSS, bool IO, int FORM, typename Tab, typename TabOut>
 __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename AdjLoad<HALF>::T *__restrict__ P,
-                                             const float *__restrict__ lam_next, float *__restrict__ lam_out,
-                                             const AdjStep &st, const AdjObjective &obj, int x, const Tab &tab,
-                                             double *__restrict__ io_acc, float &j_site, float &dtau_site) {
+                                             const float *lam_next, float *lam_out, const AdjStep &st,
+                                             const AdjObjective &obj, int x, const Tab &tab,
+                                             const TabOut &tab_out, double *__restrict__ io_acc, float &j_site,
+                                             float &dtau_site) {
     using R = AdjLoad<HALF>;
     const unsigned np = (unsigned)L.npad;
     float ne[Q];
     ne[0] = R::ld(P + x, L.inv_scale);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int si = tab(i);
-        const unsigned e = si >= 0 ? (unsigned)i * np + (unsigned)si : (unsigned)opp(i) * np + (unsigned)x;
+        unsigned e;
+        if (FORM == FORM_AA_EVEN) {
+            e = (unsigned)i * np + (unsigned)x;
+        } else {
+            const int si = tab(i);
+            const unsigned a = FORM == FORM_PULL ? (unsigned)i : (unsigned)opp(i);
+            const unsigned b = FORM == FORM_PULL ? (unsigned)opp(i) : (unsigned)i;
+            e = si >= 0 ? a * np + (unsigned)si : b * np + (unsigned)x;
+        }
         ne[i] = R::ld(P + e, L.inv_scale);
     }
     float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
@@ -262,11 +304,17 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
     ls[0] = has_next ? lam_next[x] : 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int sp = tab(opp(i));  // link i of x: >= 0 -> the site x + c_i
         ls[i] = 0.f;
+        if (FORM == FORM_AA_EVEN && !IO) {
+            // (no iolet link: mu_i in the own slot opp(i) for every link)
+            if (has_next) ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+            continue;
+        }
+        const int sp = tab(opp(i));  // link i of x: >= 0 -> the site x + c_i
         if (has_next) {
             if (sp >= 0) {
-                ls[i] = lam_next[(unsigned)i * np + (unsigned)sp];
+                ls[i] = FORM == FORM_AA_EVEN ? lam_next[(unsigned)opp(i) * np + (unsigned)x]
+                                             : lam_next[(unsigned)i * np + (unsigned)sp];
             } else if (!IO || sp == -1) {
                 ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
             } else {
@@ -349,8 +397,18 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
             }
         }
     }
+    if (FORM == FORM_AA_ODD) {
+        __stcs(lam_out + x, lam[0]);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
+        for (int j = 1; j < Q; ++j) {
+            const int sj = tab_out(j);
+            __stcs(lam_out + (sj >= 0 ? (unsigned)opp(j) * np + (unsigned)sj : (unsigned)j * np + (unsigned)x),
+                   lam[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
+    }
 }
 
 // One adjoint step over the sites [x_begin, x_end): the bulk sites (no
@@ -372,8 +430,60 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
         s[0] = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
-        adjoint_site<Q, HALF, WSS, IO>(L, P, lam_next, lam_out, st, obj, x, [&](int i) { return s[i]; },
-                                       io_acc, j_site, dtau_site);
+        auto tab = [&](int i) { return s[i]; };
+        adjoint_site<Q, HALF, WSS, IO, FORM_PULL>(L, P, lam_next, lam_out, st, obj, x, tab, tab, io_acc, j_site,
+                                                  dtau_site);
+    }
+    const float2 bsum = block_sum_f2(j_site, dtau_site, part);
+    if (threadIdx.x == 0) {
+        const int b = (x_begin == 0 ? 0 : (L.n_bulk + kBlock - 1) / kBlock) + blockIdx.x;
+        acc_block[2 * b] += (double)bsum.x;
+        acc_block[2 * b + 1] += (double)bsum.y;
+    }
+}
+
+// One adjoint step of the AA form (FORM_AA_EVEN or FORM_AA_ODD, see above) over
+// the sites [x_begin, x_end), in place on the one adjoint buffer lam (read as
+// lam(t+1), written as lam(t)); tiles and block sums as in k_adjoint.
+template <int Q, bool HALF, bool WSS, bool IO, bool ODD>
+__global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS
+                                              : IO ? HGB_ADJ_MINB : ODD ? HGB_ADJ_MINB_AA_ODD : HGB_ADJ_MINB_AA_EVEN)
+k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P, float *lam, int has_next,
+             const AdjStep st, const AdjObjective obj, int x_begin, int x_end, double *__restrict__ acc_block,
+             double *__restrict__ io_acc) {
+    __shared__ float2 part[kBlock / 32];
+    const int x = x_begin + blockIdx.x * kBlock + threadIdx.x;
+    const unsigned np = (unsigned)L.npad;
+    float j_site = 0.f, dtau_site = 0.f;
+    if (x < x_end) {
+        const float *lin = has_next ? lam : nullptr;
+        // the table entries again for the swapped-form stores of an odd step:
+        // a volatile load is not merged with the first one, so the entries
+        // need not stay in registers through the whole site
+        auto reload = [&](int i) {
+            int v;
+            asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
+            return v;
+        };
+        if (ODD || IO) {
+            int s[Q];
+            s[0] = 0;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+            auto tab = [&](int i) { return s[i]; };
+            if (HGB_ADJ_AA_RELOAD)
+                adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
+                                                                                reload, io_acc, j_site, dtau_site);
+            else
+                adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
+                                                                                tab, io_acc, j_site, dtau_site);
+        } else {
+            // even step of a bulk site: the table only for the wall normals
+            // of the wall-shear-stress term
+            auto tab = [&](int i) { return __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x); };
+            adjoint_site<Q, HALF, WSS, false, FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab, tab, io_acc, j_site,
+                                                           dtau_site);
+        }
     }
     const float2 bsum = block_sum_f2(j_site, dtau_site, part);
     if (threadIdx.x == 0) {
@@ -444,9 +554,9 @@ k_adjoint_staged(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict
         const int x = tile * kBlock + tid;
         float j_site = 0.f, dtau_site = 0.f;
         if (x < L.n_bulk)
-            adjoint_site<Q, HALF, WSS, false>(L, P, lam_next, lam_out, st, obj, x,
-                                              [&](int i) { return rows[(i - 1) * kBlock + tid]; }, nullptr,
-                                              j_site, dtau_site);
+            adjoint_site<Q, HALF, WSS, false, FORM_PULL>(
+                L, P, lam_next, lam_out, st, obj, x, [&](int i) { return rows[(i - 1) * kBlock + tid]; },
+                [&](int i) { return rows[(i - 1) * kBlock + tid]; }, nullptr, j_site, dtau_site);
         // (its barriers also tell thread 0 that every thread is done with
         // this stage's rows)
         const float2 bsum = block_sum_f2(j_site, dtau_site, part);
@@ -565,7 +675,44 @@ cudaError_t adjoint_q(const DevLattice &L, const void *P, const float *lam_next,
     return adjoint_impl<Q, HALF, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
 }
 
+template <int Q, bool HALF, bool WSS, bool ODD>
+cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool has_next, const AdjStep &st,
+                            const AdjObjective &obj, double *acc_block, double *io_acc, cudaStream_t s) {
+    using T = typename AdjLoad<HALF>::T;
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (nb > 0)
+        k_adjoint_aa<Q, HALF, WSS, false, ODD><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+            L, (const T *)P, lam, has_next ? 1 : 0, st, obj, 0, nb, acc_block, io_acc);
+    if (ni > 0)
+        k_adjoint_aa<Q, HALF, WSS, true, ODD><<<(ni + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+            L, (const T *)P, lam, has_next ? 1 : 0, st, obj, nb, L.n, acc_block, io_acc);
+    return cudaGetLastError();
+}
+
+template <int Q, bool HALF>
+cudaError_t adjoint_aa_q(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
+                         const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
+                         cudaStream_t s) {
+    const bool wss = obj.active && obj.kind == 0;
+    if (p_swapped)
+        return wss ? adjoint_aa_impl<Q, HALF, true, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s)
+                   : adjoint_aa_impl<Q, HALF, false, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s);
+    return wss ? adjoint_aa_impl<Q, HALF, true, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s)
+               : adjoint_aa_impl<Q, HALF, false, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s);
+}
+
 }  // namespace
+
+cudaError_t launch_adjoint_aa(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
+                              const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
+                              cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    if (L.q == 15)
+        return L.storage ? adjoint_aa_q<15, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s)
+                         : adjoint_aa_q<15, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s);
+    return L.storage ? adjoint_aa_q<19, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s)
+                     : adjoint_aa_q<19, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s);
+}
 
 // blocks of the bulk launch plus blocks of the iolet-site launch
 int adjoint_blocks(const DevLattice &L) {

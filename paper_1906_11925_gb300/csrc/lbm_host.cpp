@@ -102,7 +102,7 @@ struct lbm_ctx {
     // adjoint workspace, kept between lbm_objective_grad calls (grown on demand)
     struct Workspace {
         std::vector<void *> slots;
-        void *W0 = nullptr, *W1 = nullptr, *final_buf = nullptr;  // W0, final: AA mode only
+        void *W0 = nullptr, *W1 = nullptr;  // W0: AA mode only
         float *lam[2] = {nullptr, nullptr};
         double *weight = nullptr, *acc_block = nullptr, *io_acc = nullptr, *out = nullptr;
         double *lam0 = nullptr;
@@ -617,7 +617,6 @@ void free_workspace(lbm_ctx *c) {
     w.slots.clear();
     cudaFree(w.W0);
     cudaFree(w.W1);
-    cudaFree(w.final_buf);
     cudaFree(w.lam[0]);
     cudaFree(w.lam[1]);
     cudaFree(w.weight);
@@ -1298,9 +1297,14 @@ struct AdjointRun {
     int kind = 0;
     double scale = 1.0;
     int64_t t_begin = 0, t_end = 0, t0 = 0, T = 0;
-    void *final_buf = nullptr;  // receives f(T), pull layout
+    void *final_buf = nullptr;  // receives f(T)
     bool terminal_done = false;
     int64_t fwd_steps = 0, adj_steps = 0;
+    // AA form: states in the AA layouts (the state of time t swapped when
+    // p0 + t - t0 is odd), recomputation in place after an out-of-place first
+    // step, one adjoint buffer lam[0] updated in place by the AA adjoint
+    bool aa = false, p0 = false;
+    bool swapped_at(int64_t t) const { return (((p0 ? 1 : 0) + (t - t0)) & 1) != 0; }
 
     AdjObjective objective_at(int64_t t) const {
         AdjObjective o{};
@@ -1330,10 +1334,22 @@ struct AdjointRun {
     }
     cudaError_t step(const void *in, void *out, int64_t t) {
         ++fwd_steps;
+        if (aa) {
+            const bool odd = swapped_at(t);
+            if (in == out) return launch_step_aa(c->L, out, odd, iolet_step(c, t), nullptr, c->stream);
+            return launch_step_aa_oop(c->L, in, out, odd, iolet_step(c, t), c->stream);
+        }
         return launch_step(c->L, in, out, iolet_step(c, t), nullptr, c->stream);
     }
     // m steps from the state src of time a; the result lands in dst
     cudaError_t advance(const void *src, int64_t a, int64_t m, void *dst) {
+        if (aa) {
+            for (int64_t k = 0; k < m; ++k) {
+                cudaError_t e = step(k == 0 ? src : dst, dst, a + k);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
         const void *in = src;
         const bool dst_is_work = dst == W[0] || dst == W[1];
         void *other = dst == W[0] ? W[1] : W[0];
@@ -1349,6 +1365,9 @@ struct AdjointRun {
         return cudaSuccess;
     }
     cudaError_t adjoint(const void *state, const float *next, float *out, int64_t t) {
+        if (aa)
+            return launch_adjoint_aa(c->L, state, swapped_at(t), out, next != nullptr, adj_step(t),
+                                     objective_at(t), acc_block, io_acc, c->stream);
         return launch_adjoint(c->L, state, next, out, adj_step(t), objective_at(t), acc_block, io_acc,
                               c->stream);
     }
@@ -1361,8 +1380,12 @@ struct AdjointRun {
             if ((e = adjoint(final_buf, nullptr, lam[lc], T)) != cudaSuccess) return e;
             terminal_done = true;
         }
-        if ((e = adjoint(state, lam[lc], lam[1 - lc], k)) != cudaSuccess) return e;
-        lc = 1 - lc;
+        if (aa) {
+            if ((e = adjoint(state, lam[0], lam[0], k)) != cudaSuccess) return e;  // in place
+        } else {
+            if ((e = adjoint(state, lam[lc], lam[1 - lc], k)) != cudaSuccess) return e;
+            lc = 1 - lc;
+        }
         ++adj_steps;
         return cudaSuccess;
     }
@@ -1488,10 +1511,7 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     // the per-context sizes of everything but the snapshots never change
     const bool aa = ctx->streaming == LBM_STREAM_AA;
     grow(&ws.W1, sbytes);
-    if (aa) {
-        grow(&ws.W0, sbytes);
-        grow(&ws.final_buf, sbytes);
-    }
+    if (aa) grow(&ws.W0, sbytes);
     grow((void **)&ws.lam[0], (size_t)q * npad * 4);
     grow((void **)&ws.lam[1], (size_t)q * npad * 4);
     grow((void **)&ws.weight, (size_t)npad * 8);
@@ -1517,7 +1537,9 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     R.slots.assign(ws.slots.begin(), ws.slots.begin() + n_snap);
     R.W[1] = ws.W1;
     R.W[0] = aa ? ws.W0 : ctx->f_nxt;
-    R.final_buf = aa ? ws.final_buf : ctx->f_cur;
+    R.final_buf = ctx->f_cur;  // f(t0) is copied into slot 0 first
+    R.aa = aa;
+    R.p0 = aa && ctx->aa_swapped;
     R.lam[0] = ws.lam[0];
     R.lam[1] = ws.lam[1];
     R.acc_block = ws.acc_block;
@@ -1534,13 +1556,9 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     R.weight = weight_dev;
     for (int i = n_snap - 1; i >= 1; --i) R.free_slots.push_back(i);
     if (e == cudaSuccess) e = cudaEventRecord(ws.ev[0], ctx->stream);
-    // the sweep works on pull-layout states; slot 0 receives f(t0)
-    if (e == cudaSuccess) {
-        if (aa)
-            e = launch_relayout(ctx->L, ctx->f_cur, cur_layout(ctx), R.slots[0], LAYOUT_PULL, ctx->stream);
-        else
-            e = cudaMemcpyAsync(R.slots[0], ctx->f_cur, sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
-    }
+    // slot 0 receives f(t0) in the context's own layout (pull, or the AA
+    // layout of the context's phase)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.slots[0], ctx->f_cur, sbytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess) {
         if (nsteps == 0) {
             e = R.adjoint(R.slots[0], nullptr, R.lam[0], R.t0);
@@ -1551,12 +1569,19 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
             e = R.reverse(R.t0, R.T, R.slots[0], n_snap - 1);
         }
     }
-    // AA mode: the final state back into the single buffer, natural layout
-    if (e == cudaSuccess && aa && nsteps > 0)
-        e = launch_relayout(ctx->L, R.final_buf, LAYOUT_PULL, ctx->f_cur, LAYOUT_NATURAL, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ws.ev[1], ctx->stream);
     if (e == cudaSuccess) e = launch_adjoint_final(ctx->L, R.acc_block, R.io_acc, out_dev, ctx->stream);
-    if (e == cudaSuccess && dJ_df0) e = launch_lam_to_caller(ctx->L, R.lam[R.lc], lam0_dev, ctx->stream);
+    if (e == cudaSuccess && dJ_df0) {
+        const float *lam0 = R.lam[R.lc];
+        if (aa && R.p0) {
+            // lam(t0) of an AA context in the swapped phase is in swapped form
+            DevLattice Lf = ctx->L;
+            Lf.storage = 0;
+            e = launch_relayout(Lf, R.lam[0], LAYOUT_AA_SWAPPED, R.lam[1], LAYOUT_NATURAL, ctx->stream);
+            lam0 = R.lam[1];
+        }
+        if (e == cudaSuccess) e = launch_lam_to_caller(ctx->L, lam0, lam0_dev, ctx->stream);
+    }
     std::vector<double> out((size_t)(2 + 3 * K), 0.0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out.data(), out_dev, out.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
@@ -1568,7 +1593,7 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_objective_grad");
     ctx->last_sweep_ms = sweep_ms;
     ctx->t = R.T;
-    if (aa && nsteps > 0) ctx->aa_swapped = false;
+    if (aa) ctx->aa_swapped = R.swapped_at(R.T);
     ctx->last_fwd_steps = R.fwd_steps;
     ctx->last_adj_steps = R.adj_steps;
     double jsum = out[0];

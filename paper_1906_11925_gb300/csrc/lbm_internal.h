@@ -202,6 +202,19 @@ struct AdjObjective {
 };
 
 int adjoint_blocks(const DevLattice &L);
+// The adjoint of one AA step, in place on the one adjoint buffer lam: P is
+// the stored state of time t in the AA form (natural layout: the adjoint of
+// an even step, reading lam(t+1) in swapped form and writing lam(t) in site
+// form; swapped layout: of an odd step, reading site form and writing
+// swapped form); has_next = false for the terminal lam(T) (explicit terms
+// only, written in the form the step t reads).
+cudaError_t launch_adjoint_aa(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
+                              const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
+                              cudaStream_t s);
+// One AA step from the state in src into dst (out of place: every slot of
+// dst written), the layouts as for launch_step_aa.
+cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, bool odd, const IoletStep &io,
+                               cudaStream_t s);
 // lam_out = adjoint of step t at the state P = stored state of time t, from
 // lam_next = lam(t+1) (null for the terminal state); accumulates J and
 // dJ/dtau into acc_block[2 * blocks] and iolet derivatives into io_acc

@@ -508,6 +508,37 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Iolet
     }
 }
 
+// The AA step out of place, from the state in S into D (the same slots as
+// k_step_aa reads and writes, S and D distinct; every slot of D is written):
+// the first step of a recomputation from an adjoint snapshot, which must stay
+// intact.  The per-site arithmetic is k_step_aa's.
+template <int Q, bool HALF, bool ODD, bool IO>
+__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
+k_step_aa_oop(const DevLattice L, const typename Raw<HALF>::T *__restrict__ S, typename Raw<HALF>::T *__restrict__ D,
+              const IoletStep io) {
+    using R = Raw<HALF>;
+    const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
+    if (x >= (IO ? L.n : L.n_bulk)) return;
+    const unsigned np = (unsigned)L.npad;
+    int s[Q];
+    s[0] = 0;
+    if (ODD || IO) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
+    }
+    auto slot = [&](int i) -> unsigned {
+        if (!ODD || i == 0) return (unsigned)i * np + (unsigned)x;
+        return s[i] >= 0 ? (unsigned)opp(i) * np + (unsigned)s[i] : (unsigned)i * np + (unsigned)x;
+    };
+    float d[Q], out[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = R::ld(S + slot(i));
+    const Velocity v = collide<Q, HALF>(L, d, out);
+    if (IO) iolet_override<Q, HALF>(L, x, s, v, io, nullptr, nullptr, out);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) R::st(D + slot(i), out[opp(i)]);
+}
+
 // Table-staged persistent form of the odd AA step for the bulk sites: the
 // 18 table rows of each 256-site tile arrive in shared memory by bulk
 // asynchronous copies (two tiles ahead, as in k_step_staged), and each site
@@ -699,6 +730,29 @@ cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const 
                         const IoletStep *io_dev) {
     if (L.n == 0) return cudaSuccess;
     return HGB_DISPATCH(L, step_impl, L, fin, fout, io, rho_io, s, side, io_dev);
+}
+
+namespace {
+template <int Q, bool HALF>
+cudaError_t step_aa_oop_impl(const DevLattice &L, const void *src, void *dst, bool odd, const IoletStep &io,
+                             cudaStream_t s) {
+    using T = typename Raw<HALF>::T;
+    const int nb = L.n_bulk, ni = L.n - L.n_bulk;
+    if (odd) {
+        if (nb) k_step_aa_oop<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+        if (ni) k_step_aa_oop<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+    } else {
+        if (nb) k_step_aa_oop<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+        if (ni) k_step_aa_oop<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, bool odd, const IoletStep &io,
+                               cudaStream_t s) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_aa_oop_impl, L, src, dst, odd, io, s);
 }
 
 cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
