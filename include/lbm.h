@@ -329,8 +329,11 @@ typedef struct {
  * Every output pointer except J may be NULL.  Forward arithmetic is that of
  * lbm_step (fp32 or fp16 storage), the adjoint state is float32, and every
  * time accumulation (J and all derivatives) is float64; results are bitwise
- * reproducible and do not depend on n_snap.  n_snap >= 1 device snapshots of
- * the stored state are used (one holds f(t0)); the schedule is Griewank's
+ * reproducible and do not depend on n_snap.  An LBM_STREAM_AA context runs
+ * the sweep in the AA form (states in the AA layouts, the adjoint steps in
+ * place on one buffer, the adjoint of every other step without the table);
+ * its results are those of the pull form to the bit.  n_snap >= 1 device
+ * snapshots of the stored state are used (one holds f(t0)); the schedule is Griewank's
  * binomial checkpointing, lbm_revolve_steps forward steps in total.  Device
  * memory: (n_snap + 1) state buffers + 2 float32 adjoint buffers + small,
  * allocated on the first call and kept in the context for later calls

@@ -19,10 +19,13 @@
 //   dJ/drho_k(t) += sum over iolet-k links of lam_opp(i)(x, t+1) feq_opp(i)/rho_k,
 // chained to mean, amp and phase of rho_k(t) = mean + amp sin(2 pi t/T + phase).
 //
-// The adjoint state is kept in site form, lam[i][x] (float32), so the
-// kernel is a pull like the forward step: lam*_i at x is read from the site
-// that the forward table lists as the source of population opp(i) (the site
-// x + c_i), or from x itself for wall and iolet links.  Arithmetic is float32;
+// In the pull form the adjoint state is kept in site form, lam[i][x]
+// (float32), so the kernel is a pull like the forward step: lam*_i at x is
+// read from the site that the forward table lists as the source of
+// population opp(i) (the site x + c_i), or from x itself for wall and iolet
+// links.  In the AA form (an AA context) the adjoint steps run in place on one
+// buffer, alternating like the forward AA kernels (FORM_AA_EVEN / FORM_AA_ODD
+// below).  Arithmetic is float32;
 // the time accumulation of J and of every derivative is float64:
 //   - J and dJ/dtau: the per-site terms (float) are summed over each thread
 //     block in float, and the block totals go into one float64 pair per
