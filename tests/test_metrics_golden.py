@@ -21,3 +21,21 @@ def test_bytes_per_site_update():
     assert metrics.bytes_per_site_update(19, "fp16") == 148
     assert metrics.bytes_per_site_update(19, "fp32", "aa") == 188
     assert metrics.bytes_per_site_update(19, "fp16", "aa") == 112
+
+
+def test_profile_summaries_match_the_step_source():
+    """The DRAM traffic the benchmark reports comes from the committed ncu
+    summaries only while they name the hash of the current step-kernel
+    source; a change to the step kernels without a new capture (or an
+    explained hash update) shows here."""
+    import bench
+
+    for form in ("aa", "pull"):
+        t = bench.recorded_traffic(bench.PROFILE_SUMMARY[form])
+        assert t is not None, form
+        assert set(t) == {"traffic_bytes_per_launch_fp32", "traffic_bytes_per_launch_fp16"}
+        # within a few percent of the algorithmic bytes of one launch on the tree
+        bulk = 10_752_421
+        alg = {"aa": (188, 112), "pull": (224, 148)}[form]
+        assert 0.9 < t["traffic_bytes_per_launch_fp32"] / (alg[0] * bulk) < 1.1
+        assert 0.9 < t["traffic_bytes_per_launch_fp16"] / (alg[1] * bulk) < 1.1
