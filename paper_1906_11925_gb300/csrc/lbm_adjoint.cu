@@ -637,7 +637,7 @@ k_lam_to_caller(const DevLattice L, const float *__restrict__ lam, double *__res
 template <int Q, bool HALF, bool WSS>
 cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                          const AdjStep &st, const AdjObjective &obj, double *acc_block,
-                         double *io_acc, cudaStream_t s) {
+                         double *io_acc, cudaStream_t s, cudaStream_t t) {
     using T = typename AdjLoad<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     if (nb > 0 && HGB_ADJ_STAGED && L.err) {
@@ -664,7 +664,7 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
             L, (const T *)P, lam_next, lam_out, st, obj, 0, nb, acc_block, io_acc);
     }
     if (ni > 0)
-        k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+        k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);
     return cudaGetLastError();
 }
@@ -672,22 +672,23 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
 template <int Q, bool HALF>
 cudaError_t adjoint_q(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                       const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
-                      cudaStream_t s) {
+                      cudaStream_t s, cudaStream_t t) {
     if (obj.active && obj.kind == 0)
-        return adjoint_impl<Q, HALF, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
-    return adjoint_impl<Q, HALF, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+        return adjoint_impl<Q, HALF, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
+    return adjoint_impl<Q, HALF, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
 }
 
 template <int Q, bool HALF, bool WSS, bool ODD>
 cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool has_next, const AdjStep &st,
-                            const AdjObjective &obj, double *acc_block, double *io_acc, cudaStream_t s) {
+                            const AdjObjective &obj, double *acc_block, double *io_acc, cudaStream_t s,
+                            cudaStream_t t) {
     using T = typename AdjLoad<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     if (nb > 0)
         k_adjoint_aa<Q, HALF, WSS, false, ODD><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam, has_next ? 1 : 0, st, obj, 0, nb, acc_block, io_acc);
     if (ni > 0)
-        k_adjoint_aa<Q, HALF, WSS, true, ODD><<<(ni + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+        k_adjoint_aa<Q, HALF, WSS, true, ODD><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
             L, (const T *)P, lam, has_next ? 1 : 0, st, obj, nb, L.n, acc_block, io_acc);
     return cudaGetLastError();
 }
@@ -695,26 +696,26 @@ cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool
 template <int Q, bool HALF>
 cudaError_t adjoint_aa_q(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
                          const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
-                         cudaStream_t s) {
+                         cudaStream_t s, cudaStream_t t) {
     const bool wss = obj.active && obj.kind == 0;
     if (p_swapped)
-        return wss ? adjoint_aa_impl<Q, HALF, true, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s)
-                   : adjoint_aa_impl<Q, HALF, false, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s);
-    return wss ? adjoint_aa_impl<Q, HALF, true, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s)
-               : adjoint_aa_impl<Q, HALF, false, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s);
+        return wss ? adjoint_aa_impl<Q, HALF, true, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s, t)
+                   : adjoint_aa_impl<Q, HALF, false, true>(L, P, lam, has_next, st, obj, acc_block, io_acc, s, t);
+    return wss ? adjoint_aa_impl<Q, HALF, true, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s, t)
+               : adjoint_aa_impl<Q, HALF, false, false>(L, P, lam, has_next, st, obj, acc_block, io_acc, s, t);
 }
 
 }  // namespace
 
 cudaError_t launch_adjoint_aa(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
                               const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
-                              cudaStream_t s) {
+                              cudaStream_t s, cudaStream_t t) {
     if (L.n == 0) return cudaSuccess;
     if (L.q == 15)
-        return L.storage ? adjoint_aa_q<15, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s)
-                         : adjoint_aa_q<15, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s);
-    return L.storage ? adjoint_aa_q<19, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s)
-                     : adjoint_aa_q<19, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s);
+        return L.storage ? adjoint_aa_q<15, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+                         : adjoint_aa_q<15, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
+    return L.storage ? adjoint_aa_q<19, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+                     : adjoint_aa_q<19, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
 }
 
 // blocks of the bulk launch plus blocks of the iolet-site launch
@@ -724,13 +725,13 @@ int adjoint_blocks(const DevLattice &L) {
 
 cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                            const AdjStep &st, const AdjObjective &obj, double *acc_block,
-                           double *io_acc, cudaStream_t s) {
+                           double *io_acc, cudaStream_t s, cudaStream_t t) {
     if (L.n == 0) return cudaSuccess;
     if (L.q == 15)
-        return L.storage ? adjoint_q<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
-                         : adjoint_q<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
-    return L.storage ? adjoint_q<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s)
-                     : adjoint_q<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s);
+        return L.storage ? adjoint_q<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+                         : adjoint_q<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
+    return L.storage ? adjoint_q<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+                     : adjoint_q<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
 }
 
 cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,

@@ -1336,10 +1336,10 @@ struct AdjointRun {
         ++fwd_steps;
         if (aa) {
             const bool odd = swapped_at(t);
-            if (in == out) return launch_step_aa(c->L, out, odd, iolet_step(c, t), nullptr, c->stream);
+            if (in == out) return launch_step_aa(c->L, out, odd, iolet_step(c, t), nullptr, c->stream, side());
             return launch_step_aa_oop(c->L, in, out, odd, iolet_step(c, t), c->stream);
         }
-        return launch_step(c->L, in, out, iolet_step(c, t), nullptr, c->stream);
+        return launch_step(c->L, in, out, iolet_step(c, t), nullptr, c->stream, side());
     }
     // m steps from the state src of time a; the result lands in dst
     cudaError_t advance(const void *src, int64_t a, int64_t m, void *dst) {
@@ -1364,12 +1364,30 @@ struct AdjointRun {
         }
         return cudaSuccess;
     }
+    // the side stream of the context (null: none): the launch of the sites
+    // with iolet links runs beside the bulk launch, as in lbm_step
+    const SideStream *side() const { return c->side.s ? &c->side : nullptr; }
     cudaError_t adjoint(const void *state, const float *next, float *out, int64_t t) {
-        if (aa)
-            return launch_adjoint_aa(c->L, state, swapped_at(t), out, next != nullptr, adj_step(t),
-                                     objective_at(t), acc_block, io_acc, c->stream);
-        return launch_adjoint(c->L, state, next, out, adj_step(t), objective_at(t), acc_block, io_acc,
-                              c->stream);
+        const SideStream *sd = side();
+        cudaStream_t io_stream = c->stream;
+        if (sd) {
+            cudaError_t e = cudaEventRecord(sd->fork, c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sd->s, sd->fork, 0);
+            if (e != cudaSuccess) return e;
+            io_stream = sd->s;
+        }
+        cudaError_t e =
+            aa ? launch_adjoint_aa(c->L, state, swapped_at(t), out, next != nullptr, adj_step(t), objective_at(t),
+                                   acc_block, io_acc, c->stream, io_stream)
+               : launch_adjoint(c->L, state, next, out, adj_step(t), objective_at(t), acc_block, io_acc,
+                                c->stream, io_stream);
+        if (sd) {
+            // join even after a failed launch, so that nothing is left forked
+            const cudaError_t e2 = cudaEventRecord(sd->join, sd->s);
+            const cudaError_t e3 = e2 == cudaSuccess ? cudaStreamWaitEvent(c->stream, sd->join, 0) : e2;
+            if (e == cudaSuccess) e = e3;
+        }
+        return e;
     }
     // adjoint of step k (state of time k in `state`); the first call also
     // forms f(T) in the context's buffer and the terminal adjoint lam(T)

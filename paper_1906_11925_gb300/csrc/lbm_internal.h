@@ -207,10 +207,12 @@ int adjoint_blocks(const DevLattice &L);
 // an even step, reading lam(t+1) in swapped form and writing lam(t) in site
 // form; swapped layout: of an odd step, reading site form and writing
 // swapped form); has_next = false for the terminal lam(T) (explicit terms
-// only, written in the form the step t reads).
+// only, written in the form the step t reads).  The bulk sites run on s, the
+// sites with iolet links on t (t = s, or a stream forked from s and joined
+// back by the caller: the two launches touch disjoint slots and accumulators).
 cudaError_t launch_adjoint_aa(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
                               const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaStream_t t);
 // One AA step from the state in src into dst (out of place: every slot of
 // dst written), the layouts as for launch_step_aa.
 cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, bool odd, const IoletStep &io,
@@ -218,10 +220,10 @@ cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, 
 // lam_out = adjoint of step t at the state P = stored state of time t, from
 // lam_next = lam(t+1) (null for the terminal state); accumulates J and
 // dJ/dtau into acc_block[2 * blocks] and iolet derivatives into io_acc
-// [3][n - n_bulk][q - 1].
+// [3][n - n_bulk][q - 1].  Streams as for launch_adjoint_aa.
 cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                            const AdjStep &st, const AdjObjective &obj, double *acc_block,
-                           double *io_acc, cudaStream_t s);
+                           double *io_acc, cudaStream_t s, cudaStream_t t);
 // out[0] = sum J, out[1] = dJ/dtau, out[2 + c * K + k] = iolet derivative c of iolet k
 cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,
                                  double *out, cudaStream_t s);
