@@ -174,6 +174,39 @@ def pin_mass_walled(o, q, steps=300):
     assert np.abs(f - f0).max() > 1e-4
 
 
+def pin_mass_sum(o, q):
+    """The total mass is the sum of every population of every site, each
+    counted once.  Closed forms: the rest state of n sites has mass
+    n rho0 sum_i w_i = n rho0 (the weights sum to 1); populations numbered
+    f[i, x] = 1 + i n + x (distinct integers, exact in float64) sum to
+    m (m + 1) / 2 with m = q n, so a dropped direction or site, a wrong plane
+    stride or a transposed index changes the value; and in a closed periodic
+    box the mass of the final state equals the exactly rounded sum of the
+    initial populations.  Float64 sums of N terms are held to the recursive
+    summation bound N u sum |f|, u = 2^-53."""
+    u = 2.0 ** -53
+    for n in (1, 2, 7, 130):
+        for rho0 in (1.0, 1.25):
+            m = o.mass(o.rest_state(q, n, rho0))
+            assert abs(m - n * rho0) <= (q * n + q) * u * n * rho0, (n, rho0, m)
+        f = (1.0 + np.arange(q * n, dtype=np.float64)).reshape(q, n)
+        qn = q * n
+        assert o.mass(f) == qn * (qn + 1) // 2, (n, o.mass(f))
+        # one population carries all the mass: each position in turn
+        for x in {0, n // 2, n - 1}:
+            for i in {0, q // 2, q - 1}:
+                e = np.zeros((q, n))
+                e[i, x] = 3.0
+                assert o.mass(e) == 3.0, (i, x)
+    g = G.periodic_box(4, 3, 5)
+    nbr, link = _setup(o, q, g)
+    f0 = G.random_populations(q, g.n, seed=12, amplitude=0.3)
+    exact = math.fsum(f0.ravel())
+    assert abs(o.mass(f0) - exact) <= q * g.n * u * np.abs(f0).sum()
+    f = o.run(q, nbr, link, 0.8, f0, 50)
+    assert abs(o.mass(f) - exact) <= 1e-13 * exact
+
+
 def pin_rest(o, q, steps=100):
     """Fluid at rest between iolets of the rest density stays at rest."""
     g = G.tube(radius=3, length=8, nx=7, ny=7, rho_in=1.0, rho_out=1.0)
@@ -291,6 +324,8 @@ ALL_FAST = [
     ("links19p", lambda o: pin_links(o, 19, 2, True)),
     ("mass_periodic19", lambda o: pin_mass_periodic(o, 19)),
     ("mass_walled15", lambda o: pin_mass_walled(o, 15, 200)),
+    ("mass_sum15", lambda o: pin_mass_sum(o, 15)),
+    ("mass_sum19", lambda o: pin_mass_sum(o, 19)),
     ("rest19", lambda o: pin_rest(o, 19)),
     ("iolet_density15", lambda o: pin_iolet_density(o, 15)),
     ("iolet_time19", lambda o: pin_iolet_time(o, 19)),

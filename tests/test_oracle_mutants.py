@@ -62,6 +62,11 @@ MUTANTS = {
     "bfl_high_own_population": ("(1.0 - 1.0 / (2.0 * qw)) * fsa[L.opp[i]]", "(1.0 - 1.0 / (2.0 * qw)) * fsa[i]"),
     "bfl_high_factor": ("fs / (2.0 * qw) +", "fs / qw +"),
     "bfl_collision_tau": ("return h[i] - (h[i] - he[i]) / tau;", "return h[i] - (h[i] - he[i]) * tau;"),
+    "mass_direction_dropped": ("for (int i = 0; i < q; ++i) m += f[(int64_t)i * n + x];",
+                               "for (int i = 1; i < q; ++i) m += f[(int64_t)i * n + x];"),
+    "mass_last_site_dropped": ("for (int64_t x = 0; x < n; ++x)\n        for (int i = 0; i < q; ++i) m +=",
+                               "for (int64_t x = 0; x < n - 1; ++x)\n        for (int i = 0; i < q; ++i) m +="),
+    "mass_plane_stride": ("m += f[(int64_t)i * n + x];", "m += f[(int64_t)i * q + x];"),
     "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
                   "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }

@@ -40,6 +40,11 @@ def test_mass_walled(o, q):
 
 
 @pytest.mark.parametrize("q", [15, 19])
+def test_mass_sum(o, q):
+    pins.pin_mass_sum(o, q)
+
+
+@pytest.mark.parametrize("q", [15, 19])
 def test_rest_state(o, q):
     pins.pin_rest(o, q)
 
