@@ -169,6 +169,23 @@ class Oracle:
             raise ValueError("orc_run failed")
         return f
 
+    def run_inplace(self, q, nbr, link, tau, f, work, nsteps, t0=0, geom=None, **io):
+        """nsteps steps from time t0 on the caller's arrays: f (float64
+        [q, n], C order) holds the state on entry and on exit, work is
+        scratch of the same shape.  No copy is made, so a caller that steps
+        one state repeatedly pays only for the steps themselves."""
+        for a in (f, work):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.shape != f.shape:
+                raise ValueError("f and work must be C-contiguous float64 arrays of one shape")
+        nbr = _c(nbr, np.int32)
+        link = _c(link, np.uint8)
+        I = _Iolets(geom, **io)
+        r = self.lib.orc_run(q, f.shape[1], _p(nbr), _p(link), float(tau), I.k, _p(I.mean),
+                             _p(I.amp), _p(I.period), _p(I.phase), int(t0), int(nsteps), _p(f),
+                             _p(work))
+        if r != 0:
+            raise ValueError("orc_run failed")
+
     def run_bc(self, q, nbr, link, tau, f, nsteps, io_kind=None, io_normal=None, weight=None,
                t0=0, geom=None, wall_q=None, **io):
         """As run(), with velocity (Ladd) iolets: io_kind[k] = 1 marks iolet k as
