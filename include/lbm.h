@@ -217,7 +217,12 @@ lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss_d);
 
 /* Total mass sum_x sum_i f_i(x, t), accumulated in float64 in a fixed order
  * (deterministic for a given context).  Synchronous.  Returns
- * LBM_ERR_UNSTABLE (and stores the value) when the sum is not finite. */
+ * LBM_ERR_UNSTABLE (and stores the value) when the sum is not finite.  Also
+ * reads the error flag of the step kernels: when a step kernel gave up
+ * waiting for its table copies (or, in the checked build, met a table entry
+ * out of range) it returns LBM_ERR_CUDA, the stored state is undefined, and
+ * lbm_step, lbm_step_driven and lbm_objective_grad return LBM_ERR_STATE
+ * until lbm_set_state or lbm_set_populations replaces the state. */
 lbm_status lbm_mass(lbm_ctx *ctx, double *out);
 
 /* Weighted sum over the sites of the current state f(t), accumulated in
@@ -230,8 +235,9 @@ lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, 
 
 /* Failure detection, checked on its own: the table-staged step waits for its
  * bulk copies on mbarriers with a bounded number of polls (about 4M); a step
- * kernel that gives up sets an error flag, returns without leaving anything
- * in flight, and lbm_mass reports LBM_ERR_CUDA.  This call runs that bounded
+ * kernel that gives up sets an error flag and returns, and lbm_mass reports
+ * LBM_ERR_CUDA.  A copy it gave up on may still land afterwards, so the
+ * output of that launch is undefined (see lbm_mass).  This call runs that bounded
  * wait, with `limit` polls (1 .. 2^24), on a barrier that no copy completes,
  * and stores 1 in *gave_up when the wait gave up (it always should).  The
  * context and the device stay usable.  Synchronous on cuda_stream.  The
@@ -272,8 +278,12 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f_host);
  * the process exits); q * n above 2^20 is rejected with LBM_ERR_ARG.  No
  * cudaMalloc, cudaFree or other allocating routine is called.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress,
- * with the context's device made current for the lookup); make that first
- * call before any stream capture.  All calls share the one array: calls whose
+ * with the context's device made current for the lookup) and keeps it for
+ * the life of the process, so the device must not be reset
+ * (cudaDeviceReset) while the library is loaded.  The call copies to host
+ * memory and waits for the context's stream, so it must never be made while
+ * that stream is being captured into a CUDA graph: it then returns
+ * LBM_ERR_STATE without doing anything.  All calls share the one array: calls whose
  * work overlaps on the GPU (several contexts on different streams, or several
  * threads) race on it and must be serialised by the caller.  Every call
  * overwrites the first q * n values before reading them, so nothing needs

@@ -41,13 +41,11 @@
 
 #include "lattice.h"
 #include "lbm_internal.h"
-#include "staging.cuh"
 
 namespace hemelb_gb300 {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kAdjStages = 2;  // table tiles in flight per CTA of the staged kernel
 // resident blocks per SM requested from the register allocator for the
 // adjoint kernel without and with the wall-shear-stress objective term
 #ifndef HGB_ADJ_MINB
@@ -55,11 +53,6 @@ constexpr int kAdjStages = 2;  // table tiles in flight per CTA of the staged ke
 #endif
 #ifndef HGB_ADJ_MINB_WSS
 #define HGB_ADJ_MINB_WSS 2
-#endif
-// 1: the adjoint of an odd AA step loads its table entries a second time for
-// its stores instead of holding them in registers
-#ifndef HGB_ADJ_AA_RELOAD
-#define HGB_ADJ_AA_RELOAD 1
 #endif
 // resident blocks per SM of the adjoint of an odd AA step
 #ifndef HGB_ADJ_MINB_AA_ODD
@@ -70,20 +63,6 @@ constexpr int kAdjStages = 2;  // table tiles in flight per CTA of the staged ke
 #ifndef HGB_ADJ_MINB_AA_EVEN
 #define HGB_ADJ_MINB_AA_EVEN 4
 #endif
-// resident blocks per SM of the table-staged persistent adjoint kernel
-#ifndef HGB_ADJ_MINB_STAGED
-#define HGB_ADJ_MINB_STAGED 3
-#endif
-// 1: the bulk sites of an adjoint step run in the table-staged persistent
-// kernel (the table rows of each 256-site tile copied into shared memory by
-// bulk asynchronous copies, two tiles ahead), 0: one block per tile.  On the
-// vessel tree (fp16 forward state) the staged kernel measured slower: 0.764
-// ms per adjoint step against 0.676 (2 or 4 CTAs per SM: 0.855, 0.812), with
-// the same bits; so it is off
-#ifndef HGB_ADJ_STAGED
-#define HGB_ADJ_STAGED 0
-#endif
-
 template <bool HALF>
 struct AdjLoad;
 template <>
@@ -244,7 +223,7 @@ enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2 };
 
 // The adjoint of step t at one site x (lam(t) at x from lam(t+1) and the
 // state P of time t); tab(i) is the table entry of population i at x (from
-// registers, global memory or a staged copy in shared memory).  Adds the
+// registers or global memory).  Adds the
 // site's terms of J and dJ/dtau to j_site and dtau_site (float).
 template <int Q, bool HALF, bool WSS, bool IO, int FORM, typename Tab, typename TabOut>
 __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename AdjLoad<HALF>::T *__restrict__ P,
@@ -474,12 +453,8 @@ k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P
 #pragma unroll
             for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
             auto tab = [&](int i) { return s[i]; };
-            if (HGB_ADJ_AA_RELOAD)
-                adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
-                                                                                reload, io_acc, j_site, dtau_site);
-            else
-                adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
-                                                                                tab, io_acc, j_site, dtau_site);
+            adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
+                                                                            reload, io_acc, j_site, dtau_site);
         } else {
             // even step of a bulk site: the table only for the wall normals
             // of the wall-shear-stress term
@@ -493,85 +468,6 @@ k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P
         const int b = (x_begin == 0 ? 0 : (L.n_bulk + kBlock - 1) / kBlock) + blockIdx.x;
         acc_block[2 * b] += (double)bsum.x;
         acc_block[2 * b + 1] += (double)bsum.y;
-    }
-}
-
-// The bulk sites of one adjoint step in persistent CTAs walking the 256-site
-// tiles blockIdx.x, blockIdx.x + gridDim.x, ...: thread 0 copies the q - 1
-// table rows of a tile into shared memory with bulk asynchronous copies
-// completing on an mbarrier, two tiles ahead, so the table reads leave the
-// threads' load path and the registers that held them.  The per-site
-// arithmetic and the per-tile float block sums are those of k_adjoint (the
-// same acc_block slot per tile, the same order), so both give the same bits.
-// Every wait is bounded: on a timeout the CTA sets *err, waits (bounded) for
-// its other copy in flight, and returns.
-template <int Q, bool HALF, bool WSS>
-__global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB_STAGED)
-k_adjoint_staged(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
-                 const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
-                 const AdjObjective obj, double *__restrict__ acc_block, int *__restrict__ err) {
-    constexpr int NE = Q - 1;
-    constexpr int SB = NE * kBlock * 4;
-    extern __shared__ __align__(128) unsigned char sbuf[];  // [kAdjStages][SB]
-    __shared__ __align__(8) uint64_t bar[kAdjStages];
-    __shared__ float2 part[kBlock / 32];
-    __shared__ int ok;
-    const int tid = threadIdx.x;
-    const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
-    const unsigned np = (unsigned)L.npad;
-    auto issue = [&](int stage, int tile) {
-        // ragged last tile: the row rounded up to 16 bytes stays inside the
-        // plane (npad is a multiple of 128 and >= n_bulk)
-        const int count = min(kBlock, L.n_bulk - tile * kBlock);
-        const unsigned bytes = ((unsigned)count * 4u + 15u) & ~15u;
-        unsigned char *dst = sbuf + stage * SB;
-        mbar_expect_tx(&bar[stage], bytes * NE);
-#pragma unroll 1
-        for (int i = 0; i < NE; ++i)
-            bulk_g2s(dst + i * kBlock * 4, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
-    };
-    if (tid == 0) {
-        for (int k = 0; k < kAdjStages; ++k) mbar_init(&bar[k], 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int k = 0; k < kAdjStages; ++k) {
-            const int tile = blockIdx.x + k * gridDim.x;
-            if (tile < ntiles) issue(k, tile);
-        }
-    }
-    __syncthreads();
-    int k = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        const int stage = k % kAdjStages;
-        const unsigned parity = (unsigned)(k / kAdjStages) & 1u;
-        if (tid == 0) ok = mbar_wait_bounded(&bar[stage], parity) ? 1 : 0;
-        __syncthreads();
-        if (!ok) {
-            if (tid == 0) {
-                atomicExch(err, 1);
-                const int other = tile + gridDim.x;
-                if (other < ntiles) mbar_wait_bounded(&bar[(k + 1) % kAdjStages], (unsigned)((k + 1) / kAdjStages) & 1u);
-            }
-            return;
-        }
-        const int32_t *rows = reinterpret_cast<const int32_t *>(sbuf + stage * SB);
-        const int x = tile * kBlock + tid;
-        float j_site = 0.f, dtau_site = 0.f;
-        if (x < L.n_bulk)
-            adjoint_site<Q, HALF, WSS, false, FORM_PULL>(
-                L, P, lam_next, lam_out, st, obj, x, [&](int i) { return rows[(i - 1) * kBlock + tid]; },
-                [&](int i) { return rows[(i - 1) * kBlock + tid]; }, nullptr, j_site, dtau_site);
-        // (its barriers also tell thread 0 that every thread is done with
-        // this stage's rows)
-        const float2 bsum = block_sum_f2(j_site, dtau_site, part);
-        if (tid == 0) {
-            acc_block[2 * tile] += (double)bsum.x;
-            acc_block[2 * tile + 1] += (double)bsum.y;
-            const int nt = tile + kAdjStages * gridDim.x;
-            if (nt < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(stage, nt);
-            }
-        }
     }
 }
 
@@ -640,29 +536,9 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
                          double *io_acc, cudaStream_t s, cudaStream_t t) {
     using T = typename AdjLoad<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
-    if (nb > 0 && HGB_ADJ_STAGED && L.err) {
-        static int grid_cache[2][2] = {{0, 0}, {0, 0}};
-        const size_t smem = (size_t)kAdjStages * (Q - 1) * kBlock * 4;
-        int &g = grid_cache[HALF ? 1 : 0][WSS ? 1 : 0];
-        if (g == 0) {
-            int dev = 0, sms = 0, per = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (smem > 48 * 1024) {
-                const cudaError_t e = cudaFuncSetAttribute(k_adjoint_staged<Q, HALF, WSS>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-            }
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint_staged<Q, HALF, WSS>, kBlock, smem);
-            g = std::max(1, sms * std::max(per, 1));
-        }
-        const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
-        k_adjoint_staged<Q, HALF, WSS><<<grid, kBlock, smem, s>>>(L, (const T *)P, lam_next, lam_out, st, obj,
-                                                                  acc_block, L.err);
-    } else if (nb > 0) {
+    if (nb > 0)
         k_adjoint<Q, HALF, WSS, false><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, 0, nb, acc_block, io_acc);
-    }
     if (ni > 0)
         k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);

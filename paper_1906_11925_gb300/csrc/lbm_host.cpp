@@ -93,6 +93,10 @@ struct lbm_ctx {
     float *vel_weight = nullptr;
     double *partials = nullptr, *mass_dev = nullptr;
     int *err_flag = nullptr;
+    // a step kernel gave up waiting for its table copies (read back by
+    // lbm_mass): the stored state is undefined until lbm_set_state or
+    // lbm_set_populations replaces it, and the stepping calls refuse to run
+    bool state_undefined = false;
     double *rho_io = nullptr;  // driven iolet densities, grown on demand
     size_t rho_io_cap = 0;
     double *mass_series = nullptr;
@@ -930,6 +934,9 @@ HGB_API lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 namespace {
 // nsteps steps: whole graph chunks, then one launch per step
 lbm_status run_steps(lbm_ctx *ctx, int64_t nsteps) {
+    if (ctx->state_undefined)
+        return fail(ctx, LBM_ERR_STATE, "the state is undefined after a failed step; replace it with "
+                    "lbm_set_state or lbm_set_populations");
     int64_t s = 0;
     if (nsteps > 0 && !ctx->graphs.ready) {
         // the first step goes through the launchers directly (their one-time
@@ -1012,6 +1019,9 @@ HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *r
     if (!ctx) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return LBM_OK;
+    if (ctx->state_undefined)
+        return fail(ctx, LBM_ERR_STATE, "the state is undefined after a failed step; replace it with "
+                    "lbm_set_state or lbm_set_populations");
     const int K = ctx->n_iolets;
     if (K > 0 && !rho_io_host) return fail(ctx, LBM_ERR_ARG, "rho_io_host is NULL");
     const size_t need = (size_t)nsteps * (size_t)std::max(K, 1) * 8;
@@ -1076,8 +1086,13 @@ HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(&flag, ctx->err_flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    if (flag == 2) return fail(ctx, LBM_ERR_CUDA, "a step kernel read a table entry out of range (checked build)");
-    if (flag) return fail(ctx, LBM_ERR_CUDA, "a step kernel gave up waiting for its table copies");
+    if (flag) ctx->state_undefined = true;
+    if (flag == 2)
+        return fail(ctx, LBM_ERR_CUDA, "a step kernel read a table entry out of range (checked build); the state "
+                    "is undefined until lbm_set_state or lbm_set_populations");
+    if (flag)
+        return fail(ctx, LBM_ERR_CUDA, "a step kernel gave up waiting for its table copies; the state is "
+                    "undefined until lbm_set_state or lbm_set_populations");
     if (!std::isfinite(*out)) return fail(ctx, LBM_ERR_UNSTABLE, "non-finite mass");
     return LBM_OK;
 }
@@ -1147,9 +1162,11 @@ HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
     CK(ctx, cudaMalloc((void **)&tmp, bytes));
     cudaError_t e = cudaMemcpyAsync(tmp, f_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = launch_scatter_f64(ctx->L, tmp, cur_layout(ctx), ctx->f_cur, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_flag, 0, 4, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbm_set_populations");
+    ctx->state_undefined = false;
     return LBM_OK;
 }
 
@@ -1165,6 +1182,13 @@ HGB_API lbm_status lbm_get_populations_noalloc(lbm_ctx *ctx, double *f_host) {
         return fail(ctx, LBM_ERR_ARG, msg);
     }
     if (count == 0) return LBM_OK;
+    {
+        // a host copy and a stream synchronisation cannot be part of a capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(ctx, LBM_ERR_STATE, "lbm_get_populations_noalloc: the context's stream is being captured");
+    }
     // the scratch address is per device: look it up with the context's device current
     cudaPointerAttributes at{};
     CK(ctx, cudaPointerGetAttributes(&at, ctx->f_cur));
@@ -1210,8 +1234,10 @@ HGB_API lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
     if (phase != 0 && (phase != 1 || ctx->streaming != LBM_STREAM_AA))
         return fail(ctx, LBM_ERR_ARG, "state blob phase does not match the context's streaming");
     CK(ctx, cudaMemcpyAsync(ctx->f_cur, host, raw, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemsetAsync(ctx->err_flag, 0, 4, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->aa_swapped = phase == 1;
+    ctx->state_undefined = false;
     return LBM_OK;
 }
 
@@ -1491,6 +1517,9 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
         return fail(ctx, LBM_ERR_STATE, "contexts with interpolated walls are not differentiated");
     if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
     if (!J) return fail(ctx, LBM_ERR_ARG, "J is NULL");
+    if (ctx->state_undefined)
+        return fail(ctx, LBM_ERR_STATE, "the state is undefined after a failed step; replace it with "
+                    "lbm_set_state or lbm_set_populations");
     const int q = ctx->q, K = ctx->n_iolets;
     const int64_t n = ctx->n, npad = ctx->npad;
     const size_t sbytes = (size_t)q * npad * elem_bytes(ctx->storage);

@@ -12,7 +12,10 @@
 // The array is a fixed 8 MiB (kNoAllocMaxValues float64 values) that every GPU
 // loading this library holds until the process exits.  In host code its name
 // is only a host-side stand-in: the device address is looked up once per
-// device with cudaGetSymbolAddress, with that device current, and cached.
+// device with cudaGetSymbolAddress, with that device current, and cached for
+// the life of the process.  A device reset (cudaDeviceReset) unloads the
+// module and would leave the cached address stale, so the library assumes the
+// device is not reset while it is loaded.
 #include <mutex>
 
 #include "lbm_internal.h"

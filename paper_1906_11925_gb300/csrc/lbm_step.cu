@@ -309,7 +309,11 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 // with bulk asynchronous copies completing on an mbarrier, two tiles ahead,
 // so the table reads leave the threads' load path and arrive while the
 // previous tile computes.  Every wait is bounded: on a timeout the CTA sets
-// *err, waits (bounded) for its other copy in flight, and returns.
+// *err, waits (bounded) for its other copy in flight, and returns.  The copy
+// it gave up on may still land later, in shared memory that another CTA then
+// owns, so after a give-up the whole output of the launch is undefined:
+// lbm_mass reports the flag and the context refuses to step until its state
+// is replaced (lbm_set_state, lbm_set_populations).
 #ifndef HGB_STEP_STAGED
 #define HGB_STEP_STAGED 1
 #endif
@@ -539,93 +543,6 @@ k_step_aa_oop(const DevLattice L, const typename Raw<HALF>::T *__restrict__ S, t
     for (int i = 0; i < Q; ++i) R::st(D + slot(i), out[opp(i)]);
 }
 
-// Table-staged persistent form of the odd AA step for the bulk sites: the
-// 18 table rows of each 256-site tile arrive in shared memory by bulk
-// asynchronous copies (two tiles ahead, as in k_step_staged), and each site
-// then gathers from and scatters back into the slots they name.  Every wait
-// is bounded; on a timeout the CTA sets *err and returns.  Measured on the
-// 10.8M-site tree it is slower than the plain odd kernel (AA step pair 366
-// against 324 us fp32, 278 against 256 us fp16, in the 32-site-run order),
-// so it is built but not launched unless this switch is set.
-#ifndef HGB_AA_STAGED
-#define HGB_AA_STAGED 0
-#endif
-template <int Q, bool HALF>
-__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
-k_step_aa_odd_staged(const DevLattice L, typename Raw<HALF>::T *A, int *__restrict__ err) {
-    using R = Raw<HALF>;
-    constexpr int NE = Q - 1;
-    constexpr int SB = NE * kTile * 4;
-    static_assert(kBlock == kTile, "one site per thread per tile");
-    extern __shared__ __align__(128) unsigned char sbuf[];  // [kStages][SB]
-    __shared__ __align__(8) uint64_t bar[kStages];
-    __shared__ int ok;
-    const int tid = threadIdx.x;
-    const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
-    const unsigned np = (unsigned)L.npad;
-    auto issue = [&](int stage, int tile) {
-        unsigned char *dst = sbuf + stage * SB;
-        // ragged last tile: round the row up to 16 bytes (stays inside the
-        // plane: npad is a multiple of 128 and >= n_bulk)
-        const int count = min(kBlock, L.n_bulk - tile * kBlock);
-        const unsigned bytes = ((unsigned)count * 4u + 15u) & ~15u;
-        mbar_expect_tx(&bar[stage], bytes * NE);
-#pragma unroll 1
-        for (int i = 0; i < NE; ++i)
-            bulk_g2s(dst + i * kBlock * 4, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
-    };
-    if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int st = 0; st < kStages; ++st) {
-            const int tile = blockIdx.x + st * gridDim.x;
-            if (tile < ntiles) issue(st, tile);
-        }
-    }
-    __syncthreads();
-    int k = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        const int stage = k % kStages;
-        const unsigned parity = (unsigned)(k / kStages) & 1u;
-        if (tid == 0) ok = mbar_wait_bounded(&bar[stage], parity) ? 1 : 0;
-        __syncthreads();
-        if (!ok) {
-            if (tid == 0) {
-                atomicExch(err, 1);
-                const int other = tile + gridDim.x;
-                if (other < ntiles) mbar_wait_bounded(&bar[(k + 1) % kStages], (unsigned)((k + 1) / kStages) & 1u);
-            }
-            return;
-        }
-        const int x = tile * kBlock + tid;
-        const int32_t *r32 = reinterpret_cast<const int32_t *>(sbuf + stage * SB);
-        if (x < L.n_bulk) {
-            unsigned slot[Q];
-            slot[0] = (unsigned)x;
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int si = r32[(i - 1) * kTile + tid];
-                slot[i] = si >= 0 ? (unsigned)opp(i) * np + (unsigned)si : (unsigned)i * np + (unsigned)x;
-            }
-            float d[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot[i]);
-            float out[Q];
-            collide<Q, HALF>(L, d, out);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) R::st_rw(A + slot[i], out[opp(i)]);
-        }
-        __syncthreads();  // every thread is done with this stage's buffer
-        if (tid == 0) {
-            const int nt = tile + kStages * gridDim.x;
-            if (nt < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(stage, nt);
-            }
-        }
-    }
-}
-
 // Fork the side stream off s before the bulk launch; returns the stream the
 // launch of the sites after the bulk goes to.
 inline cudaStream_t fork_side(cudaStream_t s, const SideStream *side, bool both) {
@@ -649,27 +566,7 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
     if (odd) {
-        if (nb && HGB_AA_STAGED && L.err) {
-            static int grid_cache[2] = {0, 0};
-            const size_t smem = (size_t)kStages * (Q - 1) * kTile * 4;
-            int &g = grid_cache[HALF ? 1 : 0];
-            if (g == 0) {
-                int dev = 0, sms = 0, per = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                if (smem > 48 * 1024) {
-                    cudaError_t e = cudaFuncSetAttribute(k_step_aa_odd_staged<Q, HALF>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                    if (e != cudaSuccess) return e;
-                }
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_aa_odd_staged<Q, HALF>, kBlock, smem);
-                g = std::max(1, sms * std::max(per, 1));
-            }
-            const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
-            k_step_aa_odd_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (T *)A, L.err);
-        } else if (nb) {
-            k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
-        }
+        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
         if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io, io_dev);
     } else {
         if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);

@@ -79,3 +79,33 @@ def test_noalloc_rejects_sizes_beyond_the_static_array():
     assert "exceeds the static scratch" in str(ei.value)
     # the context stays usable
     assert L.get_populations().shape == (19, g.n)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call copies to host memory and waits for the context's stream,
+    which cannot be recorded into a CUDA graph: while that stream is being
+    captured it returns LBM_ERR_STATE, does nothing, and leaves the capture
+    usable."""
+    q = 15
+    g = G.tube(radius=4, length=12, nx=9, ny=9)
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    cs = torch.cuda.Stream()
+    A = lbm.Lattice(q, g.xyz, nbr, link, 0.7, rho_mean=g.rho_mean, stream=cs)
+    B = lbm.Lattice(q, g.xyz, nbr, link, 0.7, rho_mean=g.rho_mean)
+    A.step(2)
+    torch.cuda.synchronize()
+    lib = lbm.load_library()
+    out = np.full((q, g.n), np.nan)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cs):
+        A.step(4)
+        st = lib.lbm_get_populations_noalloc(A._ctx, out.ctypes.data_as(C.c_void_p))
+    assert st == 6, st  # LBM_ERR_STATE
+    assert "captured" in lib.lbm_last_error(A._ctx).decode()
+    assert np.isnan(out).all()
+    graph.replay()
+    torch.cuda.synchronize()
+    B.step(6)
+    ref = B.get_populations()
+    assert np.array_equal(A.get_populations(), ref)
+    assert np.array_equal(_noalloc_via_abi(A), ref)
