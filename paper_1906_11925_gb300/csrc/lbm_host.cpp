@@ -58,9 +58,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     void *f_cur = nullptr, *f_nxt = nullptr;
     int32_t *tab = nullptr, *perm = nullptr;
-    uint8_t *c16_rec = nullptr;
-    int32_t *c16_esc = nullptr;
-    uint32_t *c16_off = nullptr, *c16_cnt = nullptr;
+    uint32_t *slots = nullptr;  // slot table of the bulk step kernels (see DevLattice::slots)
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
     int io_kind[LBM_MAX_IOLETS] = {};
@@ -232,85 +230,6 @@ inline uint64_t spread3(uint64_t v) {
     return v;
 }
 
-// Compressed table of the bulk sites [0, n_bulk) (format in lbm_internal.h).
-struct CompressedTable {
-    std::vector<uint8_t> rec;
-    std::vector<int32_t> esc;
-    std::vector<uint32_t> off, cnt;
-};
-
-bool compress_table(int q, int64_t npad, int64_t n_bulk, const std::vector<int32_t> &tab,
-                    CompressedTable &ct) {
-    const int ne = q - 1;
-    const int64_t tiles = (n_bulk + kTile - 1) / kTile;
-    const size_t rb = (size_t)tile_record_bytes(q);
-    ct.rec.assign((size_t)tiles * rb, 0);
-    ct.off.assign((size_t)tiles, 0);
-    ct.cnt.assign((size_t)tiles, 0);
-    std::vector<std::vector<int32_t>> tile_esc((size_t)tiles);
-#pragma omp parallel for schedule(static)
-    for (int64_t t = 0; t < tiles; ++t) {
-        int16_t *r16 = reinterpret_cast<int16_t *>(ct.rec.data() + (size_t)t * rb);
-        uint16_t *pre = reinterpret_cast<uint16_t *>(ct.rec.data() + (size_t)t * rb + (size_t)ne * kTile * 2);
-        std::vector<int32_t> &e = tile_esc[(size_t)t];
-        for (int i = 0; i < ne; ++i) {
-            for (int w = 0; w < kTile / 32; ++w) {
-                pre[i * 8 + w] = (uint16_t)std::min<size_t>(e.size(), 0xffff);
-                for (int l = 0; l < 32; ++l) {
-                    const int64_t x = t * kTile + w * 32 + l;
-                    int code = 0;
-                    if (x < n_bulk) {
-                        const int32_t v = tab[(size_t)i * npad + x];
-                        const int64_t d = (int64_t)v - x;
-                        if (v == -1) code = kCodeWall;
-                        else if (v >= 0 && d >= -32766 && d <= 32767) code = (int)d;
-                        else {
-                            code = kCodeEscape;
-                            e.push_back(v);
-                        }
-                    }
-                    r16[(size_t)i * kTile + w * 32 + l] = (int16_t)code;
-                }
-            }
-        }
-    }
-    for (int64_t t = 0; t < tiles; ++t) {
-        std::vector<int32_t> &e = tile_esc[(size_t)t];
-        if (e.size() > (size_t)kEscapeCap) {
-            ct.cnt[(size_t)t] = kTileFallback;
-            ct.off[(size_t)t] = 0;
-            continue;
-        }
-        while (e.size() % 4) e.push_back(0);  // 16-byte segments
-        ct.off[(size_t)t] = (uint32_t)ct.esc.size();
-        ct.cnt[(size_t)t] = (uint32_t)e.size();
-        ct.esc.insert(ct.esc.end(), e.begin(), e.end());
-    }
-    if (ct.esc.empty()) ct.esc.assign(4, 0);
-    // decode every entry and compare (lossless by construction; checked anyway)
-    bool ok = true;
-#pragma omp parallel for schedule(static) reduction(&& : ok)
-    for (int64_t t = 0; t < tiles; ++t) {
-        if (ct.cnt[(size_t)t] == kTileFallback) continue;
-        const int16_t *r16 = reinterpret_cast<const int16_t *>(ct.rec.data() + (size_t)t * rb);
-        const uint16_t *pre =
-            reinterpret_cast<const uint16_t *>(ct.rec.data() + (size_t)t * rb + (size_t)ne * kTile * 2);
-        for (int i = 0; i < ne; ++i)
-            for (int w = 0; w < kTile / 32; ++w) {
-                int rank = 0;
-                for (int l = 0; l < 32; ++l) {
-                    const int64_t x = t * kTile + w * 32 + l;
-                    const int code = r16[(size_t)i * kTile + w * 32 + l];
-                    int64_t v;
-                    if (code == kCodeEscape) v = ct.esc[ct.off[(size_t)t] + pre[i * 8 + w] + rank++];
-                    else if (code == kCodeWall) v = -1;
-                    else v = x + code;
-                    if (x < n_bulk && v != tab[(size_t)i * npad + x]) ok = false;
-                }
-            }
-    }
-    return ok;
-}
 
 // Iolet densities of step t: rho_k(t) = mean + amp sin(2 pi t / period + phase),
 // in float64 on the host; the kernel receives rho_k and rho_k - rho0 as float.
@@ -641,10 +560,7 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->f_nxt);
     cudaFree(c->tab);
     cudaFree(c->vel_weight);
-    cudaFree(c->c16_rec);
-    cudaFree(c->c16_esc);
-    cudaFree(c->c16_off);
-    cudaFree(c->c16_cnt);
+    cudaFree(c->slots);
     cudaFree(c->perm);
     cudaFree(c->partials);
     cudaFree(c->err_flag);
@@ -711,12 +627,10 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
 
     const size_t eb = elem_bytes(p->storage);
     const size_t nbuf = p->streaming == LBM_STREAM_AA ? 1 : 2;
-    const size_t need = nbuf * ((size_t)q * npad + (size_t)kGuardSlots) * eb + (size_t)(q - 1) * npad * 4 +
-                        (size_t)n * 4 +
-                        (kUseCompressedTable ? ((size_t)npad / kTile + 1) * (size_t)tile_record_bytes(q) +
-                                                   (size_t)npad * 8
-                                             : 0) +
-                        (size_t)(mass_blocks() + 8) * 8;
+    // populations, the pull-source table, the slot table of the bulk sites,
+    // the permutation and the reduction scratch
+    const size_t need = nbuf * ((size_t)q * npad + (size_t)kGuardSlots) * eb + 2 * (size_t)(q - 1) * npad * 4 +
+                        (size_t)n * 4 + (size_t)(mass_blocks() + 8) * 8;
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMemGetInfo");
@@ -778,9 +692,23 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         }
     }
 
-    CompressedTable ct;
-    if (kUseCompressedTable && !compress_table(q, npad, n_bulk, tab, ct))
-        return fail(nullptr, LBM_ERR_TABLE, "internal error: compressed table does not decode");
+    // slot table of the bulk sites: the element offset, in the population
+    // buffer, that the bulk step kernel reads population i of site xi from
+    // (pull: the pull source's slot; AA: the slot the odd step reads and
+    // writes back), so that those kernels do no address arithmetic beyond one
+    // multiply-add per population
+    std::vector<uint32_t> slots((size_t)(q - 1) * npad, 0);
+    {
+        const bool aa = p->streaming == LBM_STREAM_AA;
+#pragma omp parallel for schedule(static)
+        for (int64_t xi = 0; xi < n_bulk; ++xi)
+            for (int i = 1; i < q; ++i) {
+                const int32_t s = tab[(size_t)(i - 1) * npad + xi];
+                const int64_t e = s >= 0 ? (int64_t)(aa ? opp(i) : i) * npad + s
+                                         : (int64_t)(aa ? i : opp(i)) * npad + xi;
+                slots[(size_t)(i - 1) * npad + xi] = (uint32_t)e;
+            }
+    }
 
     lbm_ctx *c = new lbm_ctx();
     c->q = q;
@@ -818,6 +746,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(dmalloc(c, &c->flags, 16));
     if (c->streaming == LBM_STREAM_PULL) CKC(dmalloc(c, &c->f_nxt, fbytes));
     CKC(dmalloc(c, &c->tab, tab.size() * 4));
+    CKC(dmalloc(c, &c->slots, slots.size() * 4));
     CKC(dmalloc(c, &c->perm, (size_t)n * 4));
     {
         // velocity-iolet weights of the iolet sites, internal order
@@ -834,19 +763,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(dmalloc(c, &c->err_flag, 16));
     CKC(cudaMemsetAsync(c->err_flag, 0, 16, c->stream));
     CKC(cudaMemcpyAsync(c->tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, c->stream));
-    if (kUseCompressedTable) {
-        CKC(dmalloc(c, &c->c16_rec, ct.rec.size()));
-        CKC(dmalloc(c, &c->c16_esc, ct.esc.size() * 4));
-        CKC(dmalloc(c, &c->c16_off, ct.off.size() * 4));
-        CKC(dmalloc(c, &c->c16_cnt, ct.cnt.size() * 4));
-        if (!ct.rec.empty())
-            CKC(cudaMemcpyAsync(c->c16_rec, ct.rec.data(), ct.rec.size(), cudaMemcpyHostToDevice, c->stream));
-        CKC(cudaMemcpyAsync(c->c16_esc, ct.esc.data(), ct.esc.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        if (!ct.off.empty()) {
-            CKC(cudaMemcpyAsync(c->c16_off, ct.off.data(), ct.off.size() * 4, cudaMemcpyHostToDevice, c->stream));
-            CKC(cudaMemcpyAsync(c->c16_cnt, ct.cnt.data(), ct.cnt.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        }
-    }
+    CKC(cudaMemcpyAsync(c->slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice, c->stream));
     if (n) CKC(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
     DevLattice &L = c->L;
     L.q = q;
@@ -864,10 +781,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     L.perm = c->perm;
     L.err = c->err_flag;
     L.vel_weight = c->vel_weight;
-    L.c16_rec = c->c16_rec;
-    L.c16_esc = c->c16_esc;
-    L.c16_off = c->c16_off;
-    L.c16_cnt = c->c16_cnt;
+    L.slots = c->slots;
     L.bfl = any_bfl ? 1 : 0;
     c->has_bfl = any_bfl;
     if (n_bulk > 0 && n_bulk < n) {

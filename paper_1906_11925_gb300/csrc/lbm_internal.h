@@ -11,29 +11,8 @@ namespace hemelb_gb300 {
 
 constexpr int kMaxIolets = 64;
 
-// Compressed pull table of the bulk sites, per tile of kTile sites (see
-// k_step_staged in lbm_step.cu): a record of q - 1 rows of int16 codes
-// (entry - x for a fluid source within +-32766, kCodeWall for a wall link,
-// kCodeEscape when the entry is in the tile's escape list) followed by a
-// (q - 1) x 8 table of uint16 offsets: the escape-list index of the first
-// escaped entry of each (row, warp); the escape list holds the int32
-// entries of the escaped codes in (row, lane) order.  A tile with more than
-// kEscapeCap escapes keeps the int32 rows (escape count kTileFallback).
-// Measured on the vessel tree: the compressed table cuts the fp32 step's DRAM
-// traffic by ~15% but its time by only 1.5% (the step is bound by the
-// gathers' request rate near the copy roofline) and slows the fp16 step
-// (the decode adds instructions to an issue-bound kernel); it is therefore
-// not built unless this switch is set.
-constexpr bool kUseCompressedTable = false;
+// Sites per tile of the table-staged pull kernel (one site per thread).
 constexpr int kTile = 256;
-constexpr int kEscapeCap = 1024;
-constexpr int kCodeEscape = -32768;
-constexpr int kCodeWall = -32767;
-constexpr uint32_t kTileFallback = 0xffffffffu;
-#if defined(__CUDACC__)
-__host__ __device__
-#endif
-constexpr int tile_record_bytes(int q) { return (q - 1) * (kTile * 2 + 8 * 2); }
 
 // Interpolated (BFL) wall links in the pull table: the entry of population
 // p whose link opp(p) is a wall at fluid fraction q != 1/2 is
@@ -98,10 +77,14 @@ struct DevLattice {
     const int32_t *tab;           // [q-1][npad]
     const int32_t *perm;          // [n] internal -> caller index
     int *err;                     // device flag: a bounded wait in a kernel timed out
-    const uint8_t *c16_rec;       // [ceil(n_bulk / kTile)][tile_record_bytes(q)], or null
-    const int32_t *c16_esc;       // escape lists (16-byte aligned per tile)
-    const uint32_t *c16_off;      // [tiles] first escape-list index of the tile
-    const uint32_t *c16_cnt;      // [tiles] escape count (padded to x4), or kTileFallback
+    // Slot table of the bulk sites [0, n_bulk), [q-1][npad]: slots[(i - 1) *
+    // npad + x] is the element offset in the population buffer that the bulk
+    // step kernel reads population i of site x from: pull streaming, the
+    // slot i * npad + tab of the pull source (opp(i) * npad + x for a wall
+    // link); AA streaming, the slot that the odd step reads and writes back,
+    // opp(i) * npad + tab (i * npad + x for a wall link).  The same
+    // information as tab, with the address arithmetic done once at create.
+    const uint32_t *slots;
     const float *vel_weight;      // [n - n_bulk] velocity-iolet weight of the iolet sites
     int bfl;                      // the table holds interpolated wall links
 };

@@ -106,6 +106,27 @@ __device__ __forceinline__ int checked_entry(const DevLattice &L, int e) {
     return -1;
 }
 
+// Checked builds: a slot-table entry outside the population buffer sets
+// *L.err = 2 and is replaced by the site's own slot `own` (the wall link's).
+__device__ __forceinline__ unsigned checked_slot(const DevLattice &L, unsigned e, unsigned own) {
+    if (!HGB_CHECK_TABLE) return e;
+    if (e < (unsigned)L.q * (unsigned)L.npad) return e;
+    atomicExch(L.err, 2);
+    return own;
+}
+
+// Base pointers of the q population planes of one buffer, and of the q - 1
+// rows of the slot table, passed by value: an access to plane i of site x is
+// then one multiply-add of x onto a pointer held in the constant bank, with
+// no per-plane offset to form.
+template <typename T>
+struct Planes {
+    T *p[19];
+};
+struct SlotRows {
+    const uint32_t *p[18];
+};
+
 // Velocity moments of one site after its collision (for the iolet values).
 struct Velocity {
     float ux, uy, uz, usq15, rs;  // rs: density in stored units
@@ -115,6 +136,20 @@ struct Velocity {
 // fp16), written per opposite pair (i, opp i): with cu = c_i.u the
 // equilibrium deviations are sym +- asym, sym = w (drho + rho (4.5 cu^2 -
 // 1.5 u^2)), asym = 3 w rho cu, and f*_i = (1 - 1/tau) d_i + (1/tau) deq_i.
+//
+// The collision conserves mass and momentum, and in float32 it must do so up
+// to rounding noise, not up to a constant factor: the products of 1/tau and
+// the weights are constants whose rounding errors have the same sign at every
+// site and step, so a collision written directly from them scales the
+// momentum by about 1 + 1e-8 per step, which adds up coherently (a relative
+// error of 1e-4 in u after 5,000 steps).  So the pairs off the axes are
+// relaxed as above, and the two conserved quantities fix the rest:
+//   axis pair a (directions +a, -a): its sum is relaxed as above, its
+//     difference is j_a minus the post-collision momentum of the other pairs
+//     along a (the momentum after the collision is the momentum before it);
+//   rest population: drho minus the sum of all the others (the mass after
+//     the collision is the mass before it).
+// In exact arithmetic this is the same collision.
 // Every step kernel (pull, AA even, AA odd) uses this one function, so all
 // streaming forms give bitwise identical populations.
 template <int Q, bool HALF>
@@ -138,12 +173,11 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
     const float rs = HALF ? rho * L.scale : rho;  // rho in stored units
     v.rs = rs;
     const float om = L.omega, omc = 1.0f - L.omega;
-    {
-        const float w0 = (float)wdir<Q>(0);
-        out[0] = fmaf(omc, d[0], om * w0 * (drs - rs * v.usq15));
-    }
+    // pairs off the axes (i >= 7): relaxed towards the equilibrium; their
+    // post-collision momentum along each axis and their mass are summed
+    float mx = 0.f, my = 0.f, mz = 0.f, mass = 0.f;
 #pragma unroll
-    for (int i = 1; i < Q; i += 2) {
+    for (int i = 7; i < Q; i += 2) {
         const float w = (float)wdir<Q>(i);
         const float cu = cdir<Q>(i, 0) * v.ux + cdir<Q>(i, 1) * v.uy + cdir<Q>(i, 2) * v.uz;
         const float t = fmaf(4.5f * cu, cu, -v.usq15);
@@ -151,7 +185,29 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
         const float asym = (3.0f * om * w * rs) * cu;
         out[i] = fmaf(omc, d[i], sym + asym);
         out[i + 1] = fmaf(omc, d[i + 1], sym - asym);
+        const float m = out[i] - out[i + 1];
+        if (cdir<Q>(i, 0)) mx += cdir<Q>(i, 0) * m;
+        if (cdir<Q>(i, 1)) my += cdir<Q>(i, 1) * m;
+        if (cdir<Q>(i, 2)) mz += cdir<Q>(i, 2) * m;
+        mass += out[i] + out[i + 1];
     }
+    // axis pairs (i = 1, 3, 5 along x, y, z): relaxed sum, difference from
+    // the momentum balance
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i = 2 * a + 1;
+        const float w = (float)wdir<Q>(i);
+        const float cu = a == 0 ? v.ux : (a == 1 ? v.uy : v.uz);
+        const float t = fmaf(4.5f * cu, cu, -v.usq15);
+        const float sym = fmaf(om * w * rs, t, om * w * drs);
+        const float sp = fmaf(omc, d[i] + d[i + 1], sym + sym);
+        const float dm = (a == 0 ? jx : (a == 1 ? jy : jz)) - (a == 0 ? mx : (a == 1 ? my : mz));
+        out[i] = 0.5f * (sp + dm);
+        out[i + 1] = 0.5f * (sp - dm);
+        mass += out[i] + out[i + 1];
+    }
+    // rest population from the mass balance
+    out[0] = drs - mass;
     return v;
 }
 
@@ -320,6 +376,10 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #ifndef HGB_STAGES
 #define HGB_STAGES 2
 #endif
+// persistent CTAs per SM of the staged kernel (0: as many as fit)
+#ifndef HGB_STAGED_CTAS
+#define HGB_STAGED_CTAS 0
+#endif
 constexpr int kStages = HGB_STAGES;
 // The failure path of the staged step, on its own: an mbarrier that expects
 // 16 bytes no copy will ever deliver, waited on with the same bounded wait;
@@ -335,42 +395,22 @@ __global__ void k_wait_probe(int *err, unsigned limit) {
 
 
 
-// bytes of one stage buffer: the larger of the int32 rows and the compressed
-// record plus a full escape list
-template <int Q>
-__host__ __device__ constexpr int stage_bytes() {
-    return (Q - 1) * kTile * 4 > tile_record_bytes(Q) + kEscapeCap * 4 ? (Q - 1) * kTile * 4
-                                                                        : tile_record_bytes(Q) + kEscapeCap * 4;
-}
-
 template <int Q, bool HALF>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
 k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
-              typename Raw<HALF>::T *__restrict__ fout, int *__restrict__ err) {
+              const Planes<typename Raw<HALF>::T> out_planes, int *__restrict__ err) {
     using R = Raw<HALF>;
     constexpr int NE = Q - 1;
-    constexpr int SB = stage_bytes<Q>();
-    constexpr int RB = tile_record_bytes(Q);
+    constexpr int SB = NE * kTile * 4;
     static_assert(kBlock == kTile, "one site per thread per tile");
     extern __shared__ __align__(128) unsigned char sbuf[];  // [kStages][SB]
     __shared__ __align__(8) uint64_t bar[kStages];
-    __shared__ int fmt[kStages];  // 1: compressed record + escapes, 0: int32 rows
     __shared__ int ok;
     const int tid = threadIdx.x;
     const int ntiles = (L.n_bulk + kBlock - 1) / kBlock;
     const unsigned np = (unsigned)L.npad;
-    const bool c16 = kUseCompressedTable && L.c16_rec != nullptr;
     auto issue = [&](int stage, int tile) {
         unsigned char *dst = sbuf + stage * SB;
-        const uint32_t cnt = c16 ? L.c16_cnt[tile] : kTileFallback;
-        if (cnt != kTileFallback) {
-            fmt[stage] = 1;
-            mbar_expect_tx(&bar[stage], (unsigned)RB + cnt * 4u);
-            bulk_g2s(dst, L.c16_rec + (size_t)tile * RB, (unsigned)RB, &bar[stage]);
-            if (cnt) bulk_g2s(dst + RB, L.c16_esc + L.c16_off[tile], cnt * 4u, &bar[stage]);
-            return;
-        }
-        fmt[stage] = 0;
         // ragged last tile: round the row up to 16 bytes (stays inside the
         // plane: npad is a multiple of 128 and >= n_bulk)
         const int count = min(kBlock, L.n_bulk - tile * kBlock);
@@ -378,7 +418,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         mbar_expect_tx(&bar[stage], bytes * NE);
 #pragma unroll 1
         for (int i = 0; i < NE; ++i)
-            bulk_g2s(dst + i * kBlock * 4, L.tab + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
+            bulk_g2s(dst + i * kBlock * 4, L.slots + (size_t)i * np + (size_t)tile * kBlock, bytes, &bar[stage]);
     };
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
@@ -389,8 +429,6 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         }
     }
     __syncthreads();
-    const int warp = tid >> 5;
-    const unsigned lt = (1u << (tid & 31)) - 1u;
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int stage = k % kStages;
@@ -407,43 +445,19 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
             return;
         }
         const int x = tile * kBlock + tid;
-        const unsigned char *buf = sbuf + stage * SB;
-        int s[Q];
-        if (kUseCompressedTable && fmt[stage]) {
-            // every thread decodes (the ballots need the whole warp)
-            const int16_t *r16 = reinterpret_cast<const int16_t *>(buf);
-            const uint16_t *pre = reinterpret_cast<const uint16_t *>(buf + NE * kTile * 2);
-            const int32_t *escs = reinterpret_cast<const int32_t *>(buf + RB);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int code = r16[(i - 1) * kTile + tid];
-                const bool esc = code == kCodeEscape;
-                const unsigned m = __ballot_sync(0xffffffffu, esc);
-                s[i] = esc ? escs[pre[(i - 1) * 8 + warp] + __popc(m & lt)]
-                           : (code == kCodeWall ? -1 : x + code);
-            }
-        } else {
-            const int32_t *r32 = reinterpret_cast<const int32_t *>(buf);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) s[i] = r32[(i - 1) * kTile + tid];
-        }
+        // (the rows of a ragged last tile run past n_bulk: only the tile's
+        // sites read them)
         if (x < L.n_bulk) {
-            // (the rows of a ragged last tile run past n_bulk: only the
-            // entries of the tile's sites are checked)
-#pragma unroll
-            for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, s[i]);
+            const uint32_t *rows = reinterpret_cast<const uint32_t *>(sbuf + stage * SB);
             float d[Q];
             d[0] = R::ld(fin + x);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
-                                             : (unsigned)opp(i) * np + (unsigned)x;
-                d[i] = R::ld(fin + e);
-            }
+            for (int i = 1; i < Q; ++i)
+                d[i] = R::ld(fin + checked_slot(L, rows[(i - 1) * kTile + tid], (unsigned)opp(i) * np + (unsigned)x));
             float out[Q];
             collide<Q, HALF>(L, d, out);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
+            for (int i = 0; i < Q; ++i) R::st(out_planes.p[i] + x, out[i]);
         }
         __syncthreads();  // every thread is done with this stage's buffer
         if (tid == 0) {
@@ -464,6 +478,9 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 //   even step: slot_i = A[i][x]                  (own site, no table for bulk sites)
 //   odd step:  slot_i = A[opp(i)][x - c_i]       (through the table), or
 //              A[i][x] for a wall or iolet link opp(i).
+// The bulk sites (IO = false) take the plane pointers P for the even step and
+// the slot table rows S (DevLattice::slots, these very slot_i) for the odd
+// step; the sites with iolet links decode the pull table.
 // After an even step A holds the populations of time t+1 in swapped slots;
 // after an odd step they are back in natural order, A[i][x] = f_i(x).
 #ifndef HGB_AA_MINB_FP32
@@ -474,20 +491,45 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #endif
 template <int Q, bool HALF, bool ODD, bool IO>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
-k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const IoletStep io,
-          const double *__restrict__ rho_io, const IoletStep *__restrict__ io_dev) {
+k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Planes<typename Raw<HALF>::T> P,
+          const SlotRows S, const IoletStep io, const double *__restrict__ rho_io,
+          const IoletStep *__restrict__ io_dev) {
     using R = Raw<HALF>;
     const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
     if (x >= (IO ? L.n : L.n_bulk)) return;
     const unsigned np = (unsigned)L.npad;
-    int s[Q];
-    s[0] = 0;
-    if (ODD || IO) {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
-    }
     float d[Q];
     float out[Q];
+    if (!IO) {
+        // bulk sites: even step on the own slots through the plane pointers,
+        // odd step through the slot table; no table codes, no iolet work
+        if (!ODD) {
+            typename Raw<HALF>::T *a[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) a[i] = P.p[i] + x;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a[i]);
+            collide<Q, HALF>(L, d, out);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) R::st_rw(a[i], out[opp(i)]);
+        } else {
+            unsigned e[Q];
+            e[0] = (unsigned)x;
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                e[i] = checked_slot(L, __ldcs(S.p[i - 1] + x), (unsigned)i * np + (unsigned)x);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + e[i]);
+            collide<Q, HALF>(L, d, out);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) R::st_rw(A + e[i], out[opp(i)]);
+        }
+        return;
+    }
+    int s[Q];
+    s[0] = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
     if (!ODD) {
         // own slots: one base pointer, plane stride np
         typename Raw<HALF>::T *a = A + x;
@@ -558,6 +600,18 @@ inline cudaError_t join_side(cudaStream_t s, cudaStream_t t, const SideStream *s
     return e;
 }
 
+template <typename T>
+Planes<T> planes_of(T *A, int q, int64_t npad) {
+    Planes<T> P{};
+    for (int i = 0; i < q; ++i) P.p[i] = A + (size_t)i * (size_t)npad;
+    return P;
+}
+inline SlotRows slot_rows_of(const DevLattice &L) {
+    SlotRows S{};
+    for (int i = 0; i + 1 < L.q; ++i) S.p[i] = L.slots + (size_t)i * (size_t)L.npad;
+    return S;
+}
+
 template <int Q, bool HALF>
 cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
                          const double *rho_io, cudaStream_t s, const SideStream *side,
@@ -565,12 +619,14 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
+    const Planes<T> P = planes_of((T *)A, Q, L.npad);
+    const SlotRows S = slot_rows_of(L);
     if (odd) {
-        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
-        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io, io_dev);
+        if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
     } else {
-        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, io, rho_io, io_dev);
-        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, io, rho_io, io_dev);
+        if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = join_side(s, t, side);
@@ -587,7 +643,7 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
     if (nb) {
         if (HGB_STEP_STAGED && L.err) {
             static int grid_cache[2] = {0, 0};
-            const size_t smem = (size_t)kStages * stage_bytes<Q>();
+            const size_t smem = (size_t)kStages * (Q - 1) * kTile * 4;
             int &g = grid_cache[HALF ? 1 : 0];
             if (g == 0) {
                 int dev = 0, sms = 0, per = 0;
@@ -599,10 +655,12 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
                     if (e != cudaSuccess) return e;
                 }
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_staged<Q, HALF>, kBlock, smem);
+                if (HGB_STAGED_CTAS > 0) per = std::min(per, HGB_STAGED_CTAS);
                 g = std::max(1, sms * std::max(per, 1));
             }
             const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
-            k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, (T *)fout, L.err);
+            k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, planes_of((T *)fout, Q, L.npad),
+                                                              L.err);
         } else {
             k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
         }
