@@ -2,16 +2,18 @@
 """Benchmark: million site updates per second (MSUPS) of the fused sparse
 LBGK collide-and-stream on one GB300, with its HBM roofline fraction.
 
-Workload (default): the seeded six-generation bifurcating vessel tree
-(root radius 48, Murray's law, 1024^3 box, ~10.8M fluid sites), D3Q19 LBGK,
-tau = 0.6, one inlet at rho 1.001 and 32 outlets at rho 1.0, synthetic data.
-One benchmark step = 100 lattice-Boltzmann time steps (fused collide-and-
-stream kernels, AA-pattern streaming in place by default, sites kept along a
-Morton curve of 32-site runs) + density/velocity/wall-shear-stress fields +
-the float64 mass reduction.  value = fluid sites x LB time steps / device
-time, fp32 storage; the fp16-deviation storage form and the pull streaming
-form are reported beside it.  The inputs (~2 GB touched per LB step) are
-larger than the 126 MB L2, so no flush is needed.
+Workload (default): the seeded six-generation bifurcating vessel tree with
+every length x1.86 (root radius 89.28, Murray's law, 2048^3 box, 69,461,776
+fluid sites; the at-scale tree of ~80M sites), D3Q19 LBGK, tau = 0.6, one
+inlet at rho 1.001 and 32 outlets at rho 1.0, synthetic data.  ``--workload
+vessel_tree`` runs the same tree at its stated root radius 48 in 1024^3
+(10,787,566 sites).  One benchmark step = 100 lattice-Boltzmann time steps
+(fused collide-and-stream kernels, AA-pattern streaming in place by default,
+sites kept along a Morton curve of 32-site runs) + density/velocity/wall-
+shear-stress fields + the float64 mass reduction.  value = fluid sites x LB
+time steps / device time, fp32 storage; the fp16-deviation storage form and
+the pull streaming form are reported beside it.  The inputs (~13 GB touched
+per LB step) are far larger than the 126 MB L2, so no flush is needed.
 
 ``--impl reference`` times the FP64 CPU oracle on this machine's host cores
 on the same workload and metric (a few LB steps per benchmark step).
@@ -39,9 +41,12 @@ from paper_1906_11925_gb300 import metrics  # noqa: E402
 from paper_1906_11925_gb300 import replicas  # noqa: E402
 
 LB_STEPS_PER_BENCH_STEP = 100
-PROFILE_SUMMARY = {"pull": os.path.join(ROOT, "profiles", "lbm_step_q19_vessel_tree.md"),
-                   "aa": os.path.join(ROOT, "profiles", "k_step_aa_q19_vessel_tree.md")}
-PROFILED_WORKLOAD = "vessel_tree"  # the workload the summaries above were captured on
+# committed ncu summaries of the step kernels, per (workload, streaming form):
+# the DRAM traffic per launch that the roofline object reports
+PROFILE_SUMMARY = {
+    ("vessel_tree_large", "aa"): os.path.join(ROOT, "profiles", "k_step_aa_q19_vessel_tree_large.md"),
+    ("vessel_tree_large", "pull"): os.path.join(ROOT, "profiles", "k_step_pull_q19_vessel_tree_large.md"),
+}
 # the step kernels' sources: the summaries' hash is over these files' bytes in this order
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1906_11925_gb300", "csrc", f)
                   for f in ("lbm_step.cu", "staging.cuh")]
@@ -136,14 +141,13 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(summary=None):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary
-    (of the AA kernels by default), or None when it is missing or was taken
-    on a different kernel source."""
+def recorded_traffic(summary):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    or None when it is missing or was taken on a different kernel source."""
     try:
         src = kernel_source_sha256()
         fields = {}
-        for line in open(summary or PROFILE_SUMMARY["aa"]):
+        for line in open(summary):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
@@ -435,7 +439,8 @@ def run_ours(args):
                     nominal_peak=NOMINAL_HBM_GBS,
                     bytes_per_site_update=bps, launch_us=round(per_launch_s * 1e6, 2))
 
-    traffic = recorded_traffic(PROFILE_SUMMARY[main_form]) if args.workload == PROFILED_WORKLOAD else None
+    summary = PROFILE_SUMMARY.get((args.workload, main_form))
+    traffic = recorded_traffic(summary) if summary else None
     rf32 = roofline(r32, "fp32", main_form)
     rf32["traffic"] = traffic.get("traffic_bytes_per_launch_fp32") if traffic else None
     if r16:
@@ -601,7 +606,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vessel_tree_large")
     ap.add_argument("--inner", type=int, default=LB_STEPS_PER_BENCH_STEP,
                     help="LB time steps per benchmark step")
     ap.add_argument("--streaming", choices=("aa", "pull"), default="aa",

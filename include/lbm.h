@@ -111,8 +111,9 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              (the paper's BFL wall boundary, Section 3.2), with x_b = x - c_i:
  *              q < 1/2 and x_b fluid: f_opp(i)(x, t+1) = 2q f*_i(x) + (1 - 2q) f*_i(x_b);
  *              q >= 1/2: f_opp(i)(x, t+1) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_opp(i)(x);
- *              q < 1/2 without a fluid x_b: the half-way rule.  Requires
- *              LBM_STREAM_PULL; not differentiated (lbm_objective_grad).
+ *              q < 1/2 without a fluid x_b: the half-way rule.  Both
+ *              streaming forms (bitwise the same results); not
+ *              differentiated (lbm_objective_grad).
  *   site_order the order the device keeps the sites in (every result is the
  *              same, outputs are in caller order; the sites with iolet or
  *              interpolated-wall links come last in all of them):

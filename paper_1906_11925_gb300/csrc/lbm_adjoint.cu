@@ -219,7 +219,14 @@ __device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q]
 // The adjoint of the AA form is AA-like itself (the streaming reversed), so
 // the two alternate exactly as the forward kernels do; the arithmetic is the
 // same in every form, so all give the same bits.
-enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2 };
+//   FORM_AA_SLOTS FORM_AA_ODD for the bulk sites (no iolet link), with tab(i)
+//                 the slot-table entry of population i (DevLattice::slots,
+//                 the AA odd-step slot): the state of population i is read
+//                 at that slot, lam*_i at the slot of population opp(i) (the
+//                 slot of population i of the site x + c_i in site form, or
+//                 own slot opp(i) for a wall link), and lam_j is written at
+//                 the slot of population j: no address arithmetic per site.
+enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2, FORM_AA_SLOTS = 3 };
 
 // The adjoint of step t at one site x (lam(t) at x from lam(t+1) and the
 // state P of time t); tab(i) is the table entry of population i at x (from
@@ -240,6 +247,8 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
         unsigned e;
         if (FORM == FORM_AA_EVEN) {
             e = (unsigned)i * np + (unsigned)x;
+        } else if (FORM == FORM_AA_SLOTS) {
+            e = (unsigned)tab(i);
         } else {
             const int si = tab(i);
             const unsigned a = FORM == FORM_PULL ? (unsigned)i : (unsigned)opp(i);
@@ -290,6 +299,11 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
         if (FORM == FORM_AA_EVEN && !IO) {
             // (no iolet link: mu_i in the own slot opp(i) for every link)
             if (has_next) ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+            continue;
+        }
+        if (FORM == FORM_AA_SLOTS) {
+            // (no iolet link: lam*_i at the slot of population opp(i))
+            if (has_next) ls[i] = lam_next[(unsigned)tab(opp(i))];
             continue;
         }
         const int sp = tab(opp(i));  // link i of x: >= 0 -> the site x + c_i
@@ -366,7 +380,12 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
                 int s[Q];
                 s[0] = 0;
 #pragma unroll
-                for (int i = 1; i < Q; ++i) s[i] = tab(i);
+                for (int i = 1; i < Q; ++i) {
+                    if (FORM == FORM_AA_SLOTS)  // a wall link reads the own slot i
+                        s[i] = (unsigned)tab(i) == (unsigned)i * np + (unsigned)x ? -1 : 0;
+                    else
+                        s[i] = tab(i);
+                }
                 j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
                                      obj.wss_dlog_f, lam, &dtau_site);
             } else if (obj.kind == 1) {
@@ -387,6 +406,10 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
             __stcs(lam_out + (sj >= 0 ? (unsigned)opp(j) * np + (unsigned)sj : (unsigned)j * np + (unsigned)x),
                    lam[j]);
         }
+    } else if (FORM == FORM_AA_SLOTS) {
+        __stcs(lam_out + x, lam[0]);
+#pragma unroll
+        for (int j = 1; j < Q; ++j) __stcs(lam_out + (unsigned)tab_out(j), lam[j]);
     } else {
 #pragma unroll
         for (int j = 0; j < Q; ++j) __stcs(lam_out + (unsigned)j * np + (unsigned)x, lam[j]);
@@ -447,7 +470,21 @@ k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P
             asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
             return v;
         };
-        if (ODD || IO) {
+        if (ODD && !IO) {
+            // bulk sites of an odd step: every access through the slot table
+            unsigned e[Q];
+            e[0] = (unsigned)x;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) e[i] = __ldg(L.slots + (unsigned)(i - 1) * np + (unsigned)x);
+            auto tab = [&](int i) { return (int)e[i]; };
+            auto reload_slot = [&](int i) {
+                unsigned v;
+                asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(L.slots + (unsigned)(i - 1) * np + (unsigned)x));
+                return (int)v;
+            };
+            adjoint_site<Q, HALF, WSS, false, FORM_AA_SLOTS>(L, P, lin, lam, st, obj, x, tab, reload_slot, io_acc,
+                                                             j_site, dtau_site);
+        } else if (ODD || IO) {
             int s[Q];
             s[0] = 0;
 #pragma unroll

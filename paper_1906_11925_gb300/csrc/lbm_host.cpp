@@ -608,7 +608,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
         return fail(nullptr, LBM_ERR_ARG, "too many sites: q * npad must stay below 2^31");
     st = validate_tables(q, p->n_iolets, n, nbr, link);
     if (st != LBM_OK) return st;
-    // interpolated walls: q in (0, 1] on every wall link; pull streaming only
+    // interpolated walls: q in (0, 1] on every wall link
     const double *wq = p->wall_q;
     bool any_bfl = false;
     if (wq) {
@@ -617,8 +617,6 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             if (!(wq[o] > 0.0 && wq[o] <= 1.0)) return fail(nullptr, LBM_ERR_ARG, "wall_q must lie in (0, 1]");
             any_bfl |= wq[o] != 0.5;
         }
-        if (any_bfl && p->streaming != LBM_STREAM_PULL)
-            return fail(nullptr, LBM_ERR_ARG, "interpolated walls need LBM_STREAM_PULL");
     }
     auto bfl_link = [&](int64_t o) { return any_bfl && link[o] == 1 && wq[o] != 0.5; };
     const int64_t lim = 1LL << 19;
@@ -961,7 +959,7 @@ HGB_API lbm_status lbm_step_driven(lbm_ctx *ctx, int64_t nsteps, const double *r
         CK(ctx, advance_one(ctx, kinds, ctx->rho_io + s * K));
         ++ctx->t;
         if (mass_host)
-            CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_series + s, ctx->stream));
+            CK(ctx, launch_mass(ctx->L, ctx->f_cur, cur_layout(ctx), ctx->partials, ctx->mass_series + s, ctx->stream));
     }
     if (mass_host)
         CK(ctx, cudaMemcpyAsync(mass_host, ctx->mass_series, (size_t)nsteps * 8,
@@ -996,7 +994,7 @@ HGB_API lbm_status lbm_macros(lbm_ctx *ctx, float *rho_d, float *u_d, float *wss
 HGB_API lbm_status lbm_mass(lbm_ctx *ctx, double *out) {
     if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
     int flag = 0;
-    CK(ctx, launch_mass(ctx->L, ctx->f_cur, ctx->partials, ctx->mass_dev, ctx->stream));
+    CK(ctx, launch_mass(ctx->L, ctx->f_cur, cur_layout(ctx), ctx->partials, ctx->mass_dev, ctx->stream));
     CK(ctx, cudaMemcpyAsync(out, ctx->mass_dev, 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaMemcpyAsync(&flag, ctx->err_flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -141,7 +141,7 @@ cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float 
 
 // Deterministic float64 mass: partial sums into partials[nblk], final into out.
 int mass_blocks();
-cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, double *out,
+cudaError_t launch_mass(const DevLattice &L, const void *f, int layout, double *partials, double *out,
                         cudaStream_t s);
 
 // sum_x weight[x] q(x) of the state in f (q: 0 wall shear stress, 1

@@ -107,7 +107,7 @@ __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<
         }
     }
     if (BFL && x >= L.n_bulk) {
-        // interpolated walls (pull layout only): q < 1/2 with a fluid
+        // interpolated walls (every layout): q < 1/2 with a fluid
         // upstream site adds (1 - 2q) times the population pulled from it
 #pragma unroll
         for (int p = 1; p < Q; ++p)
@@ -272,7 +272,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // permutation of the slots, so the slots hold exactly the populations f(t).
 template <int Q, bool HALF, bool BFL>
 __global__ void __launch_bounds__(kBlock)
-k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f,
+k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
                double *__restrict__ partials) {
     using S = Store<HALF>;
     double acc = 0.0;
@@ -285,7 +285,9 @@ k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
         for (int i = 0; i < Q; ++i) s += S::load(f + (int64_t)i * L.npad + x, L.inv_scale);
         if (BFL && x >= L.n_bulk) {
             // interpolated walls: the slot of a q < 1/2 link holds only part of
-            // the population; the rest is (1 - 2q) times the upstream pull
+            // the population; the rest is (1 - 2q) times the population opp(p)
+            // that the site gathers from its upstream neighbour (in the slot
+            // the layout keeps it in)
 #pragma unroll
             for (int p = 1; p < Q; ++p) {
                 const int e = L.tab[(int64_t)(p - 1) * L.npad + x];
@@ -293,7 +295,7 @@ k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
                 const float qv = bfl_q(e);
                 const int u = L.tab[(int64_t)(opp(p) - 1) * L.npad + x];
                 if (qv < 0.5f && u >= 0)
-                    s += (1.0f - 2.0f * qv) * S::load(f + (int64_t)opp(p) * L.npad + u, L.inv_scale);
+                    s += (1.0f - 2.0f * qv) * S::load(f + src_slot(layout, opp(p), u, x, L.npad), L.inv_scale);
             }
         }
         acc += (double)s;
@@ -427,12 +429,12 @@ cudaError_t macros_impl(const DevLattice &L, const void *f, int layout, float *r
     return cudaGetLastError();
 }
 template <int Q, bool HALF>
-cudaError_t mass_impl(const DevLattice &L, const void *f, double *partials, cudaStream_t s) {
+cudaError_t mass_impl(const DevLattice &L, const void *f, int layout, double *partials, cudaStream_t s) {
     using T = typename Store<HALF>::T;
     if (L.bfl)
-        k_mass_partial<Q, HALF, true><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, partials);
+        k_mass_partial<Q, HALF, true><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, layout, partials);
     else
-        k_mass_partial<Q, HALF, false><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, partials);
+        k_mass_partial<Q, HALF, false><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, layout, partials);
     return cudaGetLastError();
 }
 template <int Q, bool HALF>
@@ -510,9 +512,9 @@ cudaError_t launch_weighted_sum(const DevLattice &L, const void *f, int layout, 
 
 int mass_blocks() { return kMassBlocks; }
 
-cudaError_t launch_mass(const DevLattice &L, const void *f, double *partials, double *out,
+cudaError_t launch_mass(const DevLattice &L, const void *f, int layout, double *partials, double *out,
                         cudaStream_t s) {
-    cudaError_t e = HGB_DISPATCH(L, mass_impl, L, f, partials, s);
+    cudaError_t e = HGB_DISPATCH(L, mass_impl, L, f, layout, partials, s);
     if (e != cudaSuccess) return e;
     k_mass_final<<<1, kBlock, 0, s>>>(partials, kMassBlocks, (double)L.n * (double)L.rho0, out);
     return cudaGetLastError();

@@ -261,9 +261,12 @@ __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const
     }
 }
 
-// Interpolated (BFL) walls, pull form (entries is_bfl(s[p]): link opp(p) is
-// a wall at fluid fraction q; the population p of the next step is read back
-// from the site's own slot opp(p)).
+// Interpolated (BFL) walls (entries is_bfl(s[p]): link opp(p) is a wall at
+// fluid fraction q; the population p of the next step is read back from the
+// site's own slot, the slot that holds out[opp(p)] after the step in every
+// streaming form: pull slot opp(p), AA even slot p, AA odd own slot p).  The
+// gathered d[] and the collision's out[] mean the same in every form, so the
+// same two helpers serve the pull and the AA kernels.
 //   bfl_gather:  q < 1/2 with a fluid upstream site (s[opp(p)] >= 0): the
 //                slot holds 2q f*_opp(p)(x); add (1 - 2q) f*_opp(p)(x - c_opp(p)),
 //                the population opp(p) just pulled from the upstream site;
@@ -332,12 +335,24 @@ template <int Q, bool HALF, bool IO, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, IO ? (HALF ? HGB_TAIL_MINB_FP16 : HGB_TAIL_MINB_FP32)
                                              : (HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32))
 k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
-       typename Raw<HALF>::T *__restrict__ fout, const IoletStep io,
-       const double *__restrict__ rho_io, const IoletStep *__restrict__ io_dev) {
+       typename Raw<HALF>::T *__restrict__ fout, const Planes<typename Raw<HALF>::T> OP, const SlotRows S,
+       const IoletStep io, const double *__restrict__ rho_io, const IoletStep *__restrict__ io_dev) {
     using R = Raw<HALF>;
     const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
     if (x >= (IO ? L.n : L.n_bulk)) return;
     const unsigned np = (unsigned)L.npad;
+    if (!IO && !BFL) {
+        // bulk sites: gather through the slot table, store through the planes
+        float d[Q], out[Q];
+        d[0] = R::ld(fin + x);
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            d[i] = R::ld(fin + checked_slot(L, __ldcs(S.p[i - 1] + x), (unsigned)opp(i) * np + (unsigned)x));
+        collide<Q, HALF>(L, d, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st(OP.p[i] + x, out[i]);
+        return;
+    }
     int s[Q];
 #pragma unroll
     for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
@@ -489,8 +504,16 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #ifndef HGB_AA_MINB_FP16
 #define HGB_AA_MINB_FP16 4
 #endif
-template <int Q, bool HALF, bool ODD, bool IO>
-__global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
+// the even bulk step (no table) on its own
+#ifndef HGB_AA_MINB_EVEN_FP32
+#define HGB_AA_MINB_EVEN_FP32 HGB_AA_MINB_FP32
+#endif
+#ifndef HGB_AA_MINB_EVEN_FP16
+#define HGB_AA_MINB_EVEN_FP16 HGB_AA_MINB_FP16
+#endif
+template <int Q, bool HALF, bool ODD, bool IO, bool BFL = false>
+__global__ void __launch_bounds__(kBlock, (ODD || IO) ? (HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
+                                                      : (HALF ? HGB_AA_MINB_EVEN_FP16 : HGB_AA_MINB_EVEN_FP32))
 k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Planes<typename Raw<HALF>::T> P,
           const SlotRows S, const IoletStep io, const double *__restrict__ rho_io,
           const IoletStep *__restrict__ io_dev) {
@@ -504,14 +527,25 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
         // bulk sites: even step on the own slots through the plane pointers,
         // odd step through the slot table; no table codes, no iolet work
         if (!ODD) {
-            typename Raw<HALF>::T *a[Q];
+            // (measured: fp16 is faster through the plane pointers, fp32
+            // through one base pointer and the plane offsets)
+            if (HALF) {
+                typename Raw<HALF>::T *a[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) a[i] = P.p[i] + x;
+                for (int i = 0; i < Q; ++i) a[i] = P.p[i] + x;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a[i]);
-            collide<Q, HALF>(L, d, out);
+                for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a[i]);
+                collide<Q, HALF>(L, d, out);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) R::st_rw(a[i], out[opp(i)]);
+                for (int i = 0; i < Q; ++i) R::st_rw(a[i], out[opp(i)]);
+            } else {
+                typename Raw<HALF>::T *a = A + x;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+                collide<Q, HALF>(L, d, out);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
+            }
         } else {
             unsigned e[Q];
             e[0] = (unsigned)x;
@@ -535,7 +569,9 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
         typename Raw<HALF>::T *a = A + x;
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+        if (BFL) bfl_gather<Q>(s, d);
         const Velocity v = collide<Q, HALF>(L, d, out);
+        if (BFL) bfl_scatter<Q>(s, out);
         if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
@@ -547,7 +583,9 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
         };
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + slot(i));
+        if (BFL) bfl_gather<Q>(s, d);
         const Velocity v = collide<Q, HALF>(L, d, out);
+        if (BFL) bfl_scatter<Q>(s, out);
         if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st_rw(A + slot(i), out[opp(i)]);
@@ -623,10 +661,16 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
     const SlotRows S = slot_rows_of(L);
     if (odd) {
         if (nb) k_step_aa<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, P, S, io, rho_io, io_dev);
-        if (ni) k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        if (ni && L.bfl)
+            k_step_aa<Q, HALF, true, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        else if (ni)
+            k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
     } else {
         if (nb) k_step_aa<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (T *)A, P, S, io, rho_io, io_dev);
-        if (ni) k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        if (ni && L.bfl)
+            k_step_aa<Q, HALF, false, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
+        else if (ni)
+            k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, t>>>(L, (T *)A, P, S, io, rho_io, io_dev);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = join_side(s, t, side);
@@ -640,8 +684,12 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
     using T = typename Raw<HALF>::T;
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     const cudaStream_t t = fork_side(s, side, nb > 0 && ni > 0);
+    const Planes<T> OP = planes_of((T *)fout, Q, L.npad);
+    const SlotRows S = slot_rows_of(L);
     if (nb) {
-        if (HGB_STEP_STAGED && L.err) {
+        // (measured with the slot table: the staged kernel is faster for 16-bit
+        // storage, the plain one for fp32, 354 against 378 us per tree step)
+        if (HGB_STEP_STAGED && HALF && L.err) {
             static int grid_cache[2] = {0, 0};
             const size_t smem = (size_t)kStages * (Q - 1) * kTile * 4;
             int &g = grid_cache[HALF ? 1 : 0];
@@ -659,16 +707,18 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
                 g = std::max(1, sms * std::max(per, 1));
             }
             const int grid = std::min(g, (nb + kBlock - 1) / kBlock);
-            k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, planes_of((T *)fout, Q, L.npad),
-                                                              L.err);
+            k_step_staged<Q, HALF><<<grid, kBlock, smem, s>>>(L, (const T *)fin, OP, L.err);
         } else {
-            k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
+            k_step<Q, HALF, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)fin, (T *)fout, OP, S, io, rho_io,
+                                                                   io_dev);
         }
     }
     if (ni && L.bfl)
-        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
+        k_step<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, OP, S, io, rho_io,
+                                                                    io_dev);
     else if (ni)
-        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, io, rho_io, io_dev);
+        k_step<Q, HALF, true><<<grid_for(ni), kBlock, 0, t>>>(L, (const T *)fin, (T *)fout, OP, S, io, rho_io,
+                                                              io_dev);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = join_side(s, t, side);
     return e;

@@ -21,6 +21,13 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU containers
 FP32, FP16 = lbm.STORE_FP32, lbm.STORE_FP16
 TOL_MACRO = {FP32: 1e-5, FP16: 2e-3}
 TOL_POP = {FP32: 1e-5, FP16: 2e-3}
+# Wall shear stress is formed from g_i - feq_i, the non-equilibrium part of
+# the populations, about a tenth of the stored deviations next to the walls
+# of these flows.  A storage rounding of relative size e on the deviations
+# (fp32: 2^-24; fp16: at most 2^-11 = 4.9e-4) therefore reaches the WSS
+# amplified about tenfold: fp32 stays far below the 1e-5 bar of the other
+# fields, fp16 below 5e-3 (measured: 2e-7 and 0.9e-3 on the straight tube).
+TOL_WSS = {FP32: 1e-5, FP16: 5e-3}
 
 
 def rel_l2(a, b):
@@ -86,16 +93,20 @@ def test_tube_poiseuille_1000_steps(storage):
     L, nbr, link = make(g, q, tau, storage)
     L.step(1000)
     rho, u, wss = [t.cpu().numpy() for t in L.macros()]
+    # rho - rho0 summed in float64 from the stored populations (the float32
+    # density of lbm_macros resolves rho near 1 only to 6e-8)
+    drho = L.get_populations().sum(axis=0) - 1.0
     f = oracle.run(q, nbr, link, tau, oracle.rest_state(q, g.n), 1000, geom=g)
     orho, ou, owss = oracle.macros(q, link, tau, f)
     e_u = rel_l2(u, ou)
     e_rho = rel_l2(rho, orho)
-    e_drho = rel_l2(rho - 1.0, orho - 1.0)
+    e_drho = rel_l2(drho, orho - 1.0)
     e_wss = rel_l2(wss, owss)
     print("storage", storage, "u", e_u, "rho", e_rho, "rho-1", e_drho, "wss", e_wss)
     assert e_u <= TOL_MACRO[storage]
     assert e_rho <= TOL_MACRO[storage]
-    assert e_wss <= {FP32: 1e-4, FP16: 5e-2}[storage]
+    assert e_drho <= TOL_MACRO[storage]
+    assert e_wss <= TOL_WSS[storage]
 
 
 @pytest.mark.parametrize("q", [15, 19])
