@@ -68,6 +68,13 @@ def _bind(path: str):
     lib.orc_objective_run.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, i64, i64, P, i32, P,
                                       i64, i64, f64]
     lib.orc_objective_run.restype = f64
+    lib.orc_adjoint_step_bc.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, P, P, P, P, i64, P, P, P, P,
+                                        P, P, P]
+    lib.orc_gradient_bc.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, P, P, P, P, i64, i64, P, i32, P,
+                                    i64, i64, f64, P, P, P, P, P, P]
+    lib.orc_objective_run_bc.argtypes = [i32, i64, P, P, f64, i32, P, P, P, P, P, P, P, P, i64, i64, P, i32,
+                                         P, i64, i64, f64]
+    lib.orc_objective_run_bc.restype = f64
     lib.orc_render.argtypes = [P, i32, i32, i32, i32, i32, P, P, P, f64, f64, f64, f64, f64, P, P]
     lib.orc_render_pixels.argtypes = [P, i32, i32, i32, i32, i32, P, P, P, f64, f64, f64, f64,
                                       f64, P, i64, P, P]
@@ -95,6 +102,15 @@ class _Iolets:
         self.amp = _c(amp if (k and amp is not None) else z, np.float64)
         self.period = _c(period if (k and period is not None) else z, np.float64)
         self.phase = _c(phase if (k and phase is not None) else z, np.float64)
+
+
+def _bc(q, n, io_kind=None, io_normal=None, weight=None, wall_q=None):
+    """The boundary arrays of orc_step_bc (None where absent)."""
+    kind = None if io_kind is None else _c(io_kind, np.int32)
+    nrm = None if io_normal is None else _c(io_normal, np.float64).reshape(-1, 3)
+    w = None if weight is None else _c(weight, np.float64)
+    wq = None if wall_q is None else _c(wall_q, np.float64).reshape(q, n)
+    return kind, nrm, w, wq
 
 
 class Oracle:
@@ -229,22 +245,26 @@ class Oracle:
     OBJ_WSS = 0
     OBJ_DENSITY = 1
 
-    def adjoint_step(self, q, nbr, link, tau, f, lam_next, t=0, geom=None, **io):
-        """lam(t) = (dF_t/df)^T lam(t+1) at the state f = f(t); returns
-        (lam, dJ/dtau, dJ/dmean[K], dJ/damp[K], dJ/dphase[K]) of this step."""
+    def adjoint_step(self, q, nbr, link, tau, f, lam_next, t=0, geom=None, io_kind=None, io_normal=None,
+                     weight=None, wall_q=None, **io):
+        """lam(t) = (dF_t/df)^T lam(t+1) at the state f = f(t) (the boundary
+        arguments as in run_bc); returns (lam, dJ/dtau, dJ/dmean[K],
+        dJ/damp[K], dJ/dphase[K]) of this step."""
         nbr = _c(nbr, np.int32)
         link = _c(link, np.uint8)
         f = _c(f, np.float64)
         ln = _c(lam_next, np.float64)
         n = f.shape[1]
         I = _Iolets(geom, **io)
+        kind, nrm, w, wq = _bc(q, n, io_kind, io_normal, weight, wall_q)
         lam = np.empty_like(f)
         dtau = np.zeros(1)
         K = max(I.k, 1)
         dm, da, dp = np.zeros(K), np.zeros(K), np.zeros(K)
-        r = self.lib.orc_adjoint_step(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean),
-                                      _p(I.amp), _p(I.period), _p(I.phase), int(t), _p(f), _p(ln),
-                                      _p(lam), _p(dtau), _p(dm), _p(da), _p(dp))
+        r = self.lib.orc_adjoint_step_bc(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean),
+                                         _p(I.amp), _p(I.period), _p(I.phase), _p(kind), _p(nrm), _p(w),
+                                         _p(wq), int(t), _p(f), _p(ln), _p(lam), _p(dtau), _p(dm), _p(da),
+                                         _p(dp))
         if r != 0:
             raise ValueError("orc_adjoint_step failed")
         return lam, float(dtau[0]), dm[:I.k], da[:I.k], dp[:I.k]
@@ -263,7 +283,8 @@ class Oracle:
         return (J, lam, float(dtau[0])) if grad else J
 
     def gradient(self, q, nbr, link, tau, f0, nsteps, kind, m, t_begin, t_end, scale=1.0,
-                 t0=0, geom=None, want_lam0=False, **io):
+                 t0=0, geom=None, want_lam0=False, io_kind=None, io_normal=None, weight=None,
+                 wall_q=None, **io):
         """Objective J = scale * sum_{t_begin <= t < t_end} sum_x m_x q(x, t) over
         the states of an nsteps run from f0 at time t0, and its gradient by the
         discrete adjoint (every state stored).  Returns a dict with J, dtau,
@@ -274,14 +295,15 @@ class Oracle:
         m = _c(m, np.float64)
         n = f0.shape[1]
         I = _Iolets(geom, **io)
+        bk, bn, bw, bq = _bc(q, n, io_kind, io_normal, weight, wall_q)
         K = max(I.k, 1)
         J, dtau = np.zeros(1), np.zeros(1)
         dm, da, dp = np.zeros(K), np.zeros(K), np.zeros(K)
         lam0 = np.zeros_like(f0) if want_lam0 else None
-        r = self.lib.orc_gradient(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
-                                  _p(I.period), _p(I.phase), int(t0), int(nsteps), _p(f0),
-                                  int(kind), _p(m), int(t_begin), int(t_end), float(scale),
-                                  _p(J), _p(dtau), _p(dm), _p(da), _p(dp), _p(lam0))
+        r = self.lib.orc_gradient_bc(q, n, _p(nbr), _p(link), float(tau), I.k, _p(I.mean), _p(I.amp),
+                                     _p(I.period), _p(I.phase), _p(bk), _p(bn), _p(bw), _p(bq), int(t0),
+                                     int(nsteps), _p(f0), int(kind), _p(m), int(t_begin), int(t_end),
+                                     float(scale), _p(J), _p(dtau), _p(dm), _p(da), _p(dp), _p(lam0))
         if r != 0:
             raise ValueError("orc_gradient failed")
         out = dict(J=float(J[0]), dtau=float(dtau[0]), dmean=dm[:I.k], damp=da[:I.k],
@@ -291,17 +313,19 @@ class Oracle:
         return out
 
     def objective_run(self, q, nbr, link, tau, f0, nsteps, kind, m, t_begin, t_end, scale=1.0,
-                      t0=0, geom=None, **io):
+                      t0=0, geom=None, io_kind=None, io_normal=None, weight=None, wall_q=None, **io):
         """J alone, by running forward in C (used for finite differences)."""
         nbr = _c(nbr, np.int32)
         link = _c(link, np.uint8)
         f0 = _c(f0, np.float64)
         m = _c(m, np.float64)
         I = _Iolets(geom, **io)
-        return float(self.lib.orc_objective_run(q, f0.shape[1], _p(nbr), _p(link), float(tau), I.k,
-                                                _p(I.mean), _p(I.amp), _p(I.period), _p(I.phase),
-                                                int(t0), int(nsteps), _p(f0), int(kind), _p(m),
-                                                int(t_begin), int(t_end), float(scale)))
+        bk, bn, bw, bq = _bc(q, f0.shape[1], io_kind, io_normal, weight, wall_q)
+        return float(self.lib.orc_objective_run_bc(q, f0.shape[1], _p(nbr), _p(link), float(tau), I.k,
+                                                   _p(I.mean), _p(I.amp), _p(I.period), _p(I.phase),
+                                                   _p(bk), _p(bn), _p(bw), _p(bq), int(t0), int(nsteps),
+                                                   _p(f0), int(kind), _p(m), int(t_begin), int(t_end),
+                                                   float(scale)))
 
     def render(self, vol, width, height, eye, center, up, fov_y, dt, tf_scale, tf_offset, lut,
                a_stop=0.99):

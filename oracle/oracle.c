@@ -449,67 +449,136 @@ static void dfeq_du(const lattice_t *L, int i, double rho, const double u[3], do
     for (int a = 0; a < 3; ++a) out[a] = L->w[i] * rho * (3.0 * L->e[i][a] + 9.0 * cu * L->e[i][a] - 3.0 * u[a]);
 }
 
-int orc_adjoint_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
-                     int n_io, const double *rho_mean, const double *amp, const double *period,
-                     const double *phase, int64_t t, const double *f, const double *lam_next,
-                     double *lam, double *dtau, double *dmean, double *damp, double *dphase) {
+/* The adjoint of orc_step_bc, with velocity iolets and interpolated walls.
+ * Every outgoing population f*_i(x) enters the next state through its link
+ * (see orc_step_bc); lam*_i(x) collects lam of every population it feeds,
+ * with the same weights:
+ *   fluid link:             lam*_i(x)    += lam_i(x + c_i)
+ *   half-way wall:          lam*_i(x)    += lam_opp(i)(x)
+ *   BFL wall, q < 1/2, xb = x - c_i fluid:
+ *                           lam*_i(x)    += 2q lam_opp(i)(x),
+ *                           lam*_i(xb)   += (1 - 2q) lam_opp(i)(x)
+ *   BFL wall, q >= 1/2:     lam*_i(x)    += lam_opp(i)(x) / (2q),
+ *                           lam*_opp(i)(x) += (1 - 1/(2q)) lam_opp(i)(x)
+ *   velocity iolet k:       lam*_i(x)    += lam_opp(i)(x), and the moving-wall
+ *     term -6 w_i rho c_i.u_b (u_b = weight(x) U_k(t) n_k) feeds back through
+ *     rho: every lam_j(x) gains -6 w_i (c_i.u_b) lam_opp(i)(x), and
+ *     dJ/dU_k(t) gains -6 w_i rho weight(x) (c_i.n_k) lam_opp(i)(x);
+ *   density iolet:          as in orc_adjoint_step.
+ * Because the BFL upstream term adds to another site, all lam* are formed
+ * first (a pass over the sites), then each site's collision is reversed. */
+static void chain_schedule(int k, int64_t t, const double *amp, const double *period,
+                           const double *phase, double d, double *dmean, double *damp, double *dphase) {
+    dmean[k] += d;
+    if (period[k] != 0.0 && amp[k] != 0.0) {
+        double arg = 2.0 * M_PI * (double)t / period[k] + phase[k];
+        damp[k] += d * sin(arg);
+        dphase[k] += d * amp[k] * cos(arg);
+    } else if (period[k] != 0.0) {
+        damp[k] += d * sin(2.0 * M_PI * (double)t / period[k] + phase[k]);
+    }
+}
+
+int orc_adjoint_step_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                        int n_io, const double *rho_mean, const double *amp, const double *period,
+                        const double *phase, const int32_t *io_kind, const double *io_normal,
+                        const double *weight, const double *wall_q, int64_t t, const double *f,
+                        const double *lam_next, double *lam, double *dtau, double *dmean,
+                        double *damp, double *dphase) {
     lattice_t L;
     if (get_lattice(q, &L)) return -1;
     const double om = 1.0 / tau;
+    const size_t sz = (size_t)q * (size_t)n;
+    double *ls = (double *)calloc(sz ? sz : 1, sizeof(double));    /* lam*[i][x] */
+    double *gu = (double *)calloc(n ? 3 * (size_t)n : 1, sizeof(double)); /* density-iolet term */
+    double *gv = (double *)calloc(n ? (size_t)n : 1, sizeof(double));     /* velocity-iolet term */
+    if (!ls || !gu || !gv) { free(ls); free(gu); free(gv); return -5; }
+    for (int64_t x = 0; x < n; ++x) {
+        double g[19], rho, u[3];
+        for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
+        moments(&L, g, &rho, u);
+        for (int i = 0; i < q; ++i) {
+            const int64_t o = (int64_t)L.opp[i] * n + x;  /* slot of population opp(i) at x */
+            const int lk = link[(int64_t)i * n + x];
+            if (lk == 0) {
+                ls[(int64_t)i * n + x] += lam_next[(int64_t)i * n + nbr[(int64_t)i * n + x]];
+            } else if (lk == 1) {
+                const double qw = wall_q ? wall_q[(int64_t)i * n + x] : 0.5;
+                const double lo = lam_next[o];
+                if (qw == 0.5) {
+                    ls[(int64_t)i * n + x] += lo;
+                } else if (qw < 0.5) {
+                    if (link[o] == 0) {
+                        ls[(int64_t)i * n + x] += 2.0 * qw * lo;
+                        ls[(int64_t)i * n + nbr[o]] += (1.0 - 2.0 * qw) * lo;
+                    } else {
+                        ls[(int64_t)i * n + x] += lo;
+                    }
+                } else {
+                    ls[(int64_t)i * n + x] += lo / (2.0 * qw);
+                    ls[o] += (1.0 - 1.0 / (2.0 * qw)) * lo;
+                }
+            } else if (io_kind && io_kind[lk - 2] == 1) {
+                const int k = lk - 2;
+                const double lo = lam_next[o];
+                const double U = iolet_rho(k, t, rho_mean, amp, period, phase);
+                const double wx = weight ? weight[x] : 1.0;
+                double cn = 0.0;
+                for (int a = 0; a < 3; ++a) cn += L.e[i][a] * io_normal[3 * k + a];
+                ls[(int64_t)i * n + x] += lo;
+                gv[x] += -6.0 * L.w[i] * wx * U * cn * lo;
+                chain_schedule(k, t, amp, period, phase, -6.0 * L.w[i] * rho * wx * cn * lo, dmean, damp, dphase);
+            } else {
+                const int k = lk - 2, oi = L.opp[i];
+                const double lo = lam_next[o];
+                const double rk = iolet_rho(k, t, rho_mean, amp, period, phase);
+                double feq_k[19], d[3];
+                equilibrium(&L, rk, u, feq_k);
+                dfeq_du(&L, oi, rk, u, d);
+                for (int a = 0; a < 3; ++a) gu[3 * x + a] += lo * d[a];
+                chain_schedule(k, t, amp, period, phase, lo * feq_k[oi] / rk, dmean, damp, dphase);
+            }
+        }
+    }
     double acc_tau = 0.0;
     for (int64_t x = 0; x < n; ++x) {
-        double g[19], feq[19], ls[19], rho, u[3];
+        double g[19], feq[19], rho, u[3];
         for (int i = 0; i < q; ++i) g[i] = f[(int64_t)i * n + x];
         moments(&L, g, &rho, u);
         equilibrium(&L, rho, u, feq);
-        double gu[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < q; ++i) {
-            int lk = link[(int64_t)i * n + x];
-            if (lk == 0) {
-                ls[i] = lam_next[(int64_t)i * n + nbr[(int64_t)i * n + x]];
-            } else if (lk == 1) {
-                ls[i] = lam_next[(int64_t)L.opp[i] * n + x];
-            } else {
-                int k = lk - 2, o = L.opp[i];
-                double lo = lam_next[(int64_t)o * n + x];
-                double rk = iolet_rho(k, t, rho_mean, amp, period, phase);
-                double feq_k[19], d[3];
-                equilibrium(&L, rk, u, feq_k);
-                dfeq_du(&L, o, rk, u, d);
-                for (int a = 0; a < 3; ++a) gu[a] += lo * d[a];
-                double drk = lo * feq_k[o] / rk;
-                dmean[k] += drk;
-                if (period[k] != 0.0 && amp[k] != 0.0) {
-                    double arg = 2.0 * M_PI * (double)t / period[k] + phase[k];
-                    damp[k] += drk * sin(arg);
-                    dphase[k] += drk * amp[k] * cos(arg);
-                } else if (period[k] != 0.0) {
-                    damp[k] += drk * sin(2.0 * M_PI * (double)t / period[k] + phase[k]);
-                }
-                ls[i] = 0.0;
-            }
-        }
         double a = 0.0, b[3] = {0.0, 0.0, 0.0};
         for (int i = 0; i < q; ++i) {
+            const double li = ls[(int64_t)i * n + x];
             double d[3];
-            a += ls[i] * feq[i] / rho;
+            a += li * feq[i] / rho;
             dfeq_du(&L, i, rho, u, d);
-            for (int c = 0; c < 3; ++c) b[c] += ls[i] * d[c];
-            acc_tau += ls[i] * (g[i] - feq[i]) / (tau * tau);
+            for (int c = 0; c < 3; ++c) b[c] += li * d[c];
+            acc_tau += li * (g[i] - feq[i]) / (tau * tau);
         }
         for (int j = 0; j < q; ++j) {
             double s = a, h = 0.0;
             for (int c = 0; c < 3; ++c) {
                 double dj = (L.e[j][c] - u[c]) / rho;
                 s += b[c] * dj;
-                h += gu[c] * dj;
+                h += gu[3 * x + c] * dj;
             }
-            lam[(int64_t)j * n + x] = (1.0 - om) * ls[j] + om * s + h;
+            lam[(int64_t)j * n + x] = (1.0 - om) * ls[(int64_t)j * n + x] + om * s + h + gv[x];
         }
     }
     *dtau += acc_tau;
+    free(ls);
+    free(gu);
+    free(gv);
     (void)n_io;
     return 0;
+}
+
+int orc_adjoint_step(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                     int n_io, const double *rho_mean, const double *amp, const double *period,
+                     const double *phase, int64_t t, const double *f, const double *lam_next,
+                     double *lam, double *dtau, double *dmean, double *damp, double *dphase) {
+    return orc_adjoint_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
+                               NULL, t, f, lam_next, lam, dtau, dmean, damp, dphase);
 }
 
 /* Objective terms.  kind 0: wall shear stress (as orc_macros), kind 1:
@@ -602,11 +671,16 @@ double orc_objective(int q, int64_t n, const uint8_t *link, double tau, int kind
  * Outputs: J, dJ/dtau, per-iolet dJ/dmean, dJ/damp, dJ/dphase ([n_io] each,
  * overwritten) and, if lam0 != NULL, dJ/df(t0) ([q][n]).
  */
-int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
-                 int n_io, const double *rho_mean, const double *amp, const double *period,
-                 const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
-                 const double *m, int64_t t_begin, int64_t t_end, double scale, double *J_out,
-                 double *dtau_out, double *dmean, double *damp, double *dphase, double *lam0) {
+/* Objective and gradient over a run, with velocity iolets and interpolated
+ * walls (io_kind, io_normal, weight, wall_q as in orc_step_bc; all NULL: the
+ * plain step). */
+int orc_gradient_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                    int n_io, const double *rho_mean, const double *amp, const double *period,
+                    const double *phase, const int32_t *io_kind, const double *io_normal,
+                    const double *weight, const double *wall_q, int64_t t0, int64_t nsteps,
+                    const double *f0, int kind, const double *m, int64_t t_begin, int64_t t_end,
+                    double scale, double *J_out, double *dtau_out, double *dmean, double *damp,
+                    double *dphase, double *lam0) {
     const size_t sz = (size_t)q * (size_t)n;
     double *states = (double *)malloc(sizeof(double) * sz * (size_t)(nsteps + 1));
     double *la = (double *)malloc(sizeof(double) * (sz ? sz : 1));
@@ -614,8 +688,8 @@ int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, doub
     if (!states || !la || !lb) { free(states); free(la); free(lb); return -5; }
     memcpy(states, f0, sizeof(double) * sz);
     for (int64_t s = 0; s < nsteps; ++s) {
-        int r = orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t0 + s,
-                         states + sz * (size_t)s, states + sz * (size_t)(s + 1));
+        int r = orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, io_kind, io_normal,
+                            weight, wall_q, t0 + s, states + sz * (size_t)s, states + sz * (size_t)(s + 1));
         if (r) { free(states); free(la); free(lb); return r; }
     }
     double J = 0.0, dtau = 0.0;
@@ -627,8 +701,10 @@ int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, doub
         J += orc_objective(q, n, link, tau, kind, m, states + sz * (size_t)nsteps, scale, lb, &dtau);
     for (int64_t s = nsteps - 1; s >= 0; --s) {
         int64_t t = t0 + s;
-        orc_adjoint_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t,
-                         states + sz * (size_t)s, lb, la, &dtau, dmean, damp, dphase);
+        int r = orc_adjoint_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, io_kind,
+                                    io_normal, weight, wall_q, t, states + sz * (size_t)s, lb, la, &dtau,
+                                    dmean, damp, dphase);
+        if (r) { free(states); free(la); free(lb); return r; }
         if (t >= t_begin && t < t_end)
             J += orc_objective(q, n, link, tau, kind, m, states + sz * (size_t)s, scale, la, &dtau);
         double *tmp = la; la = lb; lb = tmp;
@@ -642,12 +718,22 @@ int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, doub
     return 0;
 }
 
-/* Objective alone, by running forward from f0 at time t0 for nsteps steps
- * (for finite differences at sizes where storing every state is too big). */
-double orc_objective_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
-                         int n_io, const double *rho_mean, const double *amp, const double *period,
-                         const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
-                         const double *m, int64_t t_begin, int64_t t_end, double scale) {
+int orc_gradient(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                 int n_io, const double *rho_mean, const double *amp, const double *period,
+                 const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
+                 const double *m, int64_t t_begin, int64_t t_end, double scale, double *J_out,
+                 double *dtau_out, double *dmean, double *damp, double *dphase, double *lam0) {
+    return orc_gradient_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL, NULL,
+                           t0, nsteps, f0, kind, m, t_begin, t_end, scale, J_out, dtau_out, dmean, damp,
+                           dphase, lam0);
+}
+
+double orc_objective_run_bc(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                            int n_io, const double *rho_mean, const double *amp, const double *period,
+                            const double *phase, const int32_t *io_kind, const double *io_normal,
+                            const double *weight, const double *wall_q, int64_t t0, int64_t nsteps,
+                            const double *f0, int kind, const double *m, int64_t t_begin, int64_t t_end,
+                            double scale) {
     const size_t sz = (size_t)q * (size_t)n;
     double *a = (double *)malloc(sizeof(double) * (sz ? sz : 1));
     double *b = (double *)malloc(sizeof(double) * (sz ? sz : 1));
@@ -658,13 +744,22 @@ double orc_objective_run(int q, int64_t n, const int32_t *nbr, const uint8_t *li
         int64_t t = t0 + s;
         if (t >= t_begin && t < t_end) J += orc_objective(q, n, link, tau, kind, m, a, scale, NULL, NULL);
         if (s < nsteps) {
-            orc_step(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, t, a, b);
+            orc_step_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, io_kind, io_normal, weight,
+                        wall_q, t, a, b);
             double *tmp = a; a = b; b = tmp;
         }
     }
     free(a);
     free(b);
     return scale * J;
+}
+
+double orc_objective_run(int q, int64_t n, const int32_t *nbr, const uint8_t *link, double tau,
+                         int n_io, const double *rho_mean, const double *amp, const double *period,
+                         const double *phase, int64_t t0, int64_t nsteps, const double *f0, int kind,
+                         const double *m, int64_t t_begin, int64_t t_end, double scale) {
+    return orc_objective_run_bc(q, n, nbr, link, tau, n_io, rho_mean, amp, period, phase, NULL, NULL, NULL,
+                                NULL, t0, nsteps, f0, kind, m, t_begin, t_end, scale);
 }
 
 /* ------------------------------------------------------------- rendering

@@ -402,10 +402,84 @@ def pin_adjoint_gradient(o, q, kind, tau=0.7, nsteps=8):
     assert abs(got - ref) <= 1e-5 * abs(ref), ("lam0", got, ref)
 
 
+def _adj_bc_setup(o, q, seed=6):
+    """A random mask with a density iolet, a pulsatile velocity iolet (with a
+    non-uniform weight profile) and interpolated walls at random fractions on
+    both sides of 1/2."""
+    g, nbr, link, f0, rng = _adj_setup(o, q, seed)
+    bc = dict(io_kind=np.array([0, 1, 0], np.int32),
+              io_normal=np.array([[0, 0, 0], [0.6, 0.0, 0.8], [0, 0, 0]], np.float64),
+              weight=0.5 + rng.random(g.n),
+              wall_q=np.where(link == 1, rng.uniform(0.05, 1.0, link.shape), 0.5))
+    io = dict(rho_mean=np.array([1.001, 0.003, 0.999]), amp=np.array([0.0005, 0.001, 0.0]),
+              period=np.array([13.0, 17.0, 0.0]), phase=np.array([0.2, 0.7, 0.0]))
+    assert ((bc["wall_q"] < 0.5) & (link == 1)).any() and ((bc["wall_q"] > 0.5) & (link == 1)).any()
+    return g, nbr, link, f0, rng, bc, io
+
+
+def pin_adjoint_dot_product_bc(o, q, tau=0.7):
+    """One step with velocity iolets and interpolated walls: <(dF/df)^T w, v>
+    equals <w, dF/df v> from central differences of the forward step."""
+    g, nbr, link, f0, rng, bc, io = _adj_bc_setup(o, q)
+    w = rng.standard_normal(f0.shape)
+    v = rng.standard_normal(f0.shape)
+    lam, _, _, _, _ = o.adjoint_step(q, nbr, link, tau, f0, w, t=4, **bc, **io)
+    h = 1e-6
+    Fp = o.run_bc(q, nbr, link, tau, f0 + h * v, 1, t0=4, **bc, **io)
+    Fm = o.run_bc(q, nbr, link, tau, f0 - h * v, 1, t0=4, **bc, **io)
+    a, b = float(np.sum(lam * v)), float(np.sum(w * (Fp - Fm) / (2 * h)))
+    assert abs(a - b) <= 1e-8 * abs(b), (a, b)
+
+
+def pin_adjoint_gradient_bc(o, q, kind, tau=0.7, nsteps=8):
+    """The windowed objective's gradient with velocity iolets and interpolated
+    walls against central differences of the FP64 forward run: d/dtau, d/d
+    (mean, amp, phase) of the velocity iolet's speed schedule and of the
+    density iolets, and d/df0 along a random direction."""
+    g, nbr, link, f0, rng, bc, io = _adj_bc_setup(o, q)
+    m = (rng.random(g.n) < 0.5).astype(np.float64)
+    args = dict(kind=kind, m=m, t_begin=3, t_end=nsteps + 1, scale=0.25)
+    r = o.gradient(q, nbr, link, tau, f0, nsteps, want_lam0=True, **bc, **io, **args)
+    J = o.objective_run(q, nbr, link, tau, f0, nsteps, **bc, **io, **args)
+    assert abs(r["J"] - J) <= 1e-13 * abs(J)
+    # the density objective is ~80 while some of its derivatives are ~2e-5,
+    # so at h = 1e-6 its differences would carry round-off of 1e-16 * 80 / h
+    # (4e-4 of the smallest derivative): h = 1e-4 there (truncation ~1e-8);
+    # the wall-shear-stress objective is small and curved: h = 1e-6
+    h = 1e-4 if kind == 1 else 1e-6
+
+    def fd(tau_h=0.0, key=None, k=None):
+        io2 = {kk: vv.copy() for kk, vv in io.items()}
+        if key:
+            io2[key][k] += h
+        Jp = o.objective_run(q, nbr, link, tau + tau_h * h, f0, nsteps, **bc, **io2, **args)
+        if key:
+            io2[key][k] -= 2 * h
+        Jm = o.objective_run(q, nbr, link, tau - tau_h * h, f0, nsteps, **bc, **io2, **args)
+        return (Jp - Jm) / (2 * h)
+
+    assert abs(r["dtau"] - fd(tau_h=1.0)) <= 1e-5 * max(abs(r["dtau"]), 1e-30), ("dtau", r["dtau"])
+    for k in range(g.n_iolets):
+        for nm, key in (("dmean", "rho_mean"), ("damp", "amp"), ("dphase", "phase")):
+            ref = fd(key=key, k=k)
+            tol = 1e-5 * max(abs(ref), 1e-3 * abs(r["dmean"][k]))
+            assert abs(r[nm][k] - ref) <= tol, (nm, k, r[nm][k], ref)
+    assert abs(r["dmean"][1]) > 1e-6  # the velocity iolet's speed does move J
+    v = rng.standard_normal(f0.shape)
+    hv = 1e-8 if kind == 0 else 1e-6
+    Jp = o.objective_run(q, nbr, link, tau, f0 + hv * v, nsteps, **bc, **io, **args)
+    Jm = o.objective_run(q, nbr, link, tau, f0 - hv * v, nsteps, **bc, **io, **args)
+    ref = (Jp - Jm) / (2 * hv)
+    got = float(np.sum(r["lam0"] * v))
+    assert abs(got - ref) <= 1e-5 * abs(ref), ("lam0", got, ref)
+
+
 ALL_FAST += [
     ("adjoint_dot19", lambda o: pin_adjoint_dot_product(o, 19)),
     ("adjoint_wss15", lambda o: pin_adjoint_gradient(o, 15, 0)),
     ("adjoint_density19", lambda o: pin_adjoint_gradient(o, 19, 1)),
+    ("adjoint_dot_bc15", lambda o: pin_adjoint_dot_product_bc(o, 15)),
+    ("adjoint_bc_density19", lambda o: pin_adjoint_gradient_bc(o, 19, 1)),
 ]
 
 

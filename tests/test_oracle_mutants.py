@@ -67,6 +67,13 @@ MUTANTS = {
     "mass_last_site_dropped": ("for (int64_t x = 0; x < n; ++x)\n        for (int i = 0; i < q; ++i) m +=",
                                "for (int64_t x = 0; x < n - 1; ++x)\n        for (int i = 0; i < q; ++i) m +="),
     "mass_plane_stride": ("m += f[(int64_t)i * n + x];", "m += f[(int64_t)i * q + x];"),
+    "adj_bfl_upstream_weight": ("ls[(int64_t)i * n + nbr[o]] += (1.0 - 2.0 * qw) * lo;",
+                                "ls[(int64_t)i * n + nbr[o]] += 2.0 * qw * lo;"),
+    "adj_bfl_own_weight": ("ls[(int64_t)i * n + x] += 2.0 * qw * lo;", "ls[(int64_t)i * n + x] += lo;"),
+    "adj_bfl_high_second_term": ("ls[o] += (1.0 - 1.0 / (2.0 * qw)) * lo;", "ls[o] += 0.0 * lo;"),
+    "adj_velocity_rho_sign": ("gv[x] += -6.0 * L.w[i] * wx * U * cn * lo;", "gv[x] += 6.0 * L.w[i] * wx * U * cn * lo;"),
+    "adj_velocity_param_rho": ("-6.0 * L.w[i] * rho * wx * cn * lo, dmean", "-6.0 * L.w[i] * wx * cn * lo, dmean"),
+    "adj_velocity_term_dropped": ("om * s + h + gv[x];", "om * s + h;"),
     "adj_wss_M": ("lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] - s);",
                   "lam[(int64_t)j * n + x] += scale * m[x] * coef * (M[j] + s);"),
 }

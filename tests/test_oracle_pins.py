@@ -126,3 +126,13 @@ def test_bfl_second_order():
     e24 = pins.bfl_slab_wall_error(o, 19, 24, 0.1, 0.7)
     for a, b in zip(e12, e24):
         assert 1.7 < a / b < 2.4, (e12, e24)
+
+
+@pytest.mark.parametrize("q", [15, 19])
+def test_adjoint_dot_product_with_velocity_iolets_and_bfl(o, q):
+    pins.pin_adjoint_dot_product_bc(o, q)
+
+
+@pytest.mark.parametrize("q,kind", [(15, 0), (19, 1), (19, 0), (15, 1)])
+def test_adjoint_gradient_with_velocity_iolets_and_bfl(o, q, kind):
+    pins.pin_adjoint_gradient_bc(o, q, kind)
