@@ -27,16 +27,17 @@ MUTANTS = {
     "velocity_not_divided": ("u[a] = j[a] / r;", "u[a] = j[a];"),
     "no_periodic_wrap": ("if (periodic && periodic[a] > 0) y[a] =", "if (0) y[a] ="),
     "iolet_id_off_by_one": ("(k >= 0 ? 2 + k : 1)", "(k >= 0 ? 1 + k : 1)"),
-    "adj_relaxation_sign": ("(1.0 - om) * ls[j]", "(1.0 + om) * ls[j]"),
+    "adj_relaxation_sign": ("(1.0 - om) * ls[(int64_t)j * n + x]", "(1.0 + om) * ls[(int64_t)j * n + x]"),
     "adj_dfeq_du_coeff": ("9.0 * cu * L->e[i][a]", "4.5 * cu * L->e[i][a]"),
-    "adj_drho_k_scale": ("feq_k[o] / rk;", "feq_k[o];"),
-    "adj_phase_cos": ("dphase[k] += drk * amp[k] * cos(arg);", "dphase[k] += drk * amp[k] * sin(arg);"),
+    "adj_drho_k_scale": ("lo * feq_k[oi] / rk, dmean", "lo * feq_k[oi], dmean"),
+    "adj_phase_cos": ("dphase[k] += d * amp[k] * cos(arg);", "dphase[k] += d * amp[k] * sin(arg);"),
     "adj_tau_power": ("(g[i] - feq[i]) / (tau * tau);", "(g[i] - feq[i]) / tau;"),
-    "adj_wall_lambda": ("ls[i] = lam_next[(int64_t)L.opp[i] * n + x];", "ls[i] = lam_next[(int64_t)i * n + x];"),
+    "adj_wall_lambda": ("const double lo = lam_next[o];\n                if (qw == 0.5)",
+                        "const double lo = lam_next[(int64_t)i * n + x];\n                if (qw == 0.5)"),
     "adj_velocity_term": ("double dj = (L.e[j][c] - u[c]) / rho;", "double dj = L.e[j][c] / rho;"),
     "ladd_factor": ("fs - 6.0 * L.w[i] * rho * cub;", "fs - 3.0 * L.w[i] * rho * cub;"),
     "ladd_sign": ("fs - 6.0 * L.w[i] * rho * cub;", "fs + 6.0 * L.w[i] * rho * cub;"),
-    "ladd_weight_ignored": ("double wx = weight ? weight[x] : 1.0;", "double wx = 1.0;"),
+    "ladd_weight_ignored": ("double wx = weight ? weight[x] : 1.0;\n                double cub", "double wx = 1.0;\n                double cub"),
     "ladd_normal_index": ("wx * U * io_normal[3 * k + a];", "wx * U * io_normal[a];"),
     "render_dt_dropped": ("double a = e[3] * l;", "double a = e[3];"),
     "render_no_transmittance": ("C[c] += (1.0 - A) * a * e[c];", "C[c] += a * e[c];"),
