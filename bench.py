@@ -75,6 +75,7 @@ WORKLOADS = {
 
 
 RENDER_SPINUP = 2000
+I16_SCALE_LOG2 = 24  # int16 leg: step 2^-24, range |d| < 1.95e-3
 
 
 def render_view(V, tf_scale: float):
@@ -241,10 +242,11 @@ def run_ours(args):
     stream_id = {"pull": lbm.STREAM_PULL, "aa": lbm.STREAM_AA}
 
     def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL, wall_q=None,
-                   site_order=lbm.ORDER_MORTON_RUNS):
+                   site_order=lbm.ORDER_MORTON_RUNS, scale_log2=None):
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
-                        streaming=streaming, wall_q=wall_q, site_order=site_order)
+                        streaming=streaming, wall_q=wall_q, site_order=site_order,
+                        fp16_scale_log2=scale_log2)
         rho = torch.empty(g.n, dtype=torch.float32, device="cuda")
         u = torch.empty(g.n, 3, dtype=torch.float32, device="cuda")
         wss = torch.empty(g.n, dtype=torch.float32, device="cuda")
@@ -408,6 +410,9 @@ def run_ours(args):
     sampler = ClockSampler(local_rank) if rank == 0 else None
     r32 = device_leg(lbm.STORE_FP32, sampler, streaming=stream_id[main_form])
     r16 = device_leg(lbm.STORE_FP16, streaming=stream_id[main_form]) if "fp16" in legs else None
+    # int16 fixed point at the scale 2^-24 (deviations of these flows stay below 1e-3)
+    ri16 = device_leg(lbm.STORE_I16, streaming=stream_id[main_form], scale_log2=I16_SCALE_LOG2) \
+        if "i16" in legs else None
     # the other streaming form, for comparison
     alt = alt_form in legs
     raa32 = device_leg(lbm.STORE_FP32, streaming=stream_id[alt_form]) if alt else None
@@ -487,6 +492,12 @@ def run_ours(args):
             "value": round(world * metrics.msups(g.n, n_lb, r16["total_ms"] / 1e3), 2),
             "unit": "MSUPS", "ms_per_step": round(r16["total_ms"] / args.steps, 4),
             "roofline": rf16, "speedup_vs_fp32": round(r32["total_ms"] / r16["total_ms"], 3)},
+        "i16": None if not ri16 else {
+            "storage": "int16 fixed-point deviations round(d 2^%d)" % I16_SCALE_LOG2,
+            "value": round(world * metrics.msups(g.n, n_lb, ri16["total_ms"] / 1e3), 2),
+            "unit": "MSUPS", "ms_per_step": round(ri16["total_ms"] / args.steps, 4),
+            "roofline": roofline(ri16, "fp16", main_form),
+            "speedup_vs_fp32": round(r32["total_ms"] / ri16["total_ms"], 3)},
         "e2e": None if not e2e else {
             "value": round(world * metrics.msups(g.n, n_lb, e2e["seconds"]), 2),
             "unit": "MSUPS", "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
@@ -514,7 +525,7 @@ def run_ours(args):
         # the fields, and the two mass kernels
         "gpu_launches": args.steps * (inner * (2 if g.n_iolets else 1) + 1 + 2),
         "clocks": r32["clocks"],
-        "finite": all(r is None or r["finite"] for r in (r32, r16, raa32, raa16, rbfl32, rbfl16)),
+        "finite": all(r is None or r["finite"] for r in (r32, r16, ri16, raa32, raa16, rbfl32, rbfl16)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, g, nbr, link, q, tau,
@@ -611,9 +622,9 @@ def main():
                     help="LB time steps per benchmark step")
     ap.add_argument("--streaming", choices=("aa", "pull"), default="aa",
                     help="streaming form of the main legs (the other one is the comparison leg)")
-    ap.add_argument("--legs", default="fp32,fp16,pull,aa,e2e,adjoint,render,bfl",
-                    help="comma list of fp32 (always run), fp16, pull, aa (the comparison leg "
-                         "of the form not chosen by --streaming), e2e, adjoint, render, bfl")
+    ap.add_argument("--legs", default="fp32,fp16,i16,pull,aa,e2e,adjoint,render,bfl",
+                    help="comma list of fp32 (always run), fp16, i16, pull, aa (the comparison "
+                         "leg of the form not chosen by --streaming), e2e, adjoint, render, bfl")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
     ap.add_argument("--adjoint-snapshots", type=int, default=0,
                     help="snapshot count (default: as many as fit in 150 GB)")

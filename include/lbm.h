@@ -64,11 +64,11 @@ typedef enum {
     LBM_ERR_STATE = 6     /* call not valid in the context's current state      */
 } lbm_status;
 
-enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1 };
+enum { LBM_STORE_FP32 = 0, LBM_STORE_FP16 = 1, LBM_STORE_I16 = 2 };
 enum { LBM_STREAM_PULL = 0, LBM_STREAM_AA = 1 };
 enum { LBM_IOLET_DENSITY = 0, LBM_IOLET_VELOCITY = 1 };
 enum { LBM_MAX_IOLETS = 64 };
-enum { LBM_ORDER_MORTON_RUNS = 0, LBM_ORDER_MORTON = 1, LBM_ORDER_ROWS = 2 };
+enum { LBM_ORDER_MORTON_RUNS = 0, LBM_ORDER_MORTON = 1, LBM_ORDER_ROWS = 2, LBM_ORDER_SLABS = 3 };
 
 typedef struct lbm_ctx lbm_ctx; /* opaque */
 
@@ -76,12 +76,21 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *   q          15 or 19.
  *   storage    LBM_STORE_FP32: populations stored as float deviations
  *              d_i = f_i - w_i rho0; LBM_STORE_FP16: stored as IEEE half
- *              h_i = RN((f_i - w_i rho0) * 2^fp16_scale_log2).  Arithmetic is
- *              float32 in both forms.
+ *              h_i = RN((f_i - w_i rho0) * 2^fp16_scale_log2); LBM_STORE_I16:
+ *              stored as int16 fixed point k_i = RN((f_i - w_i rho0) *
+ *              2^fp16_scale_log2) with |k_i| <= 32766 (the same two bytes as
+ *              fp16 with a uniform step 2^-S instead of 11 significant bits:
+ *              finer for the large deviations that dominate a flowing site,
+ *              but the caller must choose S so that every deviation stays
+ *              below 32766 * 2^-S; a value beyond that saturates, and the
+ *              saturated slot reads as NaN everywhere outside the step
+ *              kernels, so lbm_mass reports LBM_ERR_UNSTABLE).  Arithmetic is
+ *              float32 in every form.
  *   tau        relaxation time, tau > 0.5 (kinematic viscosity (tau - 1/2)/3).
  *   rho0       reference density of the deviation storage and of the initial
  *              rest state, > 0.
- *   fp16_scale_log2  S in [0, 24]; ignored for LBM_STORE_FP32.
+ *   fp16_scale_log2  S in [0, 24] for LBM_STORE_FP16, in [0, 30] for
+ *              LBM_STORE_I16; ignored for LBM_STORE_FP32.
  *   n_iolets   K in [0, LBM_MAX_IOLETS]; the four arrays hold K doubles each
  *              (host memory, may be NULL when K = 0).
  *   iolet_kind K int32 or NULL (all density iolets): LBM_IOLET_DENSITY, or
@@ -125,7 +134,16 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              sites after the bulk, a shell on the walls and iolets, stay in
  *              plain Morton order);
  *              LBM_ORDER_MORTON (1): the Morton (Z-order) curve of (x, y, z);
- *              LBM_ORDER_ROWS (2): (z, y, x) row order. */
+ *              LBM_ORDER_ROWS (2): (z, y, x) row order;
+ *              LBM_ORDER_SLABS (3): row order, and with LBM_STREAM_AA the
+ *              bulk sites are cut into chunks of whole z planes (about 16 MB
+ *              of populations each) and lbm_step runs each even step and the
+ *              odd step after it as one pass over them: chunk c's even step
+ *              is launched with chunk c - 2's odd step, which then reads the
+ *              even step's output back from L2 instead of HBM (two LB steps
+ *              per HBM pass over the populations; the same results to the
+ *              bit).  Where a site's neighbour lies more than one chunk away
+ *              (a periodic z axis) the pairs run unfused. */
 typedef struct {
     int32_t q;
     int32_t storage;
@@ -315,8 +333,10 @@ lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link);
  * Gradients of a time-windowed objective by the discrete adjoint of the step
  * (reverse mode), with binomial checkpointing of raw state snapshots.  Not in
  * the paper, whose method is the forward solver only (Section 2); this is
- * the differentiation of that solver.  Contexts with velocity iolets are not
- * differentiated (LBM_ERR_STATE). */
+ * the differentiation of that solver.  Velocity (Ladd) iolets are
+ * differentiated too (their mean, amp and phase are those of the speed
+ * schedule U_k(t)); contexts with interpolated walls are not
+ * (LBM_ERR_STATE). */
 enum { LBM_OBJ_WSS = 0, LBM_OBJ_DENSITY = 1 };
 
 /* J = scale * sum over the states f(t) with t_begin <= t < t_end (t counted
@@ -380,6 +400,12 @@ lbm_status lbm_set_iolets(lbm_ctx *ctx, int32_t n_iolets, const double *rho_mean
 
 /* Sizes: number of sites, padded plane length, and device bytes held. */
 lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_t *device_bytes);
+
+/* Number of slab chunks over which the context's AA step pairs run fused
+ * (LBM_ORDER_SLABS with LBM_STREAM_AA), or 0 when its steps run one by one
+ * (any other order or streaming, fewer than two chunks, or a neighbour more
+ * than one chunk away).  Host only. */
+lbm_status lbm_slab_chunks(const lbm_ctx *ctx, int32_t *count);
 
 /* ------------------------------------------------------------------------
  * Volume rendering (Section 3.3.2).  The paper's visualisation renders the

@@ -14,6 +14,9 @@
 //   a = sum_i lam*_i feq_i/rho,  b = sum_i lam*_i dfeq_i/du,
 //   dfeq_i/du = w_i rho (3 c_i + 9 (c_i.u) c_i - 3 u),
 //   g = sum over iolet links of lam_opp(i)(x, t+1) dfeq_opp(i)(rho_k, u)/du.
+// A velocity (Ladd) iolet link bounces like a wall less 6 w_i rho c_i.u_b:
+//   lam*_i = lam_opp(i)(x, t+1), every lam_j gains -6 w_i (c_i.u_b) lam_opp(i),
+//   dJ/dU_k(t) += -6 w_i rho weight(x) (c_i.n_k) lam_opp(i)(x, t+1).
 // Parameter derivatives of step t:
 //   dJ/dtau      += sum_i lam*_i (f_i - feq_i) / tau^2,
 //   dJ/drho_k(t) += sum over iolet-k links of lam_opp(i)(x, t+1) feq_opp(i)/rho_k,
@@ -63,18 +66,25 @@ constexpr int kBlock = 256;
 #ifndef HGB_ADJ_MINB_AA_EVEN
 #define HGB_ADJ_MINB_AA_EVEN 4
 #endif
-template <bool HALF>
+template <int HALF>
 struct AdjLoad;
 template <>
-struct AdjLoad<false> {
+struct AdjLoad<0> {
     using T = float;
     static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
 };
 template <>
-struct AdjLoad<true> {
+struct AdjLoad<1> {
     using T = __half;
     static __device__ __forceinline__ float ld(const __half *p, float inv) {
         return __half2float(__ldg(p)) * inv;
+    }
+};
+template <>
+struct AdjLoad<2> {
+    using T = short;
+    static __device__ __forceinline__ float ld(const short *p, float inv) {
+        return (__int_as_float(0x4B400000 + (int)__ldg(p)) - 12582912.0f) * inv;
     }
 };
 
@@ -232,7 +242,7 @@ enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2, FORM_AA_SLOTS = 3 };
 // state P of time t); tab(i) is the table entry of population i at x (from
 // registers or global memory).  Adds the
 // site's terms of J and dJ/dtau to j_site and dtau_site (float).
-template <int Q, bool HALF, bool WSS, bool IO, int FORM, typename Tab, typename TabOut>
+template <int Q, int HALF, bool WSS, bool IO, int FORM, typename Tab, typename TabOut>
 __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename AdjLoad<HALF>::T *__restrict__ P,
                                              const float *lam_next, float *lam_out, const AdjStep &st,
                                              const AdjObjective &obj, int x, const Tab &tab,
@@ -290,7 +300,7 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
     // (all gathers issued first, then the pairwise sums: keeping the loads
     // back to back measured faster than accumulating as they arrive)
     float ls[Q];
-    float gx = 0.f, gy = 0.f, gz = 0.f;
+    float gx = 0.f, gy = 0.f, gz = 0.f, gvel = 0.f;
     const bool has_next = lam_next != nullptr;
     ls[0] = has_next ? lam_next[x] : 0.f;
 #pragma unroll
@@ -313,6 +323,23 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
                                              : lam_next[(unsigned)i * np + (unsigned)sp];
             } else if (!IO || sp == -1) {
                 ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+            } else if ((st.io.vel_mask >> (-2 - sp)) & 1ull) {
+                // velocity iolet: the link bounces f*_i like a wall, less
+                // Ladd's moving-boundary term 6 w_i rho c_i.u_b, u_b = weight(x)
+                // U_k(t) n_k, which feeds back through rho into every lam_j
+                // (d rho / d f_j = 1) and into dJ/dU_k(t)
+                const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+                const int k = -2 - sp;
+                ls[i] = lo;
+                const float cn = cdot<Q>(i, st.io.nrm[k][0], st.io.nrm[k][1], st.io.nrm[k][2]);
+                const float wl = 6.0f * (float)wdir<Q>(i) * L.vel_weight[x - L.n_bulk] * cn * lo;
+                gvel -= wl * st.io.rho[k];
+                const float du = -wl * rho;
+                const size_t slot = (size_t)(x - L.n_bulk) * (Q - 1) + (i - 1);
+                const size_t plane = (size_t)(L.n - L.n_bulk) * (Q - 1);
+                io_acc[slot] += (double)du;
+                io_acc[plane + slot] += (double)du * st.dsin[k];
+                io_acc[2 * plane + slot] += (double)du * st.dacos[k];
             } else {
                 const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
                 const int k = -2 - sp;
@@ -361,7 +388,7 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
     const float om = L.omega, omc = 1.0f - L.omega;
     // lam_j = omc lam*_j + om a + Bv.(c_j - u), Bv = (om b + g)/rho
     const float Bx = (om * bx + gx) * ir, By = (om * by + gy) * ir, Bz = (om * bz + gz) * ir;
-    const float base = om * a - (Bx * ux + By * uy + Bz * uz);
+    const float base = om * a - (Bx * ux + By * uy + Bz * uz) + gvel;
     float lam[Q];
     lam[0] = fmaf(omc, ls[0], base);
 #pragma unroll
@@ -420,7 +447,7 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
 // iolet link, IO = false) or the iolet sites (IO = true), one block per
 // 256-site tile.  WSS = the wall-shear-stress objective term is active at
 // this step.
-template <int Q, bool HALF, bool WSS, bool IO>
+template <int Q, int HALF, bool WSS, bool IO>
 __global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB)
 k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
@@ -450,7 +477,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
 // One adjoint step of the AA form (FORM_AA_EVEN or FORM_AA_ODD, see above) over
 // the sites [x_begin, x_end), in place on the one adjoint buffer lam (read as
 // lam(t+1), written as lam(t)); tiles and block sums as in k_adjoint.
-template <int Q, bool HALF, bool WSS, bool IO, bool ODD>
+template <int Q, int HALF, bool WSS, bool IO, bool ODD>
 __global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS
                                               : IO ? HGB_ADJ_MINB : ODD ? HGB_ADJ_MINB_AA_ODD : HGB_ADJ_MINB_AA_EVEN)
 k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P, float *lam, int has_next,
@@ -567,7 +594,7 @@ k_lam_to_caller(const DevLattice L, const float *__restrict__ lam, double *__res
     for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = (double)lam[(int64_t)i * L.npad + x];
 }
 
-template <int Q, bool HALF, bool WSS>
+template <int Q, int HALF, bool WSS>
 cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                          const AdjStep &st, const AdjObjective &obj, double *acc_block,
                          double *io_acc, cudaStream_t s, cudaStream_t t) {
@@ -582,7 +609,7 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
     return cudaGetLastError();
 }
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t adjoint_q(const DevLattice &L, const void *P, const float *lam_next, float *lam_out,
                       const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
                       cudaStream_t s, cudaStream_t t) {
@@ -591,7 +618,7 @@ cudaError_t adjoint_q(const DevLattice &L, const void *P, const float *lam_next,
     return adjoint_impl<Q, HALF, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
 }
 
-template <int Q, bool HALF, bool WSS, bool ODD>
+template <int Q, int HALF, bool WSS, bool ODD>
 cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool has_next, const AdjStep &st,
                             const AdjObjective &obj, double *acc_block, double *io_acc, cudaStream_t s,
                             cudaStream_t t) {
@@ -606,7 +633,7 @@ cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool
     return cudaGetLastError();
 }
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t adjoint_aa_q(const DevLattice &L, const void *P, bool p_swapped, float *lam, bool has_next,
                          const AdjStep &st, const AdjObjective &obj, double *acc_block, double *io_acc,
                          cudaStream_t s, cudaStream_t t) {
@@ -625,10 +652,12 @@ cudaError_t launch_adjoint_aa(const DevLattice &L, const void *P, bool p_swapped
                               cudaStream_t s, cudaStream_t t) {
     if (L.n == 0) return cudaSuccess;
     if (L.q == 15)
-        return L.storage ? adjoint_aa_q<15, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
-                         : adjoint_aa_q<15, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
-    return L.storage ? adjoint_aa_q<19, true>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
-                     : adjoint_aa_q<19, false>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
+        return L.storage == 2 ? adjoint_aa_q<15, 2>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+             : L.storage      ? adjoint_aa_q<15, 1>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+                              : adjoint_aa_q<15, 0>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
+    return L.storage == 2 ? adjoint_aa_q<19, 2>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+         : L.storage      ? adjoint_aa_q<19, 1>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t)
+                          : adjoint_aa_q<19, 0>(L, P, p_swapped, lam, has_next, st, obj, acc_block, io_acc, s, t);
 }
 
 // blocks of the bulk launch plus blocks of the iolet-site launch
@@ -641,10 +670,12 @@ cudaError_t launch_adjoint(const DevLattice &L, const void *P, const float *lam_
                            double *io_acc, cudaStream_t s, cudaStream_t t) {
     if (L.n == 0) return cudaSuccess;
     if (L.q == 15)
-        return L.storage ? adjoint_q<15, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
-                         : adjoint_q<15, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
-    return L.storage ? adjoint_q<19, true>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
-                     : adjoint_q<19, false>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
+        return L.storage == 2 ? adjoint_q<15, 2>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+             : L.storage      ? adjoint_q<15, 1>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+                              : adjoint_q<15, 0>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
+    return L.storage == 2 ? adjoint_q<19, 2>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+         : L.storage      ? adjoint_q<19, 1>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t)
+                          : adjoint_q<19, 0>(L, P, lam_next, lam_out, st, obj, acc_block, io_acc, s, t);
 }
 
 cudaError_t launch_adjoint_final(const DevLattice &L, const double *acc_block, const double *io_acc,

@@ -41,6 +41,12 @@ using namespace hemelb_gb300;
 // the buffer roles and the AA layout as it found them) and pinned iolet
 // record sets in flight
 constexpr int kGraphSteps = 32;
+// populations per slab chunk of the fused AA step pairs (LBM_ORDER_SLABS):
+// a few chunks must stay in L2 between a chunk's even and odd step
+#ifndef HGB_SLAB_BYTES
+#define HGB_SLAB_BYTES (16 << 20)
+#endif
+constexpr int64_t kSlabBytes = HGB_SLAB_BYTES;
 constexpr int kGraphRing = 8;
 static_assert(kGraphSteps % 2 == 0, "a chunk must restore the buffer roles");
 
@@ -59,6 +65,9 @@ struct lbm_ctx {
     void *f_cur = nullptr, *f_nxt = nullptr;
     int32_t *tab = nullptr, *perm = nullptr;
     uint32_t *slots = nullptr;  // slot table of the bulk step kernels (see DevLattice::slots)
+    // LBM_ORDER_SLABS with AA streaming: bounds of the slab chunks of the bulk
+    // sites (empty: step pairs run unfused)
+    std::vector<int> slab_chunks;
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
     int io_kind[LBM_MAX_IOLETS] = {};
@@ -156,7 +165,7 @@ lbm_status cuda_fail(lbm_ctx *ctx, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
     } while (0)
 
-size_t elem_bytes(int storage) { return storage == LBM_STORE_FP16 ? 2 : 4; }
+size_t elem_bytes(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
 
 // ------------------------------------------------------------------ links
 
@@ -284,6 +293,18 @@ cudaError_t advance_one(lbm_ctx *c, const IoletStep &io, const double *rho_io,
     return e;
 }
 
+// An even step and the odd step after it as one fused pass over the slab
+// chunks (AA contexts in the LBM_ORDER_SLABS order, natural layout on entry);
+// the same populations as two advance_one calls.
+bool pairs_fused(const lbm_ctx *c) {
+    return c->streaming == LBM_STREAM_AA && !c->slab_chunks.empty() && !c->aa_swapped;
+}
+cudaError_t advance_pair(lbm_ctx *c, const IoletStep &io_even, const IoletStep &io_odd,
+                         const IoletStep *io_dev_even = nullptr, const IoletStep *io_dev_odd = nullptr) {
+    return launch_step_aa_pair(c->L, c->f_cur, io_even, io_odd, c->stream, io_dev_even, io_dev_odd,
+                               c->slab_chunks.data(), (int)c->slab_chunks.size() - 1);
+}
+
 // ---- CUDA graphs of lbm_step ----------------------------------------------
 // lbm_step runs whole chunks of kGraphSteps steps as one replay of a captured
 // CUDA graph: the same kernels with the same arguments as one launch per
@@ -334,7 +355,15 @@ cudaGraphExec_t graph_for(lbm_ctx *c) {
     cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const IoletStep none{};
-        for (int j = 0; j < kGraphSteps && e == cudaSuccess; ++j) e = advance_one(c, none, nullptr, G.io_dev + j);
+        for (int j = 0; j < kGraphSteps && e == cudaSuccess;) {
+            if (pairs_fused(c) && j + 1 < kGraphSteps) {
+                e = advance_pair(c, none, none, G.io_dev + j, G.io_dev + j + 1);
+                j += 2;
+            } else {
+                e = advance_one(c, none, nullptr, G.io_dev + j);
+                ++j;
+            }
+        }
         const cudaError_t e2 = cudaStreamEndCapture(G.cap, &graph);
         if (e == cudaSuccess) e = e2;
     }
@@ -458,18 +487,20 @@ namespace {
 lbm_status validate_params(const lbm_params *p) {
     if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
     if (p->q != 15 && p->q != 19) return fail(nullptr, LBM_ERR_ARG, "q must be 15 or 19");
-    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16)
-        return fail(nullptr, LBM_ERR_ARG, "storage must be LBM_STORE_FP32 or LBM_STORE_FP16");
+    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16 && p->storage != LBM_STORE_I16)
+        return fail(nullptr, LBM_ERR_ARG, "storage must be LBM_STORE_FP32, LBM_STORE_FP16 or LBM_STORE_I16");
     if (!(p->tau > 0.5) || !std::isfinite(p->tau))
         return fail(nullptr, LBM_ERR_ARG, "tau must be finite and > 0.5");
     if (!(p->rho0 > 0) || !std::isfinite(p->rho0))
         return fail(nullptr, LBM_ERR_ARG, "rho0 must be finite and > 0");
     if (p->storage == LBM_STORE_FP16 && (p->fp16_scale_log2 < 0 || p->fp16_scale_log2 > 24))
         return fail(nullptr, LBM_ERR_ARG, "fp16_scale_log2 must be in [0, 24]");
+    if (p->storage == LBM_STORE_I16 && (p->fp16_scale_log2 < 0 || p->fp16_scale_log2 > 30))
+        return fail(nullptr, LBM_ERR_ARG, "the int16 scale (fp16_scale_log2) must be in [0, 30]");
     if (p->streaming != LBM_STREAM_PULL && p->streaming != LBM_STREAM_AA)
         return fail(nullptr, LBM_ERR_ARG, "streaming must be LBM_STREAM_PULL or LBM_STREAM_AA");
     if (p->site_order != LBM_ORDER_MORTON_RUNS && p->site_order != LBM_ORDER_MORTON &&
-        p->site_order != LBM_ORDER_ROWS)
+        p->site_order != LBM_ORDER_ROWS && p->site_order != LBM_ORDER_SLABS)
         return fail(nullptr, LBM_ERR_ARG, "unknown site_order");
     if (p->n_iolets < 0 || p->n_iolets > LBM_MAX_IOLETS)
         return fail(nullptr, LBM_ERR_ARG, "n_iolets out of range");
@@ -661,7 +692,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             // the sites after the bulk lie on the walls and iolets (a shell,
             // not runs along x): they keep the plain Morton order
             uint64_t k;
-            if (p->site_order == LBM_ORDER_ROWS)
+            if (p->site_order == LBM_ORDER_ROWS || p->site_order == LBM_ORDER_SLABS)
                 k = (rz << 42) | (ry << 21) | rx;
             else if (p->site_order == LBM_ORDER_MORTON_RUNS && !io_site)
                 k = ((spread3(rx >> 5) | (spread3(ry) << 1) | (spread3(rz) << 2)) << 5) | (rx & 31);
@@ -708,10 +739,39 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             }
     }
 
+    // slab chunks of the fused AA step pairs (LBM_ORDER_SLABS): runs of whole
+    // z planes of the bulk sites, about kSlabBytes of populations each; kept
+    // only if every fluid neighbour of a chunk's bulk sites lies in the chunk
+    // or the two next to it (a periodic z axis, for instance, breaks that:
+    // the pairs then run unfused)
+    std::vector<int> slab_chunks;
+    if (p->site_order == LBM_ORDER_SLABS && p->streaming == LBM_STREAM_AA && n_bulk > 0) {
+        const int64_t target = std::max<int64_t>(4096, kSlabBytes / ((int64_t)q * (int64_t)eb));
+        std::vector<int> chunk_of((size_t)n_bulk);
+        slab_chunks.push_back(0);
+        int32_t zprev = xyz[3 * (int64_t)perm[0] + 2];
+        for (int64_t xi = 0; xi < n_bulk; ++xi) {
+            const int32_t z = xyz[3 * (int64_t)perm[(size_t)xi] + 2];
+            if (z != zprev && xi - slab_chunks.back() >= target) slab_chunks.push_back((int)xi);
+            zprev = z;
+            chunk_of[(size_t)xi] = (int)slab_chunks.size() - 1;
+        }
+        slab_chunks.push_back((int)n_bulk);
+        bool ok = slab_chunks.size() >= 3;  // at least two chunks, or nothing to gain
+#pragma omp parallel for schedule(static) reduction(&& : ok)
+        for (int64_t xi = 0; xi < n_bulk; ++xi)
+            for (int i = 1; i < q; ++i) {
+                const int32_t src = tab[(size_t)(i - 1) * npad + xi];
+                if (src >= 0 && src < n_bulk && std::abs(chunk_of[(size_t)src] - chunk_of[(size_t)xi]) > 1)
+                    ok = false;
+            }
+        if (!ok) slab_chunks.clear();
+    }
+
     lbm_ctx *c = new lbm_ctx();
     c->q = q;
     c->storage = p->storage;
-    c->scale_log2 = p->storage == LBM_STORE_FP16 ? p->fp16_scale_log2 : 0;
+    c->scale_log2 = p->storage == LBM_STORE_FP32 ? 0 : p->fp16_scale_log2;
     c->tau = p->tau;
     c->rho0 = p->rho0;
     c->n_iolets = p->n_iolets;
@@ -796,6 +856,7 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
 #undef CKC
     c->perm_host.swap(perm);
+    c->slab_chunks.swap(slab_chunks);
     {
         static std::atomic<uint64_t> next_serial{0};
         c->serial = ++next_serial;
@@ -1056,7 +1117,9 @@ HGB_API lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host) {
     if (ctx->n == 0) return LBM_OK;
     {
         // every value finite and its deviation representable in the storage
-        const double lim = ctx->storage ? 65504.0 / std::ldexp(1.0, ctx->scale_log2) : 3.4028234663852886e38;
+        const double lim = ctx->storage == LBM_STORE_FP16 ? 65504.0 / std::ldexp(1.0, ctx->scale_log2)
+                           : ctx->storage == LBM_STORE_I16 ? 32766.0 / std::ldexp(1.0, ctx->scale_log2)
+                                                           : 3.4028234663852886e38;
         for (int i = 0; i < ctx->q; ++i) {
             const double w = wdir_q(ctx->q, i) * ctx->rho0;
             const double *row = f_host + (size_t)i * ctx->n;
@@ -1423,8 +1486,6 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
         return fail(ctx, LBM_ERR_ARG, "objective kind must be LBM_OBJ_WSS or LBM_OBJ_DENSITY");
     if (ctx->n > 0 && !obj->weight) return fail(ctx, LBM_ERR_ARG, "objective weight is NULL");
     if (!std::isfinite(obj->scale)) return fail(ctx, LBM_ERR_ARG, "objective scale is not finite");
-    if (ctx->has_velocity_iolet)
-        return fail(ctx, LBM_ERR_STATE, "contexts with velocity iolets are not differentiated");
     if (ctx->has_bfl)
         return fail(ctx, LBM_ERR_STATE, "contexts with interpolated walls are not differentiated");
     if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
@@ -1597,6 +1658,12 @@ HGB_API lbm_status lbm_info(const lbm_ctx *ctx, int64_t *n, int64_t *npad, size_
     if (n) *n = ctx->n;
     if (npad) *npad = ctx->npad;
     if (device_bytes) *device_bytes = ctx->device_bytes;
+    return LBM_OK;
+}
+
+HGB_API lbm_status lbm_slab_chunks(const lbm_ctx *ctx, int32_t *count) {
+    if (!ctx || !count) return fail(nullptr, LBM_ERR_ARG, "NULL argument");
+    *count = ctx->slab_chunks.empty() ? 0 : (int32_t)ctx->slab_chunks.size() - 1;
     return LBM_OK;
 }
 

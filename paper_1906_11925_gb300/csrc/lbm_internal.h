@@ -127,6 +127,15 @@ cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletSt
                            const double *rho_io, cudaStream_t s, const SideStream *side = nullptr,
                            const IoletStep *io_dev = nullptr);
 
+// An even AA step and the odd step after it in one pass over the slab chunks
+// [chunk[c], chunk[c + 1]) of the bulk sites (c < nchunks; the chunks are
+// whole z planes of the LBM_ORDER_SLABS order, each site's neighbours in its
+// own or the two neighbouring chunks): A in natural layout on entry and exit.
+// io_dev_even / io_dev_odd, when not null, replace the iolet records.
+cudaError_t launch_step_aa_pair(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
+                                cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
+                                const int *chunk, int nchunks);
+
 // The bounded mbarrier wait of the staged step on a barrier no copy
 // completes: sets *err when it gives up after limit polls.
 cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s);

@@ -35,11 +35,11 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMassBlocks = 2 * 152;  // fixed grid: deterministic reduction order
-template <bool HALF>
+template <int HALF>
 struct Store;
 
 template <>
-struct Store<false> {
+struct Store<0> {
     using T = float;
     static __device__ __forceinline__ float load(const float *p, float) { return __ldg(p); }
     static __device__ __forceinline__ float load_plain(const float *p, float) { return *p; }
@@ -48,7 +48,7 @@ struct Store<false> {
 };
 
 template <>
-struct Store<true> {
+struct Store<1> {
     using T = __half;
     static __device__ __forceinline__ float load(const __half *p, float inv) {
         return __half2float(__ldg(p)) * inv;
@@ -62,6 +62,25 @@ struct Store<true> {
     static __device__ __forceinline__ void store_plain(__half *p, float v, float sc) {
         *p = __float2half_rn(v * sc);
     }
+};
+
+// int16 fixed point: value = round(deviation 2^S), |value| <= 32766; the
+// saturation codes +-32767 read as NaN (an out-of-range state shows as
+// non-finite, as an fp16 overflow does), -32768 is the guard code.
+__device__ __forceinline__ float i16_value(int v, float inv) {
+    return (v >= 32767 || v <= -32767) ? __int_as_float(0x7fc00000) : (__int_as_float(0x4B400000 + v) - 12582912.0f) * inv;
+}
+__device__ __forceinline__ short i16_code(float v) {
+    const float c = fminf(fmaxf(v, -32767.0f), 32767.0f);
+    return (short)(__float_as_int(c + 12582912.0f) - 0x4B400000);
+}
+template <>
+struct Store<2> {
+    using T = short;
+    static __device__ __forceinline__ float load(const short *p, float inv) { return i16_value(__ldg(p), inv); }
+    static __device__ __forceinline__ float load_plain(const short *p, float inv) { return i16_value(*p, inv); }
+    static __device__ __forceinline__ void store(short *p, float v, float sc) { __stcs(p, i16_code(v * sc)); }
+    static __device__ __forceinline__ void store_plain(short *p, float v, float sc) { *p = i16_code(v * sc); }
 };
 
 // Slot holding population i of site x (table entry s) in each layout:
@@ -78,7 +97,7 @@ __device__ __forceinline__ int64_t src_slot(int layout, int i, int s, int x, int
 // Gather the q deviations of site x (pre-collision populations f(t) - w rho0).
 // Returns the smallest table entry seen and, through wall_n, the sum of c_i
 // over wall entries (half-way or interpolated).
-template <int Q, bool HALF, bool STREAM_TAB, bool BFL = false>
+template <int Q, int HALF, bool STREAM_TAB, bool BFL = false>
 __device__ __forceinline__ int gather(const DevLattice &L, const typename Store<HALF>::T *__restrict__ f,
                                       int layout, int x, float (&d)[Q], int (&wn)[3]) {
     using S = Store<HALF>;
@@ -185,7 +204,7 @@ __device__ __forceinline__ float wall_shear(const float (&d)[Q], const Moments &
 #ifndef HGB_MACROS_MINB
 #define HGB_MACROS_MINB 3
 #endif
-template <int Q, bool HALF, bool BFL>
+template <int Q, int HALF, bool BFL>
 __global__ void __launch_bounds__(kBlock, HGB_MACROS_MINB)
 k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
          float *__restrict__ rho, float *__restrict__ u, float *__restrict__ wss) {
@@ -213,7 +232,7 @@ k_macros(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int 
 #ifndef HGB_FILL_MINB
 #define HGB_FILL_MINB 3
 #endif
-template <int Q, bool HALF, int QTY, bool BFL>
+template <int Q, int HALF, int QTY, bool BFL>
 __global__ void __launch_bounds__(kBlock, QTY == 2 ? 1 : HGB_FILL_MINB)
 k_volume_fill(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
               const uint64_t *__restrict__ vox, VolumeTarget V) {
@@ -270,7 +289,7 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // mass = n rho0 + sum over all stored slots of the deviation: the gather is a
 // permutation of the slots, so the slots hold exactly the populations f(t).
-template <int Q, bool HALF, bool BFL>
+template <int Q, int HALF, bool BFL>
 __global__ void __launch_bounds__(kBlock)
 k_mass_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
                double *__restrict__ partials) {
@@ -316,7 +335,7 @@ k_mass_final(const double *__restrict__ partials, int nparts, double base, doubl
 // density), per-block float64 partial sums in a fixed grid (deterministic):
 // weight is float64 in caller order (null: all ones).  The density is formed
 // as rho0 + drho in float64 so that the deviation keeps its precision.
-template <int Q, bool HALF, int KIND, bool BFL>
+template <int Q, int HALF, int KIND, bool BFL>
 __global__ void __launch_bounds__(kBlock)
 k_wsum_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
                const double *__restrict__ weight, double *__restrict__ partials) {
@@ -337,7 +356,7 @@ k_wsum_partial(const DevLattice L, const typename Store<HALF>::T *__restrict__ f
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-template <int Q, bool HALF, bool BFL>
+template <int Q, int HALF, bool BFL>
 __global__ void __launch_bounds__(kBlock)
 k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, int layout,
              double *__restrict__ out) {
@@ -351,7 +370,7 @@ k_gather_f64(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, 
     for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = wdir<Q>(i) * (double)L.rho0 + (double)d[i];
 }
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 __global__ void __launch_bounds__(kBlock)
 k_scatter_f64(const DevLattice L, const double *__restrict__ in, int layout,
               typename Store<HALF>::T *__restrict__ f) {
@@ -397,8 +416,10 @@ inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); 
 }  // namespace
 
 #define HGB_DISPATCH(L, FN, ...)                                                         \
-    ((L).q == 15 ? ((L).storage ? FN<15, true>(__VA_ARGS__) : FN<15, false>(__VA_ARGS__)) \
-                 : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
+    ((L).q == 15 ? ((L).storage == 2 ? FN<15, 2>(__VA_ARGS__)                                 \
+                                     : (L).storage ? FN<15, 1>(__VA_ARGS__) : FN<15, 0>(__VA_ARGS__)) \
+                 : ((L).storage == 2 ? FN<19, 2>(__VA_ARGS__)                                 \
+                                     : (L).storage ? FN<19, 1>(__VA_ARGS__) : FN<19, 0>(__VA_ARGS__)))
 
 cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,
                             int dst_layout, cudaStream_t s) {
@@ -418,7 +439,7 @@ cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout
 }
 
 namespace {
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t macros_impl(const DevLattice &L, const void *f, int layout, float *rho, float *u, float *wss,
                         cudaStream_t s) {
     using T = typename Store<HALF>::T;
@@ -428,7 +449,7 @@ cudaError_t macros_impl(const DevLattice &L, const void *f, int layout, float *r
         k_macros<Q, HALF, false><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, rho, u, wss);
     return cudaGetLastError();
 }
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t mass_impl(const DevLattice &L, const void *f, int layout, double *partials, cudaStream_t s) {
     using T = typename Store<HALF>::T;
     if (L.bfl)
@@ -437,7 +458,7 @@ cudaError_t mass_impl(const DevLattice &L, const void *f, int layout, double *pa
         k_mass_partial<Q, HALF, false><<<kMassBlocks, kBlock, 0, s>>>(L, (const T *)f, layout, partials);
     return cudaGetLastError();
 }
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t gather_impl(const DevLattice &L, const void *f, int layout, double *out, cudaStream_t s) {
     using T = typename Store<HALF>::T;
     if (L.bfl)
@@ -446,13 +467,13 @@ cudaError_t gather_impl(const DevLattice &L, const void *f, int layout, double *
         k_gather_f64<Q, HALF, false><<<grid_for(L.n), kBlock, 0, s>>>(L, (const T *)f, layout, out);
     return cudaGetLastError();
 }
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t scatter_impl(const DevLattice &L, const double *in, int layout, void *f, cudaStream_t s) {
     using T = typename Store<HALF>::T;
     k_scatter_f64<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, in, layout, (T *)f);
     return cudaGetLastError();
 }
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t volume_fill_impl(const DevLattice &L, const void *f, int layout, const uint64_t *vox,
                              const VolumeTarget &V, cudaStream_t s) {
     using T = typename Store<HALF>::T;
@@ -484,7 +505,7 @@ cudaError_t launch_macros(const DevLattice &L, const void *f, int layout, float 
 }
 
 namespace {
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t wsum_impl(const DevLattice &L, const void *f, int layout, int kind, const double *weight,
                       double *partials, cudaStream_t s) {
     using T = typename Store<HALF>::T;
@@ -537,7 +558,7 @@ namespace {
 // moments of each site's own slots give rho > 0 and |j|^2 <= u_max^2 rho^2.
 // A failing block writes `tag` into *flag if it is still 0, so the flag
 // keeps the first failing check of a series.
-template <int Q, bool HALF>
+template <int Q, int HALF>
 __global__ void __launch_bounds__(kBlock)
 k_stability(const DevLattice L, const typename Store<HALF>::T *__restrict__ f, float u_max2, int tag,
             int *__restrict__ flag) {
@@ -580,7 +601,7 @@ k_guards(W *__restrict__ f, int q, int64_t n, int64_t npad, int64_t extra, W pat
     if (check && __syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t stability_impl(const DevLattice &L, const void *f, float u_max2, int tag, int *flag,
                            cudaStream_t s) {
     k_stability<Q, HALF><<<grid_for(L.n), kBlock, 0, s>>>(L, (const typename Store<HALF>::T *)f, u_max2, tag,
@@ -598,9 +619,10 @@ cudaError_t launch_stability(const DevLattice &L, const void *f, float u_max, in
 cudaError_t launch_guards(const DevLattice &L, void *f, bool check, int *flag, cudaStream_t s) {
     const int64_t total = (int64_t)L.q * (L.npad - L.n) + kGuardSlots;
     const unsigned g = (unsigned)std::min<int64_t>((total + kBlock - 1) / kBlock, 4 * 152);
-    if (L.storage)
+    if (L.storage)  // fp16: a NaN pattern; int16: -32768, which no store writes
         k_guards<unsigned short><<<g, kBlock, 0, s>>>((unsigned short *)f, L.q, L.n, L.npad, kGuardSlots,
-                                                      (unsigned short)0x7DA5u, check ? 1 : 0, flag);
+                                                      (unsigned short)(L.storage == 2 ? 0x8000u : 0x7DA5u),
+                                                      check ? 1 : 0, flag);
     else
         k_guards<unsigned><<<g, kBlock, 0, s>>>((unsigned *)f, L.q, L.n, L.npad, kGuardSlots, 0x7FA5A5A5u,
                                                 check ? 1 : 0, flag);

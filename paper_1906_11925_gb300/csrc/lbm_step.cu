@@ -49,8 +49,8 @@ inline unsigned grid_for(int n) { return (unsigned)((n + kBlock - 1) / kBlock); 
 // Raw stored values for the step kernel: fp16 values stay in their scaled
 // units (d * 2^S) through the whole update, so that no load or store pays a
 // multiplication; only rho and u are formed in real units.
-template <bool HALF>
-struct Raw;
+template <int HALF>
+struct Raw;  // 0: float, 1: IEEE half, 2: int16 fixed point (both 16-bit forms in units of 2^-S)
 
 // Cache policy of the in-place AA kernels: 1 = evict-first (.cs), 0 = default
 #ifndef HGB_AA_LD_CS
@@ -61,8 +61,9 @@ struct Raw;
 #endif
 
 template <>
-struct Raw<false> {
+struct Raw<0> {
     using T = float;
+    static __device__ __forceinline__ void st_plain(float *p, float v) { *p = v; }
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float ld_rw(const float *p) { return HGB_AA_LD_CS ? __ldcs(p) : *p; }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
@@ -73,8 +74,9 @@ struct Raw<false> {
 };
 
 template <>
-struct Raw<true> {
+struct Raw<1> {
     using T = __half;
+    static __device__ __forceinline__ void st_plain(__half *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float ld_rw(const __half *p) {
         return HGB_AA_LD_CS ? __half2float(__short_as_half(__ldcs(reinterpret_cast<const short *>(p))))
@@ -87,6 +89,33 @@ struct Raw<true> {
     static __device__ __forceinline__ void st(__half *p, float v) {
         __stcs(reinterpret_cast<short *>(p), __half_as_short(__float2half_rn(v)));
     }
+};
+
+// int16 fixed point (storage 2): the stored value is the deviation times 2^S
+// rounded to the nearest integer, |value| <= 32766; 32767 and -32767 are the
+// saturation codes an out-of-range value is clamped to (the readers outside
+// the step kernels turn them into NaN), -32768 is the guard code.  The
+// conversions add and remove 1.5 2^23, which places the integer in the low
+// bits of a float (exact for |v| < 2^22): two instructions each way, no
+// conversion unit.
+__device__ __forceinline__ float i16_to_float(int v) { return __int_as_float(0x4B400000 + v) - 12582912.0f; }
+__device__ __forceinline__ short float_to_i16(float v) {
+    const float c = fminf(fmaxf(v, -32767.0f), 32767.0f);  // (a NaN becomes -32767)
+    return (short)(__float_as_int(c + 12582912.0f) - 0x4B400000);
+}
+template <>
+struct Raw<2> {
+    using T = short;
+    static __device__ __forceinline__ void st_plain(short *p, float v) { *p = float_to_i16(v); }
+    static __device__ __forceinline__ float ld(const short *p) { return i16_to_float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_rw(const short *p) {
+        return i16_to_float(HGB_AA_LD_CS ? __ldcs(p) : *p);
+    }
+    static __device__ __forceinline__ void st_rw(short *p, float v) {
+        if (HGB_AA_ST_CS) __stcs(p, float_to_i16(v));
+        else *p = float_to_i16(v);
+    }
+    static __device__ __forceinline__ void st(short *p, float v) { __stcs(p, float_to_i16(v)); }
 };
 
 // Checked builds (HGB_CHECK_TABLE=1, libhemelb_gb300_checked.so): every table
@@ -152,7 +181,7 @@ struct Velocity {
 // In exact arithmetic this is the same collision.
 // Every step kernel (pull, AA even, AA odd) uses this one function, so all
 // streaming forms give bitwise identical populations.
-template <int Q, bool HALF>
+template <int Q, int HALF>
 __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d)[Q], float (&out)[Q]) {
     float drs = d[0], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -219,7 +248,7 @@ __device__ __forceinline__ Velocity collide(const DevLattice &L, const float (&d
 //                   leaves the domain);
 //   velocity iolet: the bounced f*_opp(i) plus Ladd's moving-boundary term
 //                   6 w_i rho (c_i . u_b), u_b = weight(x) U_k(t) n_k.
-template <int Q, bool HALF>
+template <int Q, int HALF>
 __device__ __forceinline__ void iolet_override(const DevLattice &L, int x, const int (&s)[Q],
                                                const Velocity &v, const IoletStep &io,
                                                const double *__restrict__ rho_io,
@@ -331,7 +360,7 @@ __device__ __forceinline__ void bfl_scatter(const int (&s)[Q], float (&out)[Q]) 
 #ifndef HGB_TAIL_MINB_FP16
 #define HGB_TAIL_MINB_FP16 HGB_STEP_MINB_FP16
 #endif
-template <int Q, bool HALF, bool IO, bool BFL = false>
+template <int Q, int HALF, bool IO, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, IO ? (HALF ? HGB_TAIL_MINB_FP16 : HGB_TAIL_MINB_FP32)
                                              : (HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32))
 k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
@@ -410,7 +439,7 @@ __global__ void k_wait_probe(int *err, unsigned limit) {
 
 
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
 k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
               const Planes<typename Raw<HALF>::T> out_planes, int *__restrict__ err) {
@@ -485,6 +514,95 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
     }
 }
 
+// resident blocks per SM of the AA step kernels (fp32, 16-bit storage)
+#ifndef HGB_AA_MINB_FP32
+#define HGB_AA_MINB_FP32 4
+#endif
+#ifndef HGB_AA_MINB_FP16
+#define HGB_AA_MINB_FP16 4
+#endif
+
+// The bulk-site bodies of the AA step (shared by k_step_aa and the fused step
+// pair below, so that both give the same bits).  Even step: the site's own
+// slots (measured: fp16 is faster through the plane pointers, each address
+// one multiply-add onto a pointer in the constant bank, formed again for the
+// store; fp32 through one base pointer and the plane offsets); STREAM_ST
+// selects evict-first stores (the plain even step) or default ones (the
+// fused pair, whose odd step reads them back from L2).  Odd step: through
+// the slot table.
+template <int Q, int HALF, bool STREAM_ST>
+__device__ __forceinline__ void aa_even_bulk(const DevLattice &L, typename Raw<HALF>::T *__restrict__ A,
+                                             const Planes<typename Raw<HALF>::T> &P, int x) {
+    using R = Raw<HALF>;
+    const unsigned np = (unsigned)L.npad;
+    float d[Q], out[Q];
+    if (HALF) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(P.p[i] + x);
+        collide<Q, HALF>(L, d, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (STREAM_ST) R::st_rw(P.p[i] + x, out[opp(i)]);
+            else R::st_plain(P.p[i] + x, out[opp(i)]);
+        }
+    } else {
+        typename Raw<HALF>::T *a = A + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+        collide<Q, HALF>(L, d, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (STREAM_ST) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
+            else R::st_plain(a + (unsigned)i * np, out[opp(i)]);
+        }
+    }
+}
+
+template <int Q, int HALF>
+__device__ __forceinline__ void aa_odd_bulk(const DevLattice &L, typename Raw<HALF>::T *__restrict__ A,
+                                            const SlotRows &S, int x) {
+    using R = Raw<HALF>;
+    const unsigned np = (unsigned)L.npad;
+    float d[Q], out[Q];
+    unsigned e[Q];
+    e[0] = (unsigned)x;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) e[i] = checked_slot(L, __ldcs(S.p[i - 1] + x), (unsigned)i * np + (unsigned)x);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + e[i]);
+    collide<Q, HALF>(L, d, out);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) R::st_rw(A + e[i], out[opp(i)]);
+}
+
+// A fused AA step pair over slab chunks (LBM_ORDER_SLABS): the blocks
+// [0, e_blocks) run the even step of the bulk sites [e_begin, e_end), the
+// others the odd step of [o_begin, o_end).  The host launches chunk c's even
+// step together with chunk c - 2's odd step: the odd step of a chunk reads
+// and writes only slots of its own and its two neighbouring chunks (the
+// chunks are unions of whole (z) planes, and a site's neighbours lie in the
+// planes z - 1 .. z + 1), which the even steps of earlier launches have
+// finished, and the two halves of a launch touch disjoint slots.  So the odd
+// step reads back what the even step wrote one or two launches before, from
+// L2 instead of HBM.
+// resident blocks per SM of the fused pair (it holds both bodies)
+#ifndef HGB_AA_PAIR_MINB
+#define HGB_AA_PAIR_MINB 3
+#endif
+template <int Q, int HALF>
+__global__ void __launch_bounds__(kBlock, HGB_AA_PAIR_MINB)
+k_step_aa_pair(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Planes<typename Raw<HALF>::T> P,
+               const SlotRows S, int e_begin, int e_end, int e_blocks, int o_begin, int o_end) {
+    const int b = (int)blockIdx.x;
+    if (b < e_blocks) {
+        const int x = e_begin + b * kBlock + (int)threadIdx.x;
+        if (x < e_end) aa_even_bulk<Q, HALF, false>(L, A, P, x);
+    } else {
+        const int x = o_begin + (b - e_blocks) * kBlock + (int)threadIdx.x;
+        if (x < o_end) aa_odd_bulk<Q, HALF>(L, A, S, x);
+    }
+}
+
 // AA-pattern in-place step on one population buffer A (Bailey et al.,
 // "Accelerating lattice Boltzmann fluid flow simulations using graphics
 // processors", ICPP 2009).  Population i of site x is read from its slot and
@@ -498,12 +616,6 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 // step; the sites with iolet links decode the pull table.
 // After an even step A holds the populations of time t+1 in swapped slots;
 // after an odd step they are back in natural order, A[i][x] = f_i(x).
-#ifndef HGB_AA_MINB_FP32
-#define HGB_AA_MINB_FP32 4
-#endif
-#ifndef HGB_AA_MINB_FP16
-#define HGB_AA_MINB_FP16 4
-#endif
 // the even bulk step (no table) on its own
 #ifndef HGB_AA_MINB_EVEN_FP32
 #define HGB_AA_MINB_EVEN_FP32 HGB_AA_MINB_FP32
@@ -511,7 +623,7 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #ifndef HGB_AA_MINB_EVEN_FP16
 #define HGB_AA_MINB_EVEN_FP16 HGB_AA_MINB_FP16
 #endif
-template <int Q, bool HALF, bool ODD, bool IO, bool BFL = false>
+template <int Q, int HALF, bool ODD, bool IO, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, (ODD || IO) ? (HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
                                                       : (HALF ? HGB_AA_MINB_EVEN_FP16 : HGB_AA_MINB_EVEN_FP32))
 k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Planes<typename Raw<HALF>::T> P,
@@ -526,38 +638,10 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
     if (!IO) {
         // bulk sites: even step on the own slots through the plane pointers,
         // odd step through the slot table; no table codes, no iolet work
-        if (!ODD) {
-            // (measured: fp16 is faster through the plane pointers, fp32
-            // through one base pointer and the plane offsets)
-            if (HALF) {
-                typename Raw<HALF>::T *a[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) a[i] = P.p[i] + x;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a[i]);
-                collide<Q, HALF>(L, d, out);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) R::st_rw(a[i], out[opp(i)]);
-            } else {
-                typename Raw<HALF>::T *a = A + x;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
-                collide<Q, HALF>(L, d, out);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
-            }
-        } else {
-            unsigned e[Q];
-            e[0] = (unsigned)x;
-#pragma unroll
-            for (int i = 1; i < Q; ++i)
-                e[i] = checked_slot(L, __ldcs(S.p[i - 1] + x), (unsigned)i * np + (unsigned)x);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + e[i]);
-            collide<Q, HALF>(L, d, out);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) R::st_rw(A + e[i], out[opp(i)]);
-        }
+        if (!ODD)
+            aa_even_bulk<Q, HALF, true>(L, A, P, x);
+        else
+            aa_odd_bulk<Q, HALF>(L, A, S, x);
         return;
     }
     int s[Q];
@@ -596,7 +680,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
 // k_step_aa reads and writes, S and D distinct; every slot of D is written):
 // the first step of a recomputation from an adjoint snapshot, which must stay
 // intact.  The per-site arithmetic is k_step_aa's.
-template <int Q, bool HALF, bool ODD, bool IO>
+template <int Q, int HALF, bool ODD, bool IO>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
 k_step_aa_oop(const DevLattice L, const typename Raw<HALF>::T *__restrict__ S, typename Raw<HALF>::T *__restrict__ D,
               const IoletStep io) {
@@ -650,7 +734,7 @@ inline SlotRows slot_rows_of(const DevLattice &L) {
     return S;
 }
 
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep &io,
                          const double *rho_io, cudaStream_t s, const SideStream *side,
                          const IoletStep *io_dev) {
@@ -677,7 +761,43 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
     return e;
 }
 
-template <int Q, bool HALF>
+// An even step and the following odd step of the AA form as one pass over
+// the slab chunks [chunk[c], chunk[c + 1]) of the bulk sites: the iolet-site
+// even step first, then launches c = 0 .. K + 1 each holding chunk c's even
+// step and chunk c - 2's odd step, then the iolet-site odd step (which reads
+// slots of bulk sites anywhere, so it waits for every even step).
+template <int Q, int HALF>
+cudaError_t step_aa_pair_impl(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
+                              cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
+                              const int *chunk, int nchunks) {
+    using T = typename Raw<HALF>::T;
+    const int ni = L.n - L.n_bulk;
+    const Planes<T> P = planes_of((T *)A, Q, L.npad);
+    const SlotRows S = slot_rows_of(L);
+    if (ni && L.bfl)
+        k_step_aa<Q, HALF, false, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_even, nullptr,
+                                                                               io_dev_even);
+    else if (ni)
+        k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_even, nullptr,
+                                                                         io_dev_even);
+    for (int c = 0; c < nchunks + 2; ++c) {
+        int eb = 0, ee = 0, ob = 0, oe = 0;
+        if (c < nchunks) eb = chunk[c], ee = chunk[c + 1];
+        if (c >= 2) ob = chunk[c - 2], oe = chunk[c - 1];
+        const int e_blocks = (int)grid_for(ee - eb), o_blocks = (int)grid_for(oe - ob);
+        if (e_blocks + o_blocks == 0) continue;
+        k_step_aa_pair<Q, HALF><<<e_blocks + o_blocks, kBlock, 0, s>>>(L, (T *)A, P, S, eb, ee, e_blocks, ob, oe);
+    }
+    if (ni && L.bfl)
+        k_step_aa<Q, HALF, true, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_odd, nullptr,
+                                                                              io_dev_odd);
+    else if (ni)
+        k_step_aa<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_odd, nullptr,
+                                                                        io_dev_odd);
+    return cudaGetLastError();
+}
+
+template <int Q, int HALF>
 cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
                       const double *rho_io, cudaStream_t s, const SideStream *side,
                       const IoletStep *io_dev) {
@@ -727,8 +847,10 @@ cudaError_t step_impl(const DevLattice &L, const void *fin, void *fout, const Io
 }  // namespace
 
 #define HGB_DISPATCH(L, FN, ...)                                                         \
-    ((L).q == 15 ? ((L).storage ? FN<15, true>(__VA_ARGS__) : FN<15, false>(__VA_ARGS__)) \
-                 : ((L).storage ? FN<19, true>(__VA_ARGS__) : FN<19, false>(__VA_ARGS__)))
+    ((L).q == 15 ? ((L).storage == 2 ? FN<15, 2>(__VA_ARGS__)                                 \
+                                     : (L).storage ? FN<15, 1>(__VA_ARGS__) : FN<15, 0>(__VA_ARGS__)) \
+                 : ((L).storage == 2 ? FN<19, 2>(__VA_ARGS__)                                 \
+                                     : (L).storage ? FN<19, 1>(__VA_ARGS__) : FN<19, 0>(__VA_ARGS__)))
 
 cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const IoletStep &io,
                         const double *rho_io, cudaStream_t s, const SideStream *side,
@@ -738,7 +860,7 @@ cudaError_t launch_step(const DevLattice &L, const void *fin, void *fout, const 
 }
 
 namespace {
-template <int Q, bool HALF>
+template <int Q, int HALF>
 cudaError_t step_aa_oop_impl(const DevLattice &L, const void *src, void *dst, bool odd, const IoletStep &io,
                              cudaStream_t s) {
     using T = typename Raw<HALF>::T;
@@ -758,6 +880,13 @@ cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, 
                                cudaStream_t s) {
     if (L.n == 0) return cudaSuccess;
     return HGB_DISPATCH(L, step_aa_oop_impl, L, src, dst, odd, io, s);
+}
+
+cudaError_t launch_step_aa_pair(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
+                                cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
+                                const int *chunk, int nchunks) {
+    if (L.n == 0) return cudaSuccess;
+    return HGB_DISPATCH(L, step_aa_pair_impl, L, A, io_even, io_odd, s, io_dev_even, io_dev_odd, chunk, nchunks);
 }
 
 cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {

@@ -18,6 +18,7 @@ from . import build as _build
 
 STORE_FP32 = 0
 STORE_FP16 = 1
+STORE_I16 = 2
 STREAM_PULL = 0
 STREAM_AA = 1
 IOLET_DENSITY = 0
@@ -26,12 +27,13 @@ MAX_IOLETS = 64
 ORDER_MORTON_RUNS = 0
 ORDER_MORTON = 1
 ORDER_ROWS = 2
+ORDER_SLABS = 3
 
 _STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_TABLE", 3: "LBM_ERR_NOMEM",
            4: "LBM_ERR_CUDA", 5: "LBM_ERR_UNSTABLE", 6: "LBM_ERR_STATE"}
 
 EXPORTED = (
-    "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream",
+    "lbm_links_build", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_stream", "lbm_slab_chunks",
     "lbm_step", "lbm_step_driven", "lbm_get_time", "lbm_set_time", "lbm_macros", "lbm_mass",
     "lbm_weighted_sum", "lbm_check_wait_timeout", "lbm_set_stability_check", "lbm_check_guards",
     "lbm_get_populations", "lbm_get_populations_noalloc", "lbm_set_populations",
@@ -139,6 +141,7 @@ def load_library(build_if_missing: bool = True):
         "lbm_set_state": [P, P, C.c_size_t],
         "lbm_get_links": [P, P, P],
         "lbm_info": [P, P, P, P],
+        "lbm_slab_chunks": [P, P],
         "lbm_objective_grad": [P, P, i64, i32, P, P, P, P, P, P],
         "lbm_revolve_steps": [i64, i32, P],
         "lbm_adjoint_counts": [P, P, P, P],
@@ -219,7 +222,7 @@ class Lattice:
     """One simulation (``lbm_create`` ... ``lbm_destroy``) on the current GPU."""
 
     def __init__(self, q: int, xyz, nbr, link, tau: float, storage: int = STORE_FP32,
-                 rho0: float = 1.0, fp16_scale_log2: int = 14,
+                 rho0: float = 1.0, fp16_scale_log2: Optional[int] = None,
                  rho_mean: Sequence[float] = (), amp: Sequence[float] = None,
                  period: Sequence[float] = None, phase: Sequence[float] = None,
                  stream=None, streaming: int = STREAM_PULL, iolet_kind=None, iolet_normal=None,
@@ -243,6 +246,11 @@ class Lattice:
         self._wq = None if wall_q is None else np.ascontiguousarray(wall_q, dtype=np.float64)
         if self._wq is not None and self._wq.shape != (q, n):
             raise ValueError("wall_q must be [q, n]")
+        if fp16_scale_log2 is None:
+            # the scale S of the 16-bit forms: fp16 only needs the small
+            # deviations kept out of its subnormal range; int16 resolves 2^-S
+            # uniformly up to 32766 2^-S (22: deviations up to 7.8e-3)
+            fp16_scale_log2 = 22 if int(storage) == STORE_I16 else 14
         prm = _Params(int(q), int(storage), float(tau), float(rho0), int(fp16_scale_log2), k,
                       *[(a.ctypes.data if k else None) for a in self._io], int(streaming),
                       None if self._kind is None else self._kind.ctypes.data,
@@ -459,6 +467,12 @@ class Lattice:
         n, npad, b = C.c_int64(), C.c_int64(), C.c_size_t()
         self._ck(self._lib.lbm_info(self._ctx, C.byref(n), C.byref(npad), C.byref(b)))
         return dict(n=n.value, npad=npad.value, device_bytes=b.value)
+
+    def slab_chunks(self) -> int:
+        """Slab chunks of the fused AA step pairs (0: steps run one by one)."""
+        c = C.c_int32(0)
+        self._ck(self._lib.lbm_slab_chunks(self._ctx, C.byref(c)))
+        return int(c.value)
 
     def box(self):
         """Bounding box of the sites: (lo [3], dims [3]) as int tuples."""

@@ -19,12 +19,16 @@ def msups(n_sites: int, steps: int, seconds: float) -> float:
 
 def bytes_per_site_update(q: int, storage: str, streaming: str = "pull") -> int:
     """Algorithmic HBM bytes of one fused collide-and-stream update:
-    q populations read and q written (4 B each in fp32, 2 B in fp16
-    deviation storage) plus the int32 neighbour entries (q - 1; the rest
-    population needs none).  Pull streaming reads the table every step; the
-    AA pattern only on odd steps, so its average over a step pair is
-    (q - 1) * 2 B."""
-    elem = {"fp32": 4, "fp16": 2}[storage]
+    q populations read and q written (4 B each in fp32, 2 B in the 16-bit
+    deviation forms, fp16 or int16) plus the int32 neighbour entries (q - 1;
+    the rest population needs none).  Pull streaming reads the table every
+    step; the AA pattern only on odd steps, so its average over a step pair
+    is (q - 1) * 2 B.  The fused AA step pair ("aa_pairs", slab chunks) reads
+    and writes the populations once per pair, the odd step finding the even
+    step's output in L2: per step half of 2 q elem + 4 (q - 1)."""
+    elem = {"fp32": 4, "fp16": 2, "i16": 2}[storage]
+    if streaming == "aa_pairs":
+        return (2 * q * elem + 4 * (q - 1)) // 2
     table = {"pull": 4 * (q - 1), "aa": 2 * (q - 1)}[streaming]
     return 2 * q * elem + table
 

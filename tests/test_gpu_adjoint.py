@@ -119,3 +119,61 @@ def test_autograd_function_matches_objective_grad():
     assert np.array_equal(mean.grad.numpy(), 3.0 * ref["dmean"])
     assert np.array_equal(amp.grad.numpy(), 3.0 * ref["damp"])
     assert np.array_equal(phase.grad.numpy(), 3.0 * ref["dphase"])
+
+
+def velocity_inlet_tube(q, storage, streaming, tau=0.7, seed=4):
+    """The pulsatile tube with its inlet (iolet 0) a velocity iolet: a
+    parabolic weight profile across the inlet sites, speed schedule
+    0.002 + 0.0005 sin(2 pi t / 9 + 0.4) along the inward normal +z."""
+    g = pulsatile_tube()
+    nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
+    x, y, z = g.xyz.T.astype(np.float64)
+    prof = np.clip(1.0 - ((x - 4.0) ** 2 + (y - 4.0) ** 2) / 20.25, 0.05, None)
+    bc = dict(iolet_kind=[1, 0], iolet_normal=[[0.0, 0.0, 1.0], [0.0, 0.0, 0.0]], velocity_weight=prof)
+    io = dict(rho_mean=np.array([0.002, 0.999]), amp=np.array([0.0005, 0.0003]),
+              period=np.array([9.0, 13.0]), phase=np.array([0.4, 1.3]))
+    L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, streaming=streaming, **io, **bc)
+    rng = np.random.default_rng(seed)
+    f0 = oracle.rest_state(q, g.n) * (1.0 + 0.002 * (2.0 * rng.random((q, g.n)) - 1.0))
+    obc = dict(io_kind=np.array([1, 0]), io_normal=np.array(bc["iolet_normal"]), weight=prof)
+    f0 = oracle.default().run_bc(q, nbr, link, tau, f0, 60, **obc, **io)
+    L.set_populations(f0)
+    L.set_time(60)
+    has_wall = (link == 1).any(axis=0)
+    weight = ((z >= 4) & (z < 12) & has_wall).astype(np.float64)
+    return g, nbr, link, L, f0, weight, obc, io
+
+
+@pytest.mark.parametrize("streaming", [lbm.STREAM_PULL, lbm.STREAM_AA])
+@pytest.mark.parametrize("q,kind", [(15, lbm.OBJ_WSS), (19, lbm.OBJ_DENSITY)])
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_adjoint_with_a_velocity_iolet_matches_oracle(q, kind, storage, streaming):
+    """Gradients through a velocity (Ladd) inlet: dJ/dtau and the derivatives
+    with respect to the inlet's speed schedule (mean, amp, phase) and the
+    outlet's density schedule, and dJ/df0, against the FP64 oracle."""
+    tau, nsteps = 0.7, 14
+    g, nbr, link, L, f0, weight, obc, io = velocity_inlet_tube(q, storage, streaming, tau)
+    t0, tb, te, scale = 60, 63, 75, 1.0 / 12
+    got = L.objective_grad(kind, weight, nsteps, tb, te, scale=scale, n_snap=4, want_df0=True)
+    ref = oracle.default().gradient(q, nbr, link, tau, f0, nsteps, kind, weight, tb, te, scale=scale,
+                                    t0=t0, want_lam0=True, **obc, **io)
+    errs = dict(J=rel(got["J"], ref["J"]), dtau=rel(got["dtau"], ref["dtau"]),
+                dmean=rel(got["dmean"], ref["dmean"]), damp=rel(got["damp"], ref["damp"]),
+                dphase=rel(got["dphase"], ref["dphase"]), df0=rel(got["df0"], ref["lam0"]))
+    print("velocity-iolet adjoint", q, storage, kind, streaming, errs, "dU/dmean", ref["dmean"][0])
+    assert abs(ref["dmean"][0]) > 0.0
+    for k, v in errs.items():
+        assert v <= TOL[storage], (k, v)
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16])
+def test_velocity_iolet_adjoint_aa_equals_pull(storage):
+    """The AA-form sweep gives the pull-form sweep's gradients bit for bit
+    with a velocity inlet too."""
+    q = 19
+    outs = []
+    for streaming in (lbm.STREAM_PULL, lbm.STREAM_AA):
+        g, nbr, link, L, f0, weight, obc, io = velocity_inlet_tube(q, storage, streaming)
+        outs.append(L.objective_grad(lbm.OBJ_WSS, weight, 15, 62, 76, n_snap=3, want_df0=True))
+    for k in ("J", "dtau", "dmean", "damp", "dphase", "df0"):
+        assert np.array_equal(np.asarray(outs[0][k]), np.asarray(outs[1][k])), k

@@ -41,7 +41,7 @@ def contexts(q, storage, pre, seed=5):
 
 
 @pytest.mark.parametrize("q", [15, 19])
-@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16])
+@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16, lbm.STORE_I16])
 @pytest.mark.parametrize("kind", [lbm.OBJ_WSS, lbm.OBJ_DENSITY])
 @pytest.mark.parametrize("pre", [0, 1])
 def test_aa_sweep_equals_pull_sweep(q, storage, kind, pre):

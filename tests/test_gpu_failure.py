@@ -34,13 +34,16 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
 
 
 FORMS = [(lbm.STORE_FP32, lbm.STREAM_PULL), (lbm.STORE_FP16, lbm.STREAM_PULL),
-         (lbm.STORE_FP32, lbm.STREAM_AA), (lbm.STORE_FP16, lbm.STREAM_AA)]
+         (lbm.STORE_FP32, lbm.STREAM_AA), (lbm.STORE_FP16, lbm.STREAM_AA),
+         (lbm.STORE_I16, lbm.STREAM_PULL), (lbm.STORE_I16, lbm.STREAM_AA)]
 
 
 def small(storage=lbm.STORE_FP32, streaming=lbm.STREAM_PULL, q=19, seed=91):
     g = G.random_mask((9, 8, 7), p=0.6, seed=seed, n_iolets=2)
     nbr, link = lbm.links_build(q, g.xyz, g.io_xyz, g.io_id, g.periodic)
-    L = lbm.Lattice(q, g.xyz, nbr, link, 0.7, storage=storage, streaming=streaming, rho_mean=g.rho_mean)
+    # (int16: a coarse scale whose range, 8, holds the fast sites of these tests)
+    kw = {"fp16_scale_log2": 12} if storage == lbm.STORE_I16 else {}
+    L = lbm.Lattice(q, g.xyz, nbr, link, 0.7, storage=storage, streaming=streaming, rho_mean=g.rho_mean, **kw)
     return g, nbr, link, L
 
 
@@ -57,8 +60,10 @@ def fast_site_state(q, n, x, ux):
 def with_nan(L, storage, i, x):
     """The raw state blob of L with slot (i, x) set to a NaN."""
     blob = L.get_state().copy()
-    esz = 2 if storage == lbm.STORE_FP16 else 4
-    nan = np.array([0x7E00], np.uint16) if storage == lbm.STORE_FP16 else np.array([np.nan], np.float32)
+    esz = 4 if storage == lbm.STORE_FP32 else 2
+    # fp16: a NaN; int16: the saturation code, which reads as NaN
+    nan = {lbm.STORE_FP16: np.array([0x7E00], np.uint16), lbm.STORE_I16: np.array([32767], np.int16),
+           lbm.STORE_FP32: np.array([np.nan], np.float32)}[storage]
     npad = (blob.nbytes - 8) // (19 * esz)
     off = (i * npad + x) * esz
     blob[off:off + esz] = nan.view(np.uint8)
@@ -108,12 +113,13 @@ def test_checked_steps_match_unchecked_bitwise(storage, streaming):
     assert np.array_equal(A.get_state(), B.get_state())
 
 
-@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16])
+@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16, lbm.STORE_I16])
 def test_non_finite_state_is_reported(storage):
     g, nbr, link, L = small(storage)
     f = oracle_rest(19, g.n)
     before = L.get_state()
-    for bad in (np.nan, np.inf, 5.0 if storage == lbm.STORE_FP16 else 1e39):
+    out_of_range = {lbm.STORE_FP32: 1e39, lbm.STORE_FP16: 5.0, lbm.STORE_I16: 20.0}[storage]
+    for bad in (np.nan, np.inf, out_of_range):
         f2 = f.copy()
         f2[3, 11] = bad
         with pytest.raises(lbm.LbmError) as ei:
@@ -150,7 +156,7 @@ def test_guard_words_survive_every_call(storage, streaming):
     # positive control: a state blob whose plane padding differs
     good = L.get_state()
     blob = good.copy()
-    esz = 2 if storage == lbm.STORE_FP16 else 4
+    esz = 4 if storage == lbm.STORE_FP32 else 2
     blob[g.n * esz:g.n * esz + esz] = 0  # first padding slot of plane 0
     L.set_state(blob)
     assert not L.check_guards()

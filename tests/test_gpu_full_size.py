@@ -35,7 +35,7 @@ def lattice(tree, storage, streaming=lbm.STREAM_PULL):
                        period=g.period, phase=g.phase, streaming=streaming)
 
 
-@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16])
+@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16, lbm.STORE_I16])
 def test_aa_equals_pull_on_the_tree(tree, storage):
     A = lattice(tree, storage, lbm.STREAM_AA)
     P = lattice(tree, storage)

@@ -18,16 +18,16 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover - CPU containers
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-FP32, FP16 = lbm.STORE_FP32, lbm.STORE_FP16
-TOL_MACRO = {FP32: 1e-5, FP16: 2e-3}
-TOL_POP = {FP32: 1e-5, FP16: 2e-3}
+FP32, FP16, I16 = lbm.STORE_FP32, lbm.STORE_FP16, lbm.STORE_I16
+TOL_MACRO = {FP32: 1e-5, FP16: 2e-3, I16: 2e-3}
+TOL_POP = {FP32: 1e-5, FP16: 2e-3, I16: 2e-3}
 # Wall shear stress is formed from g_i - feq_i, the non-equilibrium part of
 # the populations, about a tenth of the stored deviations next to the walls
 # of these flows.  A storage rounding of relative size e on the deviations
 # (fp32: 2^-24; fp16: at most 2^-11 = 4.9e-4) therefore reaches the WSS
 # amplified about tenfold: fp32 stays far below the 1e-5 bar of the other
 # fields, fp16 below 5e-3 (measured: 2e-7 and 0.9e-3 on the straight tube).
-TOL_WSS = {FP32: 1e-5, FP16: 5e-3}
+TOL_WSS = {FP32: 1e-5, FP16: 5e-3, I16: 5e-3}
 
 
 def rel_l2(a, b):
@@ -74,7 +74,7 @@ def test_device_link_table_round_trip(q, geom):
 
 
 @pytest.mark.parametrize("q", [15, 19])
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_rest_state_is_exact(q, storage):
     g = G.tube(radius=4, length=12, nx=9, ny=9, rho_in=1.0, rho_out=1.0)
     L, _, _ = make(g, q, 0.7, storage)
@@ -84,13 +84,14 @@ def test_rest_state_is_exact(q, storage):
     assert L.time == 50
 
 
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_tube_poiseuille_1000_steps(storage):
     """Straight tube r = 8, 17x17x64, D3Q15, tau = 0.8, rho 1.001 -> 0.999,
     from rest, 1000 steps: rho and u against the FP64 oracle."""
     q, tau = 15, 0.8
     g = G.tube()
-    L, nbr, link = make(g, q, tau, storage)
+    # (int16: the finest scale that holds this flow's deviations, < 8e-4)
+    L, nbr, link = make(g, q, tau, storage, **({"fp16_scale_log2": 24} if storage == I16 else {}))
     L.step(1000)
     rho, u, wss = [t.cpu().numpy() for t in L.macros()]
     # rho - rho0 summed in float64 from the stored populations (the float32
@@ -110,15 +111,21 @@ def test_tube_poiseuille_1000_steps(storage):
 
 
 @pytest.mark.parametrize("q", [15, 19])
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 @pytest.mark.parametrize("geom", ["mask", "mask_periodic"])
 def test_random_state_short_runs(q, storage, geom):
     """Random near-equilibrium state, pulsatile iolets, ragged small domain:
-    populations after 1, 7 and 40 steps."""
+    populations after 1, 7 and 40 steps.  (int16 fixed point resolves a
+    uniform step within a fixed range: a state ten times closer to rest at
+    the scale 2^-26, range 4.9e-4.)"""
     g = GEOMS[geom]()
     tau = 0.63
-    L, nbr, link = make(g, q, tau, storage)
-    f0 = near_rest(q, g.n, seed=5)
+    if storage == I16:
+        L, nbr, link = make(g, q, tau, storage, fp16_scale_log2=26)
+        f0 = near_rest(q, g.n, seed=5, amp=0.001)
+    else:
+        L, nbr, link = make(g, q, tau, storage)
+        f0 = near_rest(q, g.n, seed=5)
     L.set_populations(f0)
     L.set_time(3)
     of = f0.copy()
@@ -149,7 +156,7 @@ def test_mass_reduction_and_conservation(q):
     assert m2 == m1  # deterministic
 
 
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_resume_is_bit_exact(storage):
     g = G.random_mask((9, 8, 7), p=0.6, seed=31, n_iolets=2)
     q, tau = 19, 0.75
@@ -267,7 +274,7 @@ def tree():
     return g, nbr, link
 
 
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_vessel_tree_full_size_one_step(tree, storage):
     """The benchmark workload (~10.8M sites) in the launch configuration the
     benchmark times: the device link table bit-exact, and every population of
@@ -301,7 +308,7 @@ def test_vessel_tree_full_size_one_step(tree, storage):
 
 
 @pytest.mark.parametrize("q", [15, 19])
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_weighted_sums_match_oracle(q, storage):
     """Float64 reductions of the current state (wall shear stress and density
     over weighted site subsets) against the oracle's objective of the same

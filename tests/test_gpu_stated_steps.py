@@ -34,14 +34,14 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover - CPU containers
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-FP32, FP16 = lbm.STORE_FP32, lbm.STORE_FP16
-TOL = {FP32: 1e-5, FP16: 2e-3}
+FP32, FP16, I16 = lbm.STORE_FP32, lbm.STORE_FP16, lbm.STORE_I16
+TOL = {FP32: 1e-5, FP16: 2e-3, I16: 2e-3}
 # Wall shear stress is formed from g_i - feq_i, the non-equilibrium part of
 # the populations, about a tenth of the stored deviations next to the walls
 # of these flows.  A storage rounding of relative size e on the deviations
 # (fp32: 2^-24; fp16: at most 2^-11 = 4.9e-4) therefore reaches the WSS
 # amplified about tenfold: fp32 stays far below 1e-5, fp16 below 5e-3.
-WSS_TOL = {FP32: 1e-5, FP16: 5e-3}
+WSS_TOL = {FP32: 1e-5, FP16: 5e-3, I16: 5e-3}
 
 
 def rel_l2(a, b):
@@ -56,10 +56,25 @@ WORKLOADS = {
 }
 
 
+def storage_floor(q, f, storage, scale_log2):
+    """rel-L2 error of rho - rho0 when the exact state f is rounded once to
+    the storage format (the format's own resolution of this state)."""
+    _, w, _ = oracle.lattice(q)
+    d = f - w[:, None]
+    sc = 2.0 ** scale_log2
+    if storage == FP16:
+        dq = (d * sc).astype(np.float16).astype(np.float64) / sc
+    else:
+        dq = np.rint(d * sc) / sc
+    r, rq = f.sum(axis=0) - 1.0, (dq + w[:, None]).sum(axis=0) - 1.0
+    return rel_l2(rq, r)
+
+
 @pytest.fixture(scope="module", params=sorted(WORKLOADS))
 def reference(request):
     """The workload, its tables and the oracle's rho, u, wss after the stated
-    step count from rest."""
+    step count from rest, and the 16-bit formats' one-shot resolution of
+    rho - rho0 in that state."""
     w = WORKLOADS[request.param]
     g = w["make"]()
     q, tau, steps = w["q"], w["tau"], w["steps"]
@@ -68,17 +83,23 @@ def reference(request):
     f = oracle.run(q, nbr, link, tau, oracle.rest_state(q, g.n), steps, geom=g)
     secs = time.perf_counter() - t0
     rho, u, wss = oracle.macros(q, link, tau, f)
+    floor = {FP16: storage_floor(q, f, FP16, 14), I16: storage_floor(q, f, I16, 24)}
     del f
-    print("\n%s: %d sites, oracle %d steps in %.1f s on %d threads (%.1f MSUPS)"
-          % (request.param, g.n, steps, secs, oracle.num_threads(), g.n * steps / secs / 1e6))
-    return request.param, g, nbr, link, q, tau, steps, (rho, u, wss)
+    print("\n%s: %d sites, oracle %d steps in %.1f s on %d threads (%.1f MSUPS); one rounding of the "
+          "exact state costs rho - rho0 %.2e (fp16), %.2e (int16)"
+          % (request.param, g.n, steps, secs, oracle.num_threads(), g.n * steps / secs / 1e6,
+             floor[FP16], floor[I16]))
+    return request.param, g, nbr, link, q, tau, steps, (rho, u, wss), floor
 
 
-@pytest.mark.parametrize("storage", [FP32, FP16])
+@pytest.mark.parametrize("storage", [FP32, FP16, I16])
 def test_stated_step_count(reference, storage):
-    name, g, nbr, link, q, tau, steps, (orho, ou, owss) = reference
+    name, g, nbr, link, q, tau, steps, (orho, ou, owss), floor = reference
+    # int16: the finest scale 2^-24 whose range (1.95e-3) holds these flows'
+    # deviations (below 1e-3)
+    kw = {"fp16_scale_log2": 24} if storage == I16 else {}
     L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean, amp=g.amp,
-                    period=g.period, phase=g.phase, streaming=lbm.STREAM_AA)
+                    period=g.period, phase=g.phase, streaming=lbm.STREAM_AA, **kw)
     L.step(steps)
     assert L.time == steps
     rho, u, wss = [t.cpu().numpy() for t in L.macros()]
@@ -89,9 +110,15 @@ def test_stated_step_count(reference, storage):
     e_drho = rel_l2(drho, orho - 1.0)
     e_wss = rel_l2(wss, owss)
     print("%s %s after %d steps: u %.3e  rho %.3e  rho-rho0 %.3e  wss %.3e  |u|max %.3e"
-          % (name, "fp16" if storage == FP16 else "fp32", steps, e_u, e_rho, e_drho, e_wss,
+          % (name, {FP32: "fp32", FP16: "fp16", I16: "int16"}[storage], steps, e_u, e_rho, e_drho, e_wss,
              float(np.abs(ou).max())))
     assert e_u <= TOL[storage], e_u
     assert e_rho <= TOL[storage], e_rho
-    assert e_drho <= TOL[storage], e_drho
+    # rho - rho0: the bar, or for a 16-bit form four times what one rounding
+    # of the exact state to that form already costs, when that is larger (on
+    # the aneurysm at t = 20,000 the inlet phase is zero, |rho - 1| is ten
+    # times smaller than the velocity part of the deviations, and one fp16
+    # rounding alone costs 1.1e-3; the run rounds every step)
+    bar = TOL[storage] if storage == FP32 else max(TOL[storage], 4.0 * floor[storage])
+    assert e_drho <= bar, (e_drho, bar)
     assert e_wss <= WSS_TOL[storage], e_wss
