@@ -121,8 +121,8 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              q < 1/2 and x_b fluid: f_opp(i)(x, t+1) = 2q f*_i(x) + (1 - 2q) f*_i(x_b);
  *              q >= 1/2: f_opp(i)(x, t+1) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_opp(i)(x);
  *              q < 1/2 without a fluid x_b: the half-way rule.  Both
- *              streaming forms (bitwise the same results); not
- *              differentiated (lbm_objective_grad).
+ *              streaming forms (bitwise the same results); differentiated
+ *              by lbm_objective_grad like the half-way walls.
  *   site_order the order the device keeps the sites in (every result is the
  *              same, outputs are in caller order; the sites with iolet or
  *              interpolated-wall links come last in all of them):
@@ -138,12 +138,13 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              LBM_ORDER_SLABS (3): row order, and with LBM_STREAM_AA the
  *              bulk sites are cut into chunks of whole z planes (about 16 MB
  *              of populations each) and lbm_step runs each even step and the
- *              odd step after it as one pass over them: chunk c's even step
- *              is launched with chunk c - 2's odd step, which then reads the
- *              even step's output back from L2 instead of HBM (two LB steps
- *              per HBM pass over the populations; the same results to the
- *              bit).  Where a site's neighbour lies more than one chunk away
- *              (a periodic z axis) the pairs run unfused. */
+ *              odd step after it as one persistent launch over them: the odd
+ *              step of a chunk runs as soon as the even steps of the chunk
+ *              and its two neighbours are done, two chunks behind the even
+ *              steps, and reads the even step's output back from L2 instead
+ *              of HBM (the same results to the bit).  Where a site's
+ *              neighbour lies more than one chunk away (a periodic z axis)
+ *              the pairs run unfused. */
 typedef struct {
     int32_t q;
     int32_t storage;
@@ -252,15 +253,19 @@ lbm_status lbm_mass(lbm_ctx *ctx, double *out);
  * by its count).  Synchronous. */
 lbm_status lbm_weighted_sum(lbm_ctx *ctx, int32_t kind, const double *weight_d, double *out);
 
-/* Failure detection, checked on its own: the table-staged step waits for its
- * bulk copies on mbarriers with a bounded number of polls (about 4M); a step
- * kernel that gives up sets an error flag and returns, and lbm_mass reports
- * LBM_ERR_CUDA.  A copy it gave up on may still land afterwards, so the
- * output of that launch is undefined (see lbm_mass).  This call runs that bounded
- * wait, with `limit` polls (1 .. 2^24), on a barrier that no copy completes,
- * and stores 1 in *gave_up when the wait gave up (it always should).  The
- * context and the device stay usable.  Synchronous on cuda_stream.  The
- * paper has no counterpart. */
+/* Failure detection, checked on its own: the table-staged steps wait for
+ * their bulk copies on mbarriers with a bounded number of polls (about 4M),
+ * and the blocks of a fused AA step pair (LBM_ORDER_SLABS) wait for the even
+ * steps of neighbouring chunks on counters, again with a bounded number of
+ * polls (about 2M, a second or so); a step kernel that gives up sets an
+ * error flag and returns, and lbm_mass reports LBM_ERR_CUDA.  A copy it gave
+ * up on may still land afterwards, and a fused pair that gave up has updated
+ * only part of the sites, so the output of that launch is undefined (see
+ * lbm_mass).  This call runs both bounded waits, with `limit` polls each
+ * (1 .. 2^24), on a barrier that no copy completes and on a counter that
+ * nothing raises, and stores 1 in *gave_up when both waits gave up (they
+ * always should).  The context and the device stay usable.  Synchronous on
+ * cuda_stream.  The paper has no counterpart. */
 lbm_status lbm_check_wait_timeout(uint32_t limit, void *cuda_stream, int32_t *gave_up);
 
 /* Failure detection: an instability check on the stored state.  With
@@ -335,8 +340,7 @@ lbm_status lbm_get_links(lbm_ctx *ctx, int32_t *nbr, uint8_t *link);
  * the paper, whose method is the forward solver only (Section 2); this is
  * the differentiation of that solver.  Velocity (Ladd) iolets are
  * differentiated too (their mean, amp and phase are those of the speed
- * schedule U_k(t)); contexts with interpolated walls are not
- * (LBM_ERR_STATE). */
+ * schedule U_k(t)), and so are interpolated (BFL) walls. */
 enum { LBM_OBJ_WSS = 0, LBM_OBJ_DENSITY = 1 };
 
 /* J = scale * sum over the states f(t) with t_begin <= t < t_end (t counted

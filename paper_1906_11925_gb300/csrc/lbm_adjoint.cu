@@ -17,6 +17,16 @@
 // A velocity (Ladd) iolet link bounces like a wall less 6 w_i rho c_i.u_b:
 //   lam*_i = lam_opp(i)(x, t+1), every lam_j gains -6 w_i (c_i.u_b) lam_opp(i),
 //   dJ/dU_k(t) += -6 w_i rho weight(x) (c_i.n_k) lam_opp(i)(x, t+1).
+// An interpolated (BFL) wall link p of x (the wall along c_opp(p) at the
+// fraction q of the link, the fluid upstream site x_u = x + c_p):
+//   f_p(x, t+1) = 2q f*_opp(p)(x) + (1 - 2q) f*_opp(p)(x_u)   (q < 1/2, x_u fluid),
+//                 f*_opp(p)(x)                              (q < 1/2, no x_u),
+//                 f*_opp(p)(x)/(2q) + (1 - 1/(2q)) f*_p(x)  (q >= 1/2),
+// so lam*_opp(p)(x) = 2q, 1 or 1/(2q) times lam_p(x, t+1); for q >= 1/2
+// lam*_p(x) gains (1 - 1/(2q)) lam_p(x, t+1); and for q < 1/2 the upstream
+// site's lam*_opp(p)(x_u) = lam_opp(p)(x, t+1) gains (1 - 2q) lam_p(x, t+1),
+// which x adds to the lam_opp(p) it stores, so that every site still reads
+// one value per link (taken out again for dJ/df(t0)).
 // Parameter derivatives of step t:
 //   dJ/dtau      += sum_i lam*_i (f_i - feq_i) / tau^2,
 //   dJ/drho_k(t) += sum over iolet-k links of lam_opp(i)(x, t+1) feq_opp(i)/rho_k,
@@ -159,7 +169,7 @@ __device__ __forceinline__ Stress stress(const float (&ne)[Q]) {
     return p;
 }
 
-template <int Q>
+template <int Q, bool BFL>
 __device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q], const Stress &P,
                                           float rho, float ir, float ux, float uy, float uz,
                                           float usq15, float mx, float scale, float wss_dlog,
@@ -167,7 +177,7 @@ __device__ __forceinline__ float wss_term(const DevLattice &L, const int (&s)[Q]
     int wn0 = 0, wn1 = 0, wn2 = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if (s[i] == -1) {
+        if (s[i] == -1 || (BFL && is_bfl(s[i]))) {  // half-way and interpolated walls
             wn0 += cdir<Q>(i, 0);
             wn1 += cdir<Q>(i, 1);
             wn2 += cdir<Q>(i, 2);
@@ -242,7 +252,7 @@ enum { FORM_PULL = 0, FORM_AA_EVEN = 1, FORM_AA_ODD = 2, FORM_AA_SLOTS = 3 };
 // state P of time t); tab(i) is the table entry of population i at x (from
 // registers or global memory).  Adds the
 // site's terms of J and dJ/dtau to j_site and dtau_site (float).
-template <int Q, int HALF, bool WSS, bool IO, int FORM, typename Tab, typename TabOut>
+template <int Q, int HALF, bool WSS, bool IO, int FORM, bool BFL, typename Tab, typename TabOut>
 __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename AdjLoad<HALF>::T *__restrict__ P,
                                              const float *lam_next, float *lam_out, const AdjStep &st,
                                              const AdjObjective &obj, int x, const Tab &tab,
@@ -266,6 +276,19 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
             e = si >= 0 ? a * np + (unsigned)si : b * np + (unsigned)x;
         }
         ne[i] = R::ld(P + e, L.inv_scale);
+    }
+    if (BFL) {
+        // interpolated walls: the slot of a q < 1/2 link p with a fluid
+        // upstream site holds 2q f*; f_p(t) adds (1 - 2q) times the
+        // population opp(p) pulled from that site (the forward gather)
+#pragma unroll
+        for (int p = 1; p < Q; ++p) {
+            const int sp = tab(p);
+            if (is_bfl(sp)) {
+                const float qv = bfl_q(sp);
+                if (qv < 0.5f && tab(opp(p)) >= 0) ne[p] = fmaf(1.0f - 2.0f * qv, ne[opp(p)], ne[p]);
+            }
+        }
     }
     float drho = ne[0], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -321,6 +344,16 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
             if (sp >= 0) {
                 ls[i] = FORM == FORM_AA_EVEN ? lam_next[(unsigned)opp(i) * np + (unsigned)x]
                                              : lam_next[(unsigned)i * np + (unsigned)sp];
+            } else if (BFL && is_bfl(sp)) {
+                // interpolated wall along c_i (population p = opp(i) arrives
+                // from the wall side): f*_i feeds f_p(x, t+1) with 2q (q < 1/2
+                // and a fluid upstream site), 1 (q < 1/2, none) or 1/(2q)
+                // (a rounded product: left to the code generator, the multiply
+                // may fuse with a later add in one kernel and not in another,
+                // and the AA and pull sweeps would no longer agree to the bit)
+                const float qv = bfl_q(sp);
+                const float lo = lam_next[(unsigned)opp(i) * np + (unsigned)x];
+                ls[i] = __fmul_rn(qv < 0.5f ? (tab(i) >= 0 ? 2.0f * qv : 1.0f) : 0.5f / qv, lo);
             } else if (!IO || sp == -1) {
                 ls[i] = lam_next[(unsigned)opp(i) * np + (unsigned)x];
             } else if ((st.io.vel_mask >> (-2 - sp)) & 1ull) {
@@ -357,6 +390,18 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
                 io_acc[slot] += (double)drk;
                 io_acc[plane + slot] += (double)drk * st.dsin[k];
                 io_acc[2 * plane + slot] += (double)drk * st.dacos[k];
+            }
+        }
+    }
+    if (BFL && has_next) {
+        // q >= 1/2: f*_p feeds f_p(x, t+1) as well, with 1 - 1/(2q)
+#pragma unroll
+        for (int p = 1; p < Q; ++p) {
+            const int sp = tab(p);
+            if (is_bfl(sp)) {
+                const float qv = bfl_q(sp);
+                if (qv >= 0.5f)
+                    ls[p] = fmaf(1.0f - 0.5f / qv, lam_next[(unsigned)p * np + (unsigned)x], ls[p]);
             }
         }
     }
@@ -413,7 +458,7 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
                     else
                         s[i] = tab(i);
                 }
-                j_site = wss_term<Q>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
+                j_site = wss_term<Q, BFL>(L, s, Pst, rho, ir, ux, uy, uz, usq15, mx, obj.scale_f,
                                      obj.wss_dlog_f, lam, &dtau_site);
             } else if (obj.kind == 1) {
                 // m (rho - rho0): the host adds rho0 sum(m) per state in
@@ -422,6 +467,20 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
                 const float sm = obj.scale_f * mx;
 #pragma unroll
                 for (int j = 0; j < Q; ++j) lam[j] += sm;
+            }
+        }
+    }
+    if (BFL) {
+        // lam_opp(p)(x, t) is read by the upstream site x + c_p (fluid, q <
+        // 1/2) as its lam* of population opp(p), whose post-collision value
+        // also fed f_p(x, t) with (1 - 2q): it is stored with that term added
+        // (k_lam_to_caller takes it out again for dJ/df(t0))
+#pragma unroll
+        for (int p = 1; p < Q; ++p) {
+            const int sp = tab(p);
+            if (is_bfl(sp)) {
+                const float qv = bfl_q(sp);
+                if (qv < 0.5f && tab(opp(p)) >= 0) lam[opp(p)] = fmaf(1.0f - 2.0f * qv, lam[p], lam[opp(p)]);
             }
         }
     }
@@ -447,7 +506,7 @@ __device__ __forceinline__ void adjoint_site(const DevLattice &L, const typename
 // iolet link, IO = false) or the iolet sites (IO = true), one block per
 // 256-site tile.  WSS = the wall-shear-stress objective term is active at
 // this step.
-template <int Q, int HALF, bool WSS, bool IO>
+template <int Q, int HALF, bool WSS, bool IO, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS : HGB_ADJ_MINB)
 k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
           const float *__restrict__ lam_next, float *__restrict__ lam_out, const AdjStep st,
@@ -463,8 +522,8 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
 #pragma unroll
         for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
         auto tab = [&](int i) { return s[i]; };
-        adjoint_site<Q, HALF, WSS, IO, FORM_PULL>(L, P, lam_next, lam_out, st, obj, x, tab, tab, io_acc, j_site,
-                                                  dtau_site);
+        adjoint_site<Q, HALF, WSS, IO, FORM_PULL, BFL>(L, P, lam_next, lam_out, st, obj, x, tab, tab, io_acc,
+                                                       j_site, dtau_site);
     }
     const float2 bsum = block_sum_f2(j_site, dtau_site, part);
     if (threadIdx.x == 0) {
@@ -477,7 +536,7 @@ k_adjoint(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P,
 // One adjoint step of the AA form (FORM_AA_EVEN or FORM_AA_ODD, see above) over
 // the sites [x_begin, x_end), in place on the one adjoint buffer lam (read as
 // lam(t+1), written as lam(t)); tiles and block sums as in k_adjoint.
-template <int Q, int HALF, bool WSS, bool IO, bool ODD>
+template <int Q, int HALF, bool WSS, bool IO, bool ODD, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, WSS ? HGB_ADJ_MINB_WSS
                                               : IO ? HGB_ADJ_MINB : ODD ? HGB_ADJ_MINB_AA_ODD : HGB_ADJ_MINB_AA_EVEN)
 k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P, float *lam, int has_next,
@@ -509,22 +568,23 @@ k_adjoint_aa(const DevLattice L, const typename AdjLoad<HALF>::T *__restrict__ P
                 asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(L.slots + (unsigned)(i - 1) * np + (unsigned)x));
                 return (int)v;
             };
-            adjoint_site<Q, HALF, WSS, false, FORM_AA_SLOTS>(L, P, lin, lam, st, obj, x, tab, reload_slot, io_acc,
-                                                             j_site, dtau_site);
+            adjoint_site<Q, HALF, WSS, false, FORM_AA_SLOTS, false>(L, P, lin, lam, st, obj, x, tab, reload_slot,
+                                                                    io_acc, j_site, dtau_site);
         } else if (ODD || IO) {
             int s[Q];
             s[0] = 0;
 #pragma unroll
             for (int i = 1; i < Q; ++i) s[i] = __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x);
             auto tab = [&](int i) { return s[i]; };
-            adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab,
-                                                                            reload, io_acc, j_site, dtau_site);
+            adjoint_site<Q, HALF, WSS, IO, ODD ? FORM_AA_ODD : FORM_AA_EVEN, BFL>(L, P, lin, lam, st, obj, x, tab,
+                                                                                 reload, io_acc, j_site,
+                                                                                 dtau_site);
         } else {
             // even step of a bulk site: the table only for the wall normals
             // of the wall-shear-stress term
             auto tab = [&](int i) { return __ldg(L.tab + (unsigned)(i - 1) * np + (unsigned)x); };
-            adjoint_site<Q, HALF, WSS, false, FORM_AA_EVEN>(L, P, lin, lam, st, obj, x, tab, tab, io_acc, j_site,
-                                                           dtau_site);
+            adjoint_site<Q, HALF, WSS, false, FORM_AA_EVEN, false>(L, P, lin, lam, st, obj, x, tab, tab, io_acc,
+                                                                  j_site, dtau_site);
         }
     }
     const float2 bsum = block_sum_f2(j_site, dtau_site, part);
@@ -590,8 +650,25 @@ k_lam_to_caller(const DevLattice L, const float *__restrict__ lam, double *__res
     const int x = blockIdx.x * kBlock + threadIdx.x;
     if (x >= L.n) return;
     const int64_t xc = L.perm[x];
+    float v[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = (double)lam[(int64_t)i * L.npad + x];
+    for (int i = 0; i < Q; ++i) v[i] = lam[(int64_t)i * L.npad + x];
+    if (L.bfl && x >= L.n_bulk) {
+        // the stored lam_opp(p) of a q < 1/2 interpolated link with a fluid
+        // upstream site carries (1 - 2q) lam_p for that site: take it out
+        int s[Q];
+        s[0] = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = L.tab[(int64_t)(i - 1) * L.npad + x];
+#pragma unroll
+        for (int p = 1; p < Q; ++p)
+            if (is_bfl(s[p])) {
+                const float qv = bfl_q(s[p]);
+                if (qv < 0.5f && s[opp(p)] >= 0) v[opp(p)] = fmaf(-(1.0f - 2.0f * qv), v[p], v[opp(p)]);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[(int64_t)i * L.n + xc] = (double)v[i];
 }
 
 template <int Q, int HALF, bool WSS>
@@ -603,7 +680,10 @@ cudaError_t adjoint_impl(const DevLattice &L, const void *P, const float *lam_ne
     if (nb > 0)
         k_adjoint<Q, HALF, WSS, false><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, 0, nb, acc_block, io_acc);
-    if (ni > 0)
+    if (ni > 0 && L.bfl)
+        k_adjoint<Q, HALF, WSS, true, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
+            L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);
+    else if (ni > 0)
         k_adjoint<Q, HALF, WSS, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
             L, (const T *)P, lam_next, lam_out, st, obj, nb, L.n, acc_block, io_acc);
     return cudaGetLastError();
@@ -627,7 +707,10 @@ cudaError_t adjoint_aa_impl(const DevLattice &L, const void *P, float *lam, bool
     if (nb > 0)
         k_adjoint_aa<Q, HALF, WSS, false, ODD><<<(nb + kBlock - 1) / kBlock, kBlock, 0, s>>>(
             L, (const T *)P, lam, has_next ? 1 : 0, st, obj, 0, nb, acc_block, io_acc);
-    if (ni > 0)
+    if (ni > 0 && L.bfl)
+        k_adjoint_aa<Q, HALF, WSS, true, ODD, true><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
+            L, (const T *)P, lam, has_next ? 1 : 0, st, obj, nb, L.n, acc_block, io_acc);
+    else if (ni > 0)
         k_adjoint_aa<Q, HALF, WSS, true, ODD><<<(ni + kBlock - 1) / kBlock, kBlock, 0, t>>>(
             L, (const T *)P, lam, has_next ? 1 : 0, st, obj, nb, L.n, acc_block, io_acc);
     return cudaGetLastError();

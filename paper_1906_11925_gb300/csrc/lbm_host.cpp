@@ -47,6 +47,8 @@ constexpr int kGraphSteps = 32;
 #define HGB_SLAB_BYTES (16 << 20)
 #endif
 constexpr int64_t kSlabBytes = HGB_SLAB_BYTES;
+// sites per item of the fused pair's work list: one per thread of a block
+constexpr int kPairRun = 256;
 constexpr int kGraphRing = 8;
 static_assert(kGraphSteps % 2 == 0, "a chunk must restore the buffer roles");
 
@@ -66,8 +68,12 @@ struct lbm_ctx {
     int32_t *tab = nullptr, *perm = nullptr;
     uint32_t *slots = nullptr;  // slot table of the bulk step kernels (see DevLattice::slots)
     // LBM_ORDER_SLABS with AA streaming: bounds of the slab chunks of the bulk
-    // sites (empty: step pairs run unfused)
+    // sites (empty: step pairs run unfused) and the fused pair's work list
     std::vector<int> slab_chunks;
+    int4 *pair_items = nullptr;
+    int *pair_tiles = nullptr;
+    unsigned *pair_ctr = nullptr;
+    PairPlan pair_plan{};
     double io_mean[LBM_MAX_IOLETS] = {}, io_amp[LBM_MAX_IOLETS] = {};
     double io_period[LBM_MAX_IOLETS] = {}, io_phase[LBM_MAX_IOLETS] = {};
     int io_kind[LBM_MAX_IOLETS] = {};
@@ -302,7 +308,7 @@ bool pairs_fused(const lbm_ctx *c) {
 cudaError_t advance_pair(lbm_ctx *c, const IoletStep &io_even, const IoletStep &io_odd,
                          const IoletStep *io_dev_even = nullptr, const IoletStep *io_dev_odd = nullptr) {
     return launch_step_aa_pair(c->L, c->f_cur, io_even, io_odd, c->stream, io_dev_even, io_dev_odd,
-                               c->slab_chunks.data(), (int)c->slab_chunks.size() - 1);
+                               c->pair_plan);
 }
 
 // ---- CUDA graphs of lbm_step ----------------------------------------------
@@ -592,6 +598,9 @@ void free_ctx(lbm_ctx *c) {
     cudaFree(c->tab);
     cudaFree(c->vel_weight);
     cudaFree(c->slots);
+    cudaFree(c->pair_items);
+    cudaFree(c->pair_tiles);
+    cudaFree(c->pair_ctr);
     cudaFree(c->perm);
     cudaFree(c->partials);
     cudaFree(c->err_flag);
@@ -855,6 +864,39 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
     CKC(cudaMemsetAsync(c->flags, 0, 16, c->stream));
     CKC(cudaStreamSynchronize(c->stream));  // host vectors die at return
 #undef CKC
+    if (!slab_chunks.empty()) {
+        // the fused pair's work list: runs of up to kPairRun sites, chunk c's
+        // even runs, then chunk c - 2's odd runs, for c = 0 .. K + 1
+        const int K = (int)slab_chunks.size() - 1;
+        std::vector<int4> items;
+        std::vector<int> tiles((size_t)K);
+        auto runs = [&](int c, int odd) {
+            for (int a = slab_chunks[(size_t)c]; a < slab_chunks[(size_t)c + 1]; a += kPairRun)
+                items.push_back(make_int4(a, std::min(a + kPairRun, slab_chunks[(size_t)c + 1]), c, odd));
+        };
+        for (int c = 0; c < K + 2; ++c) {
+            if (c < K) {
+                const size_t before = items.size();
+                runs(c, 0);
+                tiles[(size_t)c] = (int)(items.size() - before);
+            }
+            if (c >= 2) runs(c - 2, 1);
+        }
+        const size_t ctr_bytes = sizeof(unsigned) * (size_t)(2 + K);
+        if (cudaMalloc((void **)&c->pair_items, sizeof(int4) * items.size()) != cudaSuccess ||
+            cudaMalloc((void **)&c->pair_tiles, sizeof(int) * tiles.size()) != cudaSuccess ||
+            cudaMalloc((void **)&c->pair_ctr, ctr_bytes) != cudaSuccess ||
+            cudaMemcpy(c->pair_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(c->pair_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemset(c->pair_ctr, 0, ctr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return fail(nullptr, LBM_ERR_CUDA, "allocation of the fused step pair's work list failed");
+        }
+        c->pair_plan = PairPlan{c->pair_items, (int)items.size(), c->pair_tiles, K, c->pair_ctr};
+    }
     c->perm_host.swap(perm);
     c->slab_chunks.swap(slab_chunks);
     {
@@ -1074,16 +1116,16 @@ HGB_API lbm_status lbm_check_wait_timeout(uint32_t limit, void *cuda_stream, int
     if (!gave_up) return fail(nullptr, LBM_ERR_ARG, "gave_up is NULL");
     if (limit < 1 || limit > (1u << 24)) return fail(nullptr, LBM_ERR_ARG, "limit must lie in [1, 2^24]");
     const cudaStream_t s = (cudaStream_t)cuda_stream;
-    int *flag = nullptr;
-    cudaError_t e = cudaMalloc((void **)&flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_wait_probe(limit, flag, s);
+    int *flag = nullptr;  // [0] the probe's flag bits, [1] a counter nothing raises
+    cudaError_t e = cudaMalloc((void **)&flag, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = launch_wait_probe(limit, flag, (const unsigned *)(flag + 1), s);
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(flag);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbm_check_wait_timeout");
-    *gave_up = h;
+    *gave_up = h == 3 ? 1 : 0;  // both waits gave up
     return LBM_OK;
 }
 
@@ -1486,8 +1528,6 @@ HGB_API lbm_status lbm_objective_grad(lbm_ctx *ctx, const lbm_objective *obj, in
         return fail(ctx, LBM_ERR_ARG, "objective kind must be LBM_OBJ_WSS or LBM_OBJ_DENSITY");
     if (ctx->n > 0 && !obj->weight) return fail(ctx, LBM_ERR_ARG, "objective weight is NULL");
     if (!std::isfinite(obj->scale)) return fail(ctx, LBM_ERR_ARG, "objective scale is not finite");
-    if (ctx->has_bfl)
-        return fail(ctx, LBM_ERR_STATE, "contexts with interpolated walls are not differentiated");
     if (nsteps < 0 || n_snap < 1) return fail(ctx, LBM_ERR_ARG, "need nsteps >= 0 and n_snap >= 1");
     if (!J) return fail(ctx, LBM_ERR_ARG, "J is NULL");
     if (ctx->state_undefined)

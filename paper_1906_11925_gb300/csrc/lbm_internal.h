@@ -23,14 +23,14 @@ constexpr int kTile = 256;
 // upstream site, is added when the site gathers); otherwise the whole
 // interpolated value.
 #if defined(__CUDACC__)
-#define HGB_HD __host__ __device__
+#define HGB_BFL_HD __host__ __device__
 #else
-#define HGB_HD
+#define HGB_BFL_HD
 #endif
 constexpr int32_t kBflMax = (int32_t)(0x80000000u + (1u << 24));
-HGB_HD inline bool is_bfl(int32_t e) { return e <= kBflMax; }
-HGB_HD inline float bfl_q(int32_t e) { return (float)((uint32_t)e ^ 0x80000000u) * (1.0f / 16777216.0f); }
-HGB_HD inline int32_t bfl_code(double q) {
+HGB_BFL_HD inline bool is_bfl(int32_t e) { return e <= kBflMax; }
+HGB_BFL_HD inline float bfl_q(int32_t e) { return (float)((uint32_t)e ^ 0x80000000u) * (1.0f / 16777216.0f); }
+HGB_BFL_HD inline int32_t bfl_code(double q) {
     const double k = q * 16777216.0 + 0.5;
     uint32_t u = (uint32_t)(k < 1.0 ? 1.0 : (k > 16777216.0 ? 16777216.0 : k));
     return (int32_t)(0x80000000u + u);
@@ -60,11 +60,12 @@ struct IoletStep {
 //   -1 -> wall link opp(i) at x (read own slot opp(i), halfway bounce-back);
 //   -2 - k -> iolet-k link opp(i) at x (read own slot opp(i), which the
 //   previous step filled with the iolet equilibrium).
-// Populations: f[i * npad + x] as float (fp32 storage) or __half bits
-// (fp16 storage) holding the deviation from w_i rho0 (times 2^S for fp16).
+// Populations: f[i * npad + x] as float (fp32 storage), __half bits (fp16
+// storage) or int16 (fixed point) holding the deviation from w_i rho0 (times
+// 2^S for the 16-bit forms).
 struct DevLattice {
     int q;
-    int storage;     // 0 fp32, 1 fp16
+    int storage;     // 0 fp32, 1 fp16, 2 int16
     int n;           // sites
     int n_bulk;      // sites [0, n_bulk) have no iolet link; [n_bulk, n) have
     int64_t npad;    // plane length (multiple of 128)
@@ -127,18 +128,34 @@ cudaError_t launch_step_aa(const DevLattice &L, void *A, bool odd, const IoletSt
                            const double *rho_io, cudaStream_t s, const SideStream *side = nullptr,
                            const IoletStep *io_dev = nullptr);
 
-// An even AA step and the odd step after it in one pass over the slab chunks
-// [chunk[c], chunk[c + 1]) of the bulk sites (c < nchunks; the chunks are
-// whole z planes of the LBM_ORDER_SLABS order, each site's neighbours in its
-// own or the two neighbouring chunks): A in natural layout on entry and exit.
-// io_dev_even / io_dev_odd, when not null, replace the iolet records.
+// The work list of a fused AA step pair (LBM_ORDER_SLABS): the bulk sites
+// fall into chunks of whole z planes, each site's neighbours in its own or
+// the two neighbouring chunks; an item is a run of at most 256 sites of one
+// chunk and one of the two steps.  Items are listed chunk c's even runs, then
+// chunk c - 2's odd runs, for c = 0 .. nchunks + 1, so every even run that an
+// odd run depends on comes earlier in the list.  All device memory.
+struct PairPlan {
+    const int4 *items;  // {first site, end site, chunk, 1 for the odd step}
+    int n_items;
+    const int *tiles;   // [nchunks] even runs per chunk
+    int nchunks;
+    // [0] next item, [1] blocks finished, [2, 2 + nchunks) even runs done per
+    // chunk; zero between launches (the last block to finish clears them)
+    unsigned *ctr;
+};
+
+// An even AA step and the odd step after it in one pass over the bulk sites,
+// by the plan W: A in natural layout on entry and exit.  io_dev_even /
+// io_dev_odd, when not null, replace the iolet records.
 cudaError_t launch_step_aa_pair(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
                                 cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
-                                const int *chunk, int nchunks);
+                                const PairPlan &W);
 
-// The bounded mbarrier wait of the staged step on a barrier no copy
-// completes: sets *err when it gives up after limit polls.
-cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s);
+// The bounded waits of the step kernels, limit polls each, on a barrier no
+// copy completes (bit 0 of *err when it gives up: the staged kernels'
+// mbarrier wait) and on the counter *never, which nothing raises (bit 1: the
+// fused step pair's counter wait).
+cudaError_t launch_wait_probe(unsigned limit, int *err, const unsigned *never, cudaStream_t s);
 
 // Exact copy of a stored state between layouts.
 cudaError_t launch_relayout(const DevLattice &L, const void *src, int src_layout, void *dst,

@@ -65,6 +65,7 @@ struct Raw<0> {
     using T = float;
     static __device__ __forceinline__ void st_plain(float *p, float v) { *p = v; }
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
     static __device__ __forceinline__ float ld_rw(const float *p) { return HGB_AA_LD_CS ? __ldcs(p) : *p; }
     static __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
     static __device__ __forceinline__ void st_rw(float *p, float v) {
@@ -78,6 +79,9 @@ struct Raw<1> {
     using T = __half;
     static __device__ __forceinline__ void st_plain(__half *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_cg(const __half *p) {
+        return __half2float(__short_as_half(__ldcg(reinterpret_cast<const short *>(p))));
+    }
     static __device__ __forceinline__ float ld_rw(const __half *p) {
         return HGB_AA_LD_CS ? __half2float(__short_as_half(__ldcs(reinterpret_cast<const short *>(p))))
                             : __half2float(*p);
@@ -108,6 +112,7 @@ struct Raw<2> {
     using T = short;
     static __device__ __forceinline__ void st_plain(short *p, float v) { *p = float_to_i16(v); }
     static __device__ __forceinline__ float ld(const short *p) { return i16_to_float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_cg(const short *p) { return i16_to_float(__ldcg(p)); }
     static __device__ __forceinline__ float ld_rw(const short *p) {
         return i16_to_float(HGB_AA_LD_CS ? __ldcs(p) : *p);
     }
@@ -370,7 +375,7 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
     const int x = (IO ? L.n_bulk : 0) + blockIdx.x * kBlock + threadIdx.x;
     if (x >= (IO ? L.n : L.n_bulk)) return;
     const unsigned np = (unsigned)L.npad;
-    if (!IO && !BFL) {
+    if constexpr (!IO && !BFL) {
         // bulk sites: gather through the slot table, store through the planes
         float d[Q], out[Q];
         d[0] = R::ld(fin + x);
@@ -380,26 +385,26 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
         collide<Q, HALF>(L, d, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) R::st(OP.p[i] + x, out[i]);
-        return;
+    } else {
+        int s[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
+        float d[Q];
+        d[0] = R::ld(fin + x);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
+                                         : (unsigned)opp(i) * np + (unsigned)x;
+            d[i] = R::ld(fin + e);
+        }
+        if (BFL) bfl_gather<Q>(s, d);
+        float out[Q];
+        const Velocity v = collide<Q, HALF>(L, d, out);
+        if (BFL) bfl_scatter<Q>(s, out);
+        if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
     }
-    int s[Q];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) s[i] = checked_entry(L, __ldcs(L.tab + (unsigned)(i - 1) * np + (unsigned)x));
-    float d[Q];
-    d[0] = R::ld(fin + x);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const unsigned e = s[i] >= 0 ? (unsigned)i * np + (unsigned)s[i]
-                                     : (unsigned)opp(i) * np + (unsigned)x;
-        d[i] = R::ld(fin + e);
-    }
-    if (BFL) bfl_gather<Q>(s, d);
-    float out[Q];
-    const Velocity v = collide<Q, HALF>(L, d, out);
-    if (BFL) bfl_scatter<Q>(s, out);
-    if (IO) iolet_override<Q, HALF>(L, x, s, v, io, rho_io, io_dev, out);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) R::st(fout + (unsigned)i * np + (unsigned)x, out[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,19 +430,6 @@ k_step(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #define HGB_STAGED_CTAS 0
 #endif
 constexpr int kStages = HGB_STAGES;
-// The failure path of the staged step, on its own: an mbarrier that expects
-// 16 bytes no copy will ever deliver, waited on with the same bounded wait;
-// on giving up the kernel sets *err and returns (no copy was issued, so
-// nothing is in flight; the barrier is left as the staged step leaves one).
-__global__ void k_wait_probe(int *err, unsigned limit) {
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x != 0) return;
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, 16u);
-    if (!mbar_wait_bounded(&bar, 0u, limit)) atomicExch(err, 1);
-}
-
-
 
 template <int Q, int HALF>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_STEP_MINB_FP16 : HGB_STEP_MINB_FP32)
@@ -522,84 +514,174 @@ k_step_staged(const DevLattice L, const typename Raw<HALF>::T *__restrict__ fin,
 #define HGB_AA_MINB_FP16 4
 #endif
 
+// The plane length, read afresh where it is used: inside the fused pair's
+// persistent loop the compiler would otherwise keep the q plane offsets
+// i * npad live across the whole loop (loop-invariant), which costs the
+// registers the bodies need.
+__device__ __forceinline__ unsigned fresh_npad(const DevLattice &L) {
+    unsigned v;
+    asm volatile("mov.u32 %0, %1;" : "=r"(v) : "r"((unsigned)L.npad));
+    return v;
+}
+
 // The bulk-site bodies of the AA step (shared by k_step_aa and the fused step
 // pair below, so that both give the same bits).  Even step: the site's own
 // slots (measured: fp16 is faster through the plane pointers, each address
 // one multiply-add onto a pointer in the constant bank, formed again for the
-// store; fp32 through one base pointer and the plane offsets); STREAM_ST
-// selects evict-first stores (the plain even step) or default ones (the
-// fused pair, whose odd step reads them back from L2).  Odd step: through
-// the slot table.
-template <int Q, int HALF, bool STREAM_ST>
+// store; fp32 through one base pointer and the plane offsets).  Odd step:
+// through the slot table.  FUSED: the body runs inside the fused step pair,
+// where other blocks of the same launch wrote the slots it reads: loads
+// bypass L1 (.cg), so that no line cached before the write is read, and the
+// even step's stores keep their lines in L2 for the odd step (default policy
+// instead of evict-first).
+template <int Q, int HALF, bool FUSED>
 __device__ __forceinline__ void aa_even_bulk(const DevLattice &L, typename Raw<HALF>::T *__restrict__ A,
                                              const Planes<typename Raw<HALF>::T> &P, int x) {
     using R = Raw<HALF>;
-    const unsigned np = (unsigned)L.npad;
+    const unsigned np = FUSED ? fresh_npad(L) : (unsigned)L.npad;
     float d[Q], out[Q];
-    if (HALF) {
+    if (HALF && !FUSED) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(P.p[i] + x);
         collide<Q, HALF>(L, d, out);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (STREAM_ST) R::st_rw(P.p[i] + x, out[opp(i)]);
-            else R::st_plain(P.p[i] + x, out[opp(i)]);
-        }
+        for (int i = 0; i < Q; ++i) R::st_rw(P.p[i] + x, out[opp(i)]);
     } else {
         typename Raw<HALF>::T *a = A + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(a + (unsigned)i * np);
+        for (int i = 0; i < Q; ++i) d[i] = FUSED ? R::ld_cg(a + (unsigned)i * np) : R::ld_rw(a + (unsigned)i * np);
         collide<Q, HALF>(L, d, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (STREAM_ST) R::st_rw(a + (unsigned)i * np, out[opp(i)]);
-            else R::st_plain(a + (unsigned)i * np, out[opp(i)]);
+            if (FUSED) R::st_plain(a + (unsigned)i * np, out[opp(i)]);
+            else R::st_rw(a + (unsigned)i * np, out[opp(i)]);
         }
     }
 }
 
-template <int Q, int HALF>
+template <int Q, int HALF, bool FUSED>
 __device__ __forceinline__ void aa_odd_bulk(const DevLattice &L, typename Raw<HALF>::T *__restrict__ A,
                                             const SlotRows &S, int x) {
     using R = Raw<HALF>;
-    const unsigned np = (unsigned)L.npad;
+    const unsigned np = FUSED ? fresh_npad(L) : (unsigned)L.npad;
     float d[Q], out[Q];
     unsigned e[Q];
     e[0] = (unsigned)x;
+    const uint32_t *srow = L.slots + x;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) e[i] = checked_slot(L, __ldcs(S.p[i - 1] + x), (unsigned)i * np + (unsigned)x);
+    for (int i = 1; i < Q; ++i)
+        e[i] = checked_slot(L, __ldcs(FUSED ? srow + (unsigned)(i - 1) * np : S.p[i - 1] + x),
+                            (unsigned)i * np + (unsigned)x);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = R::ld_rw(A + e[i]);
+    for (int i = 0; i < Q; ++i) d[i] = FUSED ? R::ld_cg(A + e[i]) : R::ld_rw(A + e[i]);
     collide<Q, HALF>(L, d, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st_rw(A + e[i], out[opp(i)]);
 }
 
-// A fused AA step pair over slab chunks (LBM_ORDER_SLABS): the blocks
-// [0, e_blocks) run the even step of the bulk sites [e_begin, e_end), the
-// others the odd step of [o_begin, o_end).  The host launches chunk c's even
-// step together with chunk c - 2's odd step: the odd step of a chunk reads
-// and writes only slots of its own and its two neighbouring chunks (the
-// chunks are unions of whole (z) planes, and a site's neighbours lie in the
-// planes z - 1 .. z + 1), which the even steps of earlier launches have
-// finished, and the two halves of a launch touch disjoint slots.  So the odd
-// step reads back what the even step wrote one or two launches before, from
-// L2 instead of HBM.
-// resident blocks per SM of the fused pair (it holds both bodies)
+// Bounded wait of the fused step pair for a counter that other blocks of the
+// same launch raise: polls (acquire, GPU scope) at most `limit` times with a
+// short sleep between polls, about a second in all; false if it gave up.
+constexpr unsigned kPairSpinLimit = 1u << 21;
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned need, unsigned limit = kPairSpinLimit) {
+    for (unsigned it = 0; it < limit; ++it) {
+        if (ld_acquire(p) >= need) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+// The same for the three chunks c - 1 .. c + 1 at once, by warp 0 (lane l
+// polls chunk c - 1 + l; called by all 32 lanes).
+__device__ __forceinline__ bool wait_chunks(const unsigned *done, const int *tiles, int c, int nchunks, int lane) {
+    const int cc = c - 1 + lane;
+    const bool mine = lane < 3 && cc >= 0 && cc < nchunks;
+    const unsigned need = mine ? (unsigned)tiles[cc] : 0u;
+    for (unsigned it = 0; it < kPairSpinLimit; ++it) {
+        const unsigned v = mine ? ld_acquire(done + cc) : 0u;
+        if (__all_sync(0xffffffffu, v >= need)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// The two bounded waits, checked on their own (lbm_check_wait_timeout): the
+// staged kernels' mbarrier wait on a barrier that expects 16 bytes no copy
+// will ever deliver (bit 0 of *err when it gives up), and the fused step
+// pair's counter wait on a counter nothing raises (bit 1).  No copy is
+// issued, so nothing is in flight when the kernel returns.
+__global__ void k_wait_probe(int *err, const unsigned *never, unsigned limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16u);
+    if (!mbar_wait_bounded(&bar, 0u, limit)) atomicOr(err, 1);
+    if (!wait_count(never, 1u, limit)) atomicOr(err, 2);
+}
+
+// A fused AA step pair (LBM_ORDER_SLABS): one persistent launch works through
+// the plan's items in list order, each block taking the next item from a
+// counter.  An even run writes only its own sites' slots and, once its block
+// is done, counts itself done for its chunk (release); an odd run of chunk c
+// reads and writes slots of the chunks c - 1 .. c + 1 only, so it first waits
+// (acquire) until their even runs are all done.  The runs it waits for come
+// earlier in the list and were taken by blocks that are running, so every
+// wait ends.  The two steps of one chunk are two chunks apart in the list, so
+// the odd step reads the even step's output back from L2.  A wait that gives
+// up sets *err and the block stops taking items (the state is then partly
+// updated and the host refuses further steps).  The last block to finish
+// clears the counters for the next launch.
 #ifndef HGB_AA_PAIR_MINB
-#define HGB_AA_PAIR_MINB 3
+#define HGB_AA_PAIR_MINB 4
 #endif
 template <int Q, int HALF>
 __global__ void __launch_bounds__(kBlock, HGB_AA_PAIR_MINB)
 k_step_aa_pair(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Planes<typename Raw<HALF>::T> P,
-               const SlotRows S, int e_begin, int e_end, int e_blocks, int o_begin, int o_end) {
-    const int b = (int)blockIdx.x;
-    if (b < e_blocks) {
-        const int x = e_begin + b * kBlock + (int)threadIdx.x;
-        if (x < e_end) aa_even_bulk<Q, HALF, false>(L, A, P, x);
-    } else {
-        const int x = o_begin + (b - e_blocks) * kBlock + (int)threadIdx.x;
-        if (x < o_end) aa_odd_bulk<Q, HALF>(L, A, S, x);
+               const SlotRows S, const PairPlan W, int *__restrict__ err) {
+    __shared__ int item, ok;
+    const int tid = (int)threadIdx.x;
+    unsigned *next = W.ctr, *finished = W.ctr + 1, *done = W.ctr + 2;
+    bool failed = false;
+    for (;;) {
+        if (tid == 0) item = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int it = item;
+        if (it >= W.n_items) break;
+        const int4 w = W.items[it];
+        const int x = w.x + tid;
+        if (w.w) {
+            if (tid < 32) {
+                const bool good = wait_chunks(done, W.tiles, w.z, W.nchunks, tid);
+                if (tid == 0) ok = good ? 1 : 0;
+            }
+            __syncthreads();
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            if (x < w.y) aa_odd_bulk<Q, HALF, true>(L, A, S, x);
+        } else {
+            if (x < w.y) aa_even_bulk<Q, HALF, true>(L, A, P, x);
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                atomicAdd(done + w.z, 1u);
+            }
+        }
+        __syncthreads();  // every thread has read `item` and `ok`
+    }
+    if (tid == 0) {
+        if (failed) atomicExch(err, 1);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (atomicAdd(finished, 1u) == gridDim.x - 1) {
+            for (int c = 0; c < W.nchunks; ++c) done[c] = 0u;
+            *next = 0u;
+            *finished = 0u;
+        }
     }
 }
 
@@ -639,9 +721,9 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
         // bulk sites: even step on the own slots through the plane pointers,
         // odd step through the slot table; no table codes, no iolet work
         if (!ODD)
-            aa_even_bulk<Q, HALF, true>(L, A, P, x);
+            aa_even_bulk<Q, HALF, false>(L, A, P, x);
         else
-            aa_odd_bulk<Q, HALF>(L, A, S, x);
+            aa_odd_bulk<Q, HALF, false>(L, A, S, x);
         return;
     }
     int s[Q];
@@ -680,7 +762,7 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
 // k_step_aa reads and writes, S and D distinct; every slot of D is written):
 // the first step of a recomputation from an adjoint snapshot, which must stay
 // intact.  The per-site arithmetic is k_step_aa's.
-template <int Q, int HALF, bool ODD, bool IO>
+template <int Q, int HALF, bool ODD, bool IO, bool BFL = false>
 __global__ void __launch_bounds__(kBlock, HALF ? HGB_AA_MINB_FP16 : HGB_AA_MINB_FP32)
 k_step_aa_oop(const DevLattice L, const typename Raw<HALF>::T *__restrict__ S, typename Raw<HALF>::T *__restrict__ D,
               const IoletStep io) {
@@ -701,7 +783,9 @@ k_step_aa_oop(const DevLattice L, const typename Raw<HALF>::T *__restrict__ S, t
     float d[Q], out[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = R::ld(S + slot(i));
+    if (BFL) bfl_gather<Q>(s, d);
     const Velocity v = collide<Q, HALF>(L, d, out);
+    if (BFL) bfl_scatter<Q>(s, out);
     if (IO) iolet_override<Q, HALF>(L, x, s, v, io, nullptr, nullptr, out);
 #pragma unroll
     for (int i = 0; i < Q; ++i) R::st(D + slot(i), out[opp(i)]);
@@ -761,32 +845,43 @@ cudaError_t step_aa_impl(const DevLattice &L, void *A, bool odd, const IoletStep
     return e;
 }
 
-// An even step and the following odd step of the AA form as one pass over
-// the slab chunks [chunk[c], chunk[c + 1]) of the bulk sites: the iolet-site
-// even step first, then launches c = 0 .. K + 1 each holding chunk c's even
-// step and chunk c - 2's odd step, then the iolet-site odd step (which reads
-// slots of bulk sites anywhere, so it waits for every even step).
+// An even step and the following odd step of the AA form in one pass: the
+// iolet-site even step first, then the persistent fused kernel over the bulk
+// sites, then the iolet-site odd step (which reads slots of bulk sites
+// anywhere, so it waits for every even step).
+template <int Q, int HALF>
+int aa_pair_grid(int n_items) {
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_aa_pair<Q, HALF>, kBlock, 0) != cudaSuccess)
+            return -1;
+        g = sms * std::max(per, 1);
+    }
+    return std::max(1, std::min(g, n_items));
+}
+
 template <int Q, int HALF>
 cudaError_t step_aa_pair_impl(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
                               cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
-                              const int *chunk, int nchunks) {
+                              const PairPlan &W) {
     using T = typename Raw<HALF>::T;
     const int ni = L.n - L.n_bulk;
     const Planes<T> P = planes_of((T *)A, Q, L.npad);
     const SlotRows S = slot_rows_of(L);
+    if (!L.err || !W.items || !W.ctr) return cudaErrorInvalidValue;
     if (ni && L.bfl)
         k_step_aa<Q, HALF, false, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_even, nullptr,
                                                                                io_dev_even);
     else if (ni)
         k_step_aa<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_even, nullptr,
                                                                          io_dev_even);
-    for (int c = 0; c < nchunks + 2; ++c) {
-        int eb = 0, ee = 0, ob = 0, oe = 0;
-        if (c < nchunks) eb = chunk[c], ee = chunk[c + 1];
-        if (c >= 2) ob = chunk[c - 2], oe = chunk[c - 1];
-        const int e_blocks = (int)grid_for(ee - eb), o_blocks = (int)grid_for(oe - ob);
-        if (e_blocks + o_blocks == 0) continue;
-        k_step_aa_pair<Q, HALF><<<e_blocks + o_blocks, kBlock, 0, s>>>(L, (T *)A, P, S, eb, ee, e_blocks, ob, oe);
+    if (W.n_items) {
+        const int grid = aa_pair_grid<Q, HALF>(W.n_items);
+        if (grid < 0) return cudaErrorInvalidConfiguration;
+        k_step_aa_pair<Q, HALF><<<grid, kBlock, 0, s>>>(L, (T *)A, P, S, W, L.err);
     }
     if (ni && L.bfl)
         k_step_aa<Q, HALF, true, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (T *)A, P, S, io_odd, nullptr,
@@ -867,10 +962,17 @@ cudaError_t step_aa_oop_impl(const DevLattice &L, const void *src, void *dst, bo
     const int nb = L.n_bulk, ni = L.n - L.n_bulk;
     if (odd) {
         if (nb) k_step_aa_oop<Q, HALF, true, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
-        if (ni) k_step_aa_oop<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+        if (ni && L.bfl)
+            k_step_aa_oop<Q, HALF, true, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+        else if (ni)
+            k_step_aa_oop<Q, HALF, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
     } else {
         if (nb) k_step_aa_oop<Q, HALF, false, false><<<grid_for(nb), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
-        if (ni) k_step_aa_oop<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
+        if (ni && L.bfl)
+            k_step_aa_oop<Q, HALF, false, true, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst,
+                                                                                     io);
+        else if (ni)
+            k_step_aa_oop<Q, HALF, false, true><<<grid_for(ni), kBlock, 0, s>>>(L, (const T *)src, (T *)dst, io);
     }
     return cudaGetLastError();
 }
@@ -884,13 +986,13 @@ cudaError_t launch_step_aa_oop(const DevLattice &L, const void *src, void *dst, 
 
 cudaError_t launch_step_aa_pair(const DevLattice &L, void *A, const IoletStep &io_even, const IoletStep &io_odd,
                                 cudaStream_t s, const IoletStep *io_dev_even, const IoletStep *io_dev_odd,
-                                const int *chunk, int nchunks) {
+                                const PairPlan &W) {
     if (L.n == 0) return cudaSuccess;
-    return HGB_DISPATCH(L, step_aa_pair_impl, L, A, io_even, io_odd, s, io_dev_even, io_dev_odd, chunk, nchunks);
+    return HGB_DISPATCH(L, step_aa_pair_impl, L, A, io_even, io_odd, s, io_dev_even, io_dev_odd, W);
 }
 
-cudaError_t launch_wait_probe(unsigned limit, int *err, cudaStream_t s) {
-    k_wait_probe<<<1, 32, 0, s>>>(err, limit);
+cudaError_t launch_wait_probe(unsigned limit, int *err, const unsigned *never, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(err, never, limit);
     return cudaGetLastError();
 }
 

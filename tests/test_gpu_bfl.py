@@ -107,9 +107,9 @@ def test_bfl_links_state_and_adjoint():
     M.set_time(t)
     M.step(7)
     assert np.array_equal(L.get_state(), M.get_state())
-    with pytest.raises(lbm.LbmError) as ei:
-        L.objective_grad(lbm.OBJ_DENSITY, np.ones(g.n), 5, L.time, L.time + 5)
-    assert ei.value.name == "LBM_ERR_STATE"
+    # (the adjoint of interpolated walls: tests/test_gpu_adjoint_bfl.py)
+    r = L.objective_grad(lbm.OBJ_DENSITY, np.ones(g.n), 5, L.time, L.time + 5)
+    assert np.isfinite(r["J"]) and np.isfinite(r["dtau"])
 
 
 def test_bfl_vessel_tree_full_size():

@@ -21,6 +21,10 @@ def test_bytes_per_site_update():
     assert metrics.bytes_per_site_update(19, "fp16") == 148
     assert metrics.bytes_per_site_update(19, "fp32", "aa") == 188
     assert metrics.bytes_per_site_update(19, "fp16", "aa") == 112
+    assert metrics.bytes_per_site_update(19, "i16", "aa") == 112
+    # fused step pairs: per step, half of (both passes' populations + one table read)
+    assert metrics.bytes_per_site_update(19, "fp32", "aa_pairs") == 112
+    assert metrics.bytes_per_site_update(19, "fp16", "aa_pairs") == 74
 
 
 def test_profile_summaries_match_the_step_source():
@@ -31,11 +35,12 @@ def test_profile_summaries_match_the_step_source():
     import bench
 
     for form in ("aa", "pull"):
-        t = bench.recorded_traffic(bench.PROFILE_SUMMARY[form])
+        t = bench.recorded_traffic(bench.PROFILE_SUMMARY[("vessel_tree_large", form)])
         assert t is not None, form
         assert set(t) == {"traffic_bytes_per_launch_fp32", "traffic_bytes_per_launch_fp16"}
-        # within a few percent of the algorithmic bytes of one launch on the tree
-        bulk = 10_752_421
+        # within a few percent of the algorithmic bytes of one bulk launch on
+        # the at-scale tree (69.46M sites, about 69.34M without iolet links)
+        bulk = 69_340_000
         alg = {"aa": (188, 112), "pull": (224, 148)}[form]
         assert 0.9 < t["traffic_bytes_per_launch_fp32"] / (alg[0] * bulk) < 1.1
         assert 0.9 < t["traffic_bytes_per_launch_fp16"] / (alg[1] * bulk) < 1.1
