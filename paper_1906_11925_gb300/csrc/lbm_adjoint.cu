@@ -83,18 +83,21 @@ struct AdjLoad<0> {
     using T = float;
     static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
 };
+// (the 16-bit forms scale by 2^-S with an explicit rounded product: a plain
+// multiply may be fused with a later add in one adjoint kernel and not in
+// another, and the AA and pull sweeps would then differ in the last bits)
 template <>
 struct AdjLoad<1> {
     using T = __half;
     static __device__ __forceinline__ float ld(const __half *p, float inv) {
-        return __half2float(__ldg(p)) * inv;
+        return __fmul_rn(__half2float(__ldg(p)), inv);
     }
 };
 template <>
 struct AdjLoad<2> {
     using T = short;
     static __device__ __forceinline__ float ld(const short *p, float inv) {
-        return (__int_as_float(0x4B400000 + (int)__ldg(p)) - 12582912.0f) * inv;
+        return __fmul_rn(__int_as_float(0x4B400000 + (int)__ldg(p)) - 12582912.0f, inv);
     }
 };
 

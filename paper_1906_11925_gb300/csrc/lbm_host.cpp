@@ -49,6 +49,12 @@ constexpr int kGraphSteps = 32;
 constexpr int64_t kSlabBytes = HGB_SLAB_BYTES;
 // sites per item of the fused pair's work list: one per thread of a block
 constexpr int kPairRun = 256;
+// chunks between a chunk's even runs and its odd runs in that list (>= 2)
+#ifndef HGB_PAIR_LAG
+#define HGB_PAIR_LAG 2
+#endif
+constexpr int kPairLag = HGB_PAIR_LAG;
+static_assert(kPairLag >= 2, "an odd run needs the even runs of the next chunk done");
 constexpr int kGraphRing = 8;
 static_assert(kGraphSteps % 2 == 0, "a chunk must restore the buffer roles");
 
@@ -866,7 +872,8 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
 #undef CKC
     if (!slab_chunks.empty()) {
         // the fused pair's work list: runs of up to kPairRun sites, chunk c's
-        // even runs, then chunk c - 2's odd runs, for c = 0 .. K + 1
+        // even runs, then chunk (c - kPairLag)'s odd runs, for c = 0 ..
+        // K + kPairLag - 1
         const int K = (int)slab_chunks.size() - 1;
         std::vector<int4> items;
         std::vector<int> tiles((size_t)K);
@@ -874,13 +881,13 @@ HGB_API lbm_status lbm_create(lbm_ctx **out, const lbm_params *p, int64_t n, con
             for (int a = slab_chunks[(size_t)c]; a < slab_chunks[(size_t)c + 1]; a += kPairRun)
                 items.push_back(make_int4(a, std::min(a + kPairRun, slab_chunks[(size_t)c + 1]), c, odd));
         };
-        for (int c = 0; c < K + 2; ++c) {
+        for (int c = 0; c < K + kPairLag; ++c) {
             if (c < K) {
                 const size_t before = items.size();
                 runs(c, 0);
                 tiles[(size_t)c] = (int)(items.size() - before);
             }
-            if (c >= 2) runs(c - 2, 1);
+            if (c >= kPairLag) runs(c - kPairLag, 1);
         }
         const size_t ctr_bytes = sizeof(unsigned) * (size_t)(2 + K);
         if (cudaMalloc((void **)&c->pair_items, sizeof(int4) * items.size()) != cudaSuccess ||

@@ -720,6 +720,14 @@ k_step_aa(const DevLattice L, typename Raw<HALF>::T *__restrict__ A, const Plane
     if (!IO) {
         // bulk sites: even step on the own slots through the plane pointers,
         // odd step through the slot table; no table codes, no iolet work
+        if (HGB_PF_BLOCKS > 0) {
+            // the population rows (and, for the odd step, the slot-table
+            // rows) of the tile HGB_PF_BLOCKS blocks ahead
+            const unsigned x0 = (blockIdx.x + HGB_PF_BLOCKS) * (unsigned)kBlock;
+            const int r = (int)threadIdx.x;
+            prefetch_rows(A, sizeof(typename Raw<HALF>::T), np, Q, x0, (unsigned)L.n_bulk, np, r);
+            if (ODD) prefetch_rows(L.slots, 4u, np, Q - 1, x0, (unsigned)L.n_bulk, np, r - Q);
+        }
         if (!ODD)
             aa_even_bulk<Q, HALF, false>(L, A, P, x);
         else

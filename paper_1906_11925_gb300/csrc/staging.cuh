@@ -49,5 +49,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// Bulk prefetch of `bytes` bytes at p into L2 (no destination, no barrier:
+// the copy engine fetches the lines while the issuing thread goes on).  p
+// must be 16-byte aligned, bytes a multiple of 16, and the whole range inside
+// one allocation.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The bulk step and adjoint kernels prefetch into L2, at their start, the
+// rows of the tile HGB_PF_BLOCKS blocks ahead of their own (the blocks of a
+// launch start roughly in index order, so that tile is read a few block
+// lifetimes later): more bytes in flight per SM than the threads' own loads
+// give at the occupancy their registers allow.  0 switches it off.
+#ifndef HGB_PF_BLOCKS
+#define HGB_PF_BLOCKS 608
+#endif
+
+// The prefetch of one tile: nrows rows of `elem` bytes per site, row r at
+// base + r * row_stride elements, sites [x0, x0 + 256) clipped to the row
+// length npad (a multiple of 128, so every range stays 256-byte aligned and
+// a multiple of 16 bytes); thread r in [0, nrows) issues row r.  Returns at
+// once when x0 is at or past `limit`.
+__device__ __forceinline__ void prefetch_rows(const void *base, unsigned elem, unsigned row_stride, int nrows,
+                                              unsigned x0, unsigned limit, unsigned npad, int r) {
+    if (r < 0 || r >= nrows || x0 >= limit) return;
+    const unsigned cnt = min(256u, npad - x0);
+    const char *p = (const char *)base + ((size_t)r * row_stride + x0) * elem;
+    l2_prefetch(p, cnt * elem);
+}
+
 }  // namespace
 }  // namespace hemelb_gb300
