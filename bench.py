@@ -9,7 +9,7 @@ inlet at rho 1.001 and 32 outlets at rho 1.0, synthetic data.  ``--workload
 vessel_tree`` runs the same tree at its stated root radius 48 in 1024^3
 (10,787,566 sites).  One benchmark step = 100 lattice-Boltzmann time steps
 (fused collide-and-stream kernels, AA-pattern streaming in place by default,
-sites kept along a Morton curve of 32-site runs) + density/velocity/wall-
+sites kept in (z, y, x) row order, ``--site-order``) + density/velocity/wall-
 shear-stress fields + the float64 mass reduction.  value = fluid sites x LB
 time steps / device time, fp32 storage; the fp16-deviation storage form and
 the pull streaming form are reported beside it.  The inputs (~13 GB touched
@@ -73,6 +73,11 @@ WORKLOADS = {
     "tube": dict(q=15, tau=0.8, desc="straight tube r=8, 17x17x64, rho 1.001 -> 0.999"),
 }
 
+
+# --site-order: the binding's constant and a description
+SITE_ORDERS = {"rows": ("ORDER_ROWS", "(z, y, x) row order"),
+               "runs": ("ORDER_MORTON_RUNS", "Morton curve of 32-site runs along x"),
+               "morton": ("ORDER_MORTON", "Morton (Z-order) curve of (x, y, z)")}
 
 RENDER_SPINUP = 2000
 I16_SCALE_LOG2 = 24  # int16 leg: step 2^-24, range |d| < 1.95e-3
@@ -239,10 +244,16 @@ def run_ours(args):
 
     main_form = args.streaming
     alt_form = "pull" if main_form == "aa" else "aa"
+    # the order the device keeps the sites in (every order gives the same
+    # results to the bit; on the 69.5M-site tree the (z, y, x) row order makes
+    # the odd AA step's scattered accesses faster than the Morton curve of
+    # 32-site runs: 1,903 / 1,318 us per fp32 / fp16 step against 1,948 / 1,438)
+    main_order = getattr(lbm, SITE_ORDERS[args.site_order][0])
     stream_id = {"pull": lbm.STREAM_PULL, "aa": lbm.STREAM_AA}
 
     def device_leg(storage, sampler=None, streaming=lbm.STREAM_PULL, wall_q=None,
-                   site_order=lbm.ORDER_MORTON_RUNS, scale_log2=None):
+                   site_order=None, scale_log2=None):
+        site_order = main_order if site_order is None else site_order
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=storage, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
                         streaming=streaming, wall_q=wall_q, site_order=site_order,
@@ -279,9 +290,10 @@ def run_ours(args):
         total_ms = max_over_ranks(t0.elapsed_time(t1))
         step_kernel_ms = sum(a.elapsed_time(b) for a, b in evs)
         finite = all(math.isfinite(m) for m in mass_dev)
+        chunks = L.slab_chunks()
         L.close()
         return dict(total_ms=total_ms, step_kernel_ms=step_kernel_ms, clocks=clocks, finite=finite,
-                    mass_last=mass_dev[-1] if mass_dev else None)
+                    mass_last=mass_dev[-1] if mass_dev else None, chunks=chunks)
 
     def e2e_leg():
         # the user's call path with host buffers: per benchmark step, the inlet
@@ -289,7 +301,7 @@ def run_ours(args):
         # memory, and the resulting total mass comes back device -> host.
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP32, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
-                        streaming=stream_id[main_form])
+                        streaming=stream_id[main_form], site_order=main_order)
         K = g.n_iolets
         rows = []
         for s in range(args.warmup + args.steps):
@@ -317,7 +329,7 @@ def run_ours(args):
         # binomial checkpointing with as many snapshots as fit in 150 GB
         L = lbm.Lattice(q, g.xyz, nbr, link, tau, storage=lbm.STORE_FP16, rho_mean=g.rho_mean,
                         amp=g.amp, period=g.period, phase=g.phase, stream=stream,
-                        streaming=stream_id[main_form])
+                        streaming=stream_id[main_form], site_order=main_order)
         nsteps = args.adjoint_steps
         inlet = (link == 2).any(axis=0)
         outlet = (link >= 3).any(axis=0)
@@ -417,6 +429,11 @@ def run_ours(args):
     alt = alt_form in legs
     raa32 = device_leg(lbm.STORE_FP32, streaming=stream_id[alt_form]) if alt else None
     raa16 = device_leg(lbm.STORE_FP16, streaming=stream_id[alt_form]) if alt else None
+    # AA step pairs fused over slab chunks of whole z planes (the odd step
+    # reads the even step's output back from L2), beside the unfused AA step
+    slabs = "slabs" in legs and main_form == "aa"
+    rsl32 = device_leg(lbm.STORE_FP32, streaming=lbm.STREAM_AA, site_order=lbm.ORDER_SLABS) if slabs else None
+    rsl16 = device_leg(lbm.STORE_FP16, streaming=lbm.STREAM_AA, site_order=lbm.ORDER_SLABS) if slabs else None
     e2e = e2e_leg() if "e2e" in legs else None
     adj = adjoint_leg() if "adjoint" in legs else None
     rnd = render_leg() if "render" in legs else None
@@ -477,7 +494,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": W["desc"], "lattice": "D3Q%d" % q,
                    "tau": tau, "fluid_sites": g.n, "iolets": g.n_iolets, "storage": "fp32",
                    "streaming": forms[main_form],
-                   "site_order": "Morton curve of 32-site runs along x",
+                   "site_order": SITE_ORDERS[args.site_order][1],
                    "lb_steps_per_bench_step": inner,
                    "bench_step": "%d fused collide-stream steps + rho/u/WSS fields + fp64 mass"
                                  % inner,
@@ -510,6 +527,19 @@ def run_ours(args):
             "fp16": {"value": round(world * metrics.msups(g.n, n_lb, raa16["total_ms"] / 1e3), 2),
                      "unit": "MSUPS", "ms_per_step": round(raa16["total_ms"] / args.steps, 4),
                      "roofline": roofline(raa16, "fp16", alt_form)}},
+        "slabs": None if not rsl32 else {
+            "streaming": "AA step pairs fused over slab chunks of whole z planes (row order): one "
+                         "persistent launch per even+odd pair, the odd step of a chunk reading the "
+                         "even step's output back from L2",
+            "chunks": {"fp32": rsl32["chunks"], "fp16": rsl16["chunks"]},
+            "fp32": {"value": round(world * metrics.msups(g.n, n_lb, rsl32["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(rsl32["total_ms"] / args.steps, 4),
+                     "launch_us": round(rsl32["step_kernel_ms"] * 1e3 / n_lb, 2),
+                     "speedup_vs_unfused": round(r32["total_ms"] / rsl32["total_ms"], 3)},
+            "fp16": {"value": round(world * metrics.msups(g.n, n_lb, rsl16["total_ms"] / 1e3), 2),
+                     "unit": "MSUPS", "ms_per_step": round(rsl16["total_ms"] / args.steps, 4),
+                     "launch_us": round(rsl16["step_kernel_ms"] * 1e3 / n_lb, 2),
+                     "speedup_vs_unfused": None if not r16 else round(r16["total_ms"] / rsl16["total_ms"], 3)}},
         "adjoint": adj,
         "render": rnd,
         "bfl": None if not rbfl32 else {
@@ -525,7 +555,8 @@ def run_ours(args):
         # the fields, and the two mass kernels
         "gpu_launches": args.steps * (inner * (2 if g.n_iolets else 1) + 1 + 2),
         "clocks": r32["clocks"],
-        "finite": all(r is None or r["finite"] for r in (r32, r16, ri16, raa32, raa16, rbfl32, rbfl16)),
+        "finite": all(r is None or r["finite"] for r in (r32, r16, ri16, raa32, raa16, rbfl32, rbfl16, rsl32,
+                                                          rsl16)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, g, nbr, link, q, tau,
@@ -622,7 +653,7 @@ def main():
                     help="LB time steps per benchmark step")
     ap.add_argument("--streaming", choices=("aa", "pull"), default="aa",
                     help="streaming form of the main legs (the other one is the comparison leg)")
-    ap.add_argument("--legs", default="fp32,fp16,i16,pull,aa,e2e,adjoint,render,bfl",
+    ap.add_argument("--legs", default="fp32,fp16,i16,pull,aa,slabs,e2e,adjoint,render,bfl",
                     help="comma list of fp32 (always run), fp16, i16, pull, aa (the comparison "
                          "leg of the form not chosen by --streaming), e2e, adjoint, render, bfl")
     ap.add_argument("--adjoint-steps", type=int, default=3000)
@@ -630,6 +661,9 @@ def main():
                     help="snapshot count (default: as many as fit in 150 GB)")
     ap.add_argument("--render-spinup", type=int, default=RENDER_SPINUP,
                     help="LB steps before the render leg's frames")
+    ap.add_argument("--site-order", choices=sorted(SITE_ORDERS), default="rows",
+                    help="order the device keeps the sites in, for every leg but the interpolated-wall "
+                         "and slab-chunk legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()

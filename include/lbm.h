@@ -136,15 +136,17 @@ typedef struct lbm_ctx lbm_ctx; /* opaque */
  *              LBM_ORDER_MORTON (1): the Morton (Z-order) curve of (x, y, z);
  *              LBM_ORDER_ROWS (2): (z, y, x) row order;
  *              LBM_ORDER_SLABS (3): row order, and with LBM_STREAM_AA the
- *              bulk sites are cut into chunks of whole z planes (about 16 MB
+ *              bulk sites are cut into chunks of whole z planes (about 1 MB
  *              of populations each) and lbm_step runs each even step and the
  *              odd step after it as one persistent launch over them: the odd
- *              step of a chunk runs as soon as the even steps of the chunk
- *              and its two neighbours are done, two chunks behind the even
- *              steps, and reads the even step's output back from L2 instead
- *              of HBM (the same results to the bit).  Where a site's
- *              neighbour lies more than one chunk away (a periodic z axis)
- *              the pairs run unfused. */
+ *              step of a chunk runs once the even steps of the chunk and its
+ *              two neighbours are done, 14 chunks behind the even steps, and
+ *              reads the even step's output back from L2 instead of HBM (the
+ *              same results to the bit; about 40% fewer HBM bytes per step,
+ *              but not faster than the unfused form in float32 and slower
+ *              with 16-bit storage, whose unfused even step runs at higher
+ *              occupancy).  Where a site's neighbour lies more than one
+ *              chunk away (a periodic z axis) the pairs run unfused. */
 typedef struct {
     int32_t q;
     int32_t storage;

@@ -42,16 +42,20 @@ using namespace hemelb_gb300;
 // record sets in flight
 constexpr int kGraphSteps = 32;
 // populations per slab chunk of the fused AA step pairs (LBM_ORDER_SLABS):
-// a few chunks must stay in L2 between a chunk's even and odd step
+// the chunks between a chunk's even and odd step must stay in L2, and the
+// lag (below) must exceed the sites that the resident blocks work on at once
+// (608 blocks of 256), so that an odd run rarely waits; measured on the
+// 10.8M-site tree, fp32: 1 MB with lag 14 306.6 us per step, 2 MB lag 6
+// 309.8, 8 MB lag 2 311.3, 16 MB lag 2 327.1 (the unfused AA step 310.7)
 #ifndef HGB_SLAB_BYTES
-#define HGB_SLAB_BYTES (16 << 20)
+#define HGB_SLAB_BYTES (1 << 20)
 #endif
 constexpr int64_t kSlabBytes = HGB_SLAB_BYTES;
 // sites per item of the fused pair's work list: one per thread of a block
 constexpr int kPairRun = 256;
 // chunks between a chunk's even runs and its odd runs in that list (>= 2)
 #ifndef HGB_PAIR_LAG
-#define HGB_PAIR_LAG 2
+#define HGB_PAIR_LAG 14
 #endif
 constexpr int kPairLag = HGB_PAIR_LAG;
 static_assert(kPairLag >= 2, "an odd run needs the even runs of the next chunk done");

@@ -630,8 +630,9 @@ __global__ void k_wait_probe(int *err, const unsigned *never, unsigned limit) {
 // reads and writes slots of the chunks c - 1 .. c + 1 only, so it first waits
 // (acquire) until their even runs are all done.  The runs it waits for come
 // earlier in the list and were taken by blocks that are running, so every
-// wait ends.  The two steps of one chunk are two chunks apart in the list, so
-// the odd step reads the even step's output back from L2.  A wait that gives
+// wait ends.  The two steps of one chunk are a fixed number of chunks apart
+// in the list (the host's lag), so the odd step reads the even step's output
+// back from L2.  A wait that gives
 // up sets *err and the block stops taking items (the state is then partly
 // updated and the host refuses further steps).  The last block to finish
 // clears the counters for the next launch.
