@@ -183,6 +183,33 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert got == want
 
 
+def test_binding_constants_match_the_header(tmp_path):
+    """Every enum value the binding passes through the ABI (storage forms,
+    streaming forms, site orders, iolet kinds, objectives, rendered
+    quantities, filters) and every status name it reports equals the
+    header's, as the C compiler sees it; and the benchmark's site-order
+    choices name the binding's constants."""
+    names = ["STORE_FP32", "STORE_FP16", "STORE_I16", "STREAM_PULL", "STREAM_AA", "IOLET_DENSITY",
+             "IOLET_VELOCITY", "MAX_IOLETS", "ORDER_MORTON_RUNS", "ORDER_MORTON", "ORDER_ROWS",
+             "ORDER_SLABS", "OBJ_WSS", "OBJ_DENSITY", "QTY_DENSITY", "QTY_SPEED", "QTY_WSS",
+             "FILTER_TEXTURE", "FILTER_EXACT"]
+    status = sorted(lbm._STATUS.items())
+    src = tmp_path / "enums.c"
+    body = "".join('  printf("%%d\\n", (int)LBM_%s);\n' % n for n in names)
+    body += "".join('  printf("%%d\\n", (int)%s);\n' % nm for _, nm in status)
+    src.write_text('#include <stdio.h>\n#include "lbm.h"\nint main(void) {\n' + body + "  return 0;\n}\n")
+    exe = tmp_path / "enums"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == [getattr(lbm, n) for n in names] + [code for code, _ in status]
+    import bench
+    orders = {k: getattr(lbm, c) for k, (c, _) in bench.SITE_ORDERS.items()}
+    assert orders == {"rows": lbm.ORDER_ROWS, "runs": lbm.ORDER_MORTON_RUNS, "morton": lbm.ORDER_MORTON}
+
+
 def test_render_calls_reject_bad_arguments_before_any_gpu_call():
     lib = lbm.load_library()
     out = C.c_void_p()
