@@ -57,11 +57,12 @@ __device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// The bulk step and adjoint kernels prefetch into L2, at their start, the
-// rows of the tile HGB_PF_BLOCKS blocks ahead of their own (the blocks of a
-// launch start roughly in index order, so that tile is read a few block
-// lifetimes later): more bytes in flight per SM than the threads' own loads
-// give at the occupancy their registers allow.  0 switches it off.
+// The bulk AA step kernels prefetch into L2, at their start, the rows of the
+// tile HGB_PF_BLOCKS blocks ahead of their own (the blocks of a launch start
+// roughly in index order, so that tile is read a few block lifetimes later):
+// more bytes in flight per SM than the threads' own loads give at the
+// occupancy their registers allow.  0 switches it off.  (The AA adjoint
+// kernels do the same with their own distances.)
 #ifndef HGB_PF_BLOCKS
 #define HGB_PF_BLOCKS 608
 #endif
