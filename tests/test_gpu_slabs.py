@@ -67,6 +67,24 @@ def test_slab_pairs_on_the_tree(tree, storage):
         assert np.array_equal(S.get_populations(), A.get_populations()), n
 
 
+@pytest.mark.parametrize("storage", [lbm.STORE_FP32, lbm.STORE_FP16])
+def test_row_order_equals_the_default_order_on_the_tree(tree, storage):
+    """The benchmark's launch configuration (AA streaming, sites in row order,
+    CUDA-graph chunks) gives the default order's populations bit for bit."""
+    q = 19
+    nbr, link = lbm.links_build(q, tree.xyz, tree.io_xyz, tree.io_id, tree.periodic)
+    kw = dict(storage=storage, rho_mean=tree.rho_mean, amp=tree.amp, period=tree.period, phase=tree.phase,
+              streaming=lbm.STREAM_AA)
+    R = lbm.Lattice(q, tree.xyz, nbr, link, 0.6, site_order=lbm.ORDER_ROWS, **kw)
+    A = lbm.Lattice(q, tree.xyz, nbr, link, 0.6, **kw)
+    for n in (67, 33):  # two graph chunks and three single steps, then one chunk and one step
+        R.step(n)
+        A.step(n)
+        assert np.array_equal(R.get_populations(), A.get_populations()), n
+    # (the mass sums the same values in another order)
+    assert abs(R.mass() - A.mass()) <= 1e-12 * A.mass()
+
+
 def test_slab_pairs_with_interpolated_walls(tree):
     """Interpolated walls (their sites run in the unfused tail launches) on
     the tree: bitwise the pull form."""
